@@ -1,0 +1,337 @@
+"""Benchmark of the QI search hot path on GB300: one JSON line on rank 0.
+
+Workload (default): 120 instances, n = 600, J_ij and h_i ~ N(0, 1) on the 2^-32 grid,
+K = 120 (K+1 = 121 kept states), R = 64 random initial states per instance, I = K = 120
+iterations, split-BF16 precision mode. One step = reset every search to its initial state,
+run I iterations of Alg. 3 on all 7680 searches, merge the R lists of every instance
+(Alg. 4) on the device.
+
+  value  pair-flip candidates evaluated per second (device time, CUDA events on the
+         library stream, inputs resident in HBM; the 520 MB of J planes exceed L2)
+  e2e    the same metric through the C ABI with host buffers: each step copies J, h and
+         the initial states to the device, iterates, and copies back the merged K+1 states
+         of every instance with FP64 energies
+  roofline  the candidate-scan kernel against the SM issue rate (2 ALU operations per
+         pair candidate: signed add and compare)
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores)
+
+--impl reference times the oracle (the CPU reference of this tier) on the same metric.
+Under torchrun every rank runs its own 120 instances (weak scaling, no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-flip candidates evaluated/s and time-to-ground-state at N=600 on 1 GB300"
+UNIT = "pair candidates/s"
+
+WORKLOADS = {
+    # name: (ensemble, n, instances, K, R, iterations, precision)
+    "gaussian_n600_120x64": ("gaussian", 600, 120, 120, 64, 120, "split_bf16"),
+    "gaussian_n100_120x32_fp64": ("gaussian", 100, 120, 120, 32, 120, "fp64"),
+    "pm1_n1024_64x128": ("pm1", 1024, 64, 120, 128, 120, "pm1_fp8"),
+    "gaussian_n16_1x4": ("gaussian", 16, 1, 8, 4, 8, "split_bf16"),
+}
+DEFAULT = "gaussian_n600_120x64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def _oracle_job(args):
+    ens, n, K, I_, seed, inst, r = args
+    from oracle import oracle as O
+    from paper_2010_00180_gb300 import inputs as I
+    J, h = I.instance(ens, n, seed=seed, inst=inst)
+    phi = I.random_states(n, 1 + r, seed=seed + 1000, inst=inst)[r]
+    t = time.perf_counter()
+    res = O.qi_search(J, h, K, I_, phi)
+    return time.perf_counter() - t, res["productive"]
+
+
+def oracle_sample(workload, n_searches, cores, seed):
+    """The oracle as it stands on `n_searches` searches of instance 0 (full I iterations each),
+    one process per core (spawned before any GPU use)."""
+    ens, n, _, K, _, I_, _ = WORKLOADS[workload]
+    from oracle import oracle as O
+    O.build()
+    jobs = [(ens, n, K, I_, seed, 0, r) for r in range(n_searches)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        out = pool.map(_oracle_job, jobs)
+    wall = time.perf_counter() - t0
+    pairs = sum(p for _, p in out) * n * (n - 1) // 2
+    return dict(value=pairs / wall, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{n_searches} searches x {I_} iterations of instance 0 of {workload} "
+                       f"({pairs:.3e} pair candidates, {wall:.1f} s wall)", wall_s=wall)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self, device):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+            rows = [[x.strip() for x in r] for r in rows if r[0].strip() == str(device)]
+            if not rows:
+                return out
+            sm = sorted(float(r[1]) for r in rows)
+            out["sm_mhz"] = sm[len(sm) // 2]
+            out["sm_max_mhz"] = float(rows[0][2])
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            rs = set()
+            for r in rows:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        rs.add(nm)
+            out["reasons"] = sorted(rs)
+            out["samples"] = len(rows)
+        except Exception:
+            pass
+        return out
+
+
+# ------------------------------------------------------------------ GPU arm
+def make_inputs(workload, seed):
+    from paper_2010_00180_gb300 import inputs as I
+    ens, n, n_inst, K, R, I_, prec = WORKLOADS[workload]
+    data = []
+    for k in range(n_inst):
+        J, h = I.instance(ens, n, seed=seed, inst=k)
+        phi = I.random_states(n, R, seed=seed + 1000, inst=k)
+        data.append((J, h, phi))
+    return data
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    import torch.distributed as dist
+    from paper_2010_00180_gb300 import build as B, qis as Q
+
+    B.build()
+    ens, n, n_inst, K, R, I_, prec = WORKLOADS[args.workload]
+    seed = args.seed + 7919 * rank                     # each rank: its own instances
+    data = make_inputs(args.workload, seed)
+    ctx = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device)
+    for J, h, phi in data:
+        iid = ctx.create_instance(J, h)
+        ctx.init_states(iid, phi)
+    stream = torch.cuda.ExternalStream(ctx.stream_handle(), device=device)
+
+    def step():
+        ctx.reset()
+        ctx.iterate(I_)
+        ctx.merge()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.synchronize()
+    launches0 = ctx.kernel_launches()
+    pairs0, _ = ctx.candidate_count()
+    for k in range(5):
+        ctx.profile_query(k)                            # drop warm-up timings
+    ctx.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/qis_clocks_{os.getpid()}.csv") as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ctx.synchronize()
+        torch.cuda.synchronize(device)
+    ms = ev0.elapsed_time(ev1)
+    ctx.profile(False)
+    prof = {name: ctx.profile_query(k) for k, name in enumerate(Q.KERNEL_CLASSES)}
+    launches = ctx.kernel_launches() - launches0
+    pairs, _ = ctx.candidate_count()
+    pairs -= pairs0
+    t = torch.tensor([ms, float(pairs)], dtype=torch.float64, device=f"cuda:{device}")
+    if world > 1:
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:], op=dist.ReduceOp.SUM)
+        t = tm
+    ms_max, pairs_all = float(t[0]), float(t[1])
+
+    # time to ground state: best merged energy per instance vs a 4x longer reference run
+    best = np.array([ctx.topk_states(k, 1)["E"][0] for k in range(n_inst)])
+    ref_ctx = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device)
+    for J, h, phi in data:
+        iid = ref_ctx.create_instance(J, h)
+        ref_ctx.init_states(iid, phi)
+    ref_ctx.iterate(4 * I_)
+    ref_best = np.array([ref_ctx.topk_states(k, 1)["E"][0] for k in range(n_inst)])
+    ref_ctx.close()
+    gs = np.minimum(best, ref_best)
+    p1 = float(np.mean(np.abs(best - gs) <= 1e-9 * np.abs(gs)))
+    t_step = ms_max / args.steps / 1e3
+    if p1 >= 1.0:
+        tts = 0.0
+    elif p1 <= 0.0:
+        tts = math.inf
+    else:
+        tts = math.log(1 - 0.99) / math.log(1 - p1) * t_step
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        h2d = sum(J.nbytes + h.nbytes + phi.nbytes for J, h, phi in data)
+        d2h = n_inst * (K + 1) * ((n + 63) // 64 * 8 + 8 + 8)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.clear_instances()
+            for J, h, phi in data:
+                iid = ctx.create_instance(J, h)
+                ctx.init_states(iid, phi)
+            ctx.iterate(I_)
+            for k in range(n_inst):
+                ctx.topk_states(k, K + 1)
+        e2e_s = time.perf_counter() - t0
+        e2e = dict(value=pairs / args.steps * args.e2e_steps / e2e_s * world, unit=UNIT,
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+    clocks = clk.summary(device)
+    ctx.close()
+    return dict(ms=ms_max, pairs=pairs_all, prof=prof, launches=launches, p1=p1, tts=tts, t_step=t_step,
+                e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec)
+
+
+def roofline(res, pk):
+    """Candidate scan (dominant kernel) against the SM issue rate."""
+    ms, nl = res["prof"]["scan"]
+    if nl == 0 or ms <= 0:
+        return None
+    n, n_inst, R = res["n"], res["n_inst"], res["R"]
+    pairs_per_launch = res["pairs"] / max(1, nl)   # active searches only
+    ops_per_launch = 2.0 * pairs_per_launch       # signed add + compare per pair candidate
+    dur = ms / nl / 1e3
+    achieved = ops_per_launch / dur / 1e12
+    clk = pk.get("sm_max_mhz", 2070.0)
+    peak = 152 * 128 * clk * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan32",
+            "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-searches", type=int, default=0, help="oracle sample size (0 = one per core)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+    ens, n, n_inst, K, R, I_, prec = WORKLOADS[args.workload]
+    config = {"workload": args.workload, "ensemble": ens, "n": n, "instances_per_gpu": n_inst, "K": K,
+              "kept": K + 1, "R": R, "iterations": I_, "precision": prec,
+              "l2": "inputs larger than L2 (J planes of all instances streamed every iteration)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ns = args.cpu_searches or cores
+        vals = []
+        for _ in range(args.warmup + args.steps):
+            vals.append(oracle_sample(args.workload, ns, cores, args.seed))
+        timed = vals[args.warmup:]
+        v = float(np.mean([x["value"] for x in timed]))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": float(np.mean([x["wall_s"] for x in timed])) * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": UNIT},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    # CPU baseline first: its worker processes are spawned before any GPU call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.workload, args.cpu_searches or cores, cores, args.seed)
+        cpu.pop("wall_s", None)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    res = run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    pk, src = peaks()
+    rl = roofline(res, pk)
+    value = res["pairs"] / (res["ms"] / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 filter / int64 exact keys" if prec != "fp64" else "f64", "data": "synthetic",
+            "config": config, "roofline": rl, "peak_source": src,
+            "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"],
+            "tts": {"p1": res["p1"], "seconds": res["tts"], "t_run_s": res["t_step"],
+                    "reference": "best of this run and a 4x-iteration run of the same searches (not certified)"},
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["prof"].items()}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * qis.h -- C ABI of the GB300 quantum-inspired (QI) search library (libqis.so).
+ *
+ * The method is the QI search of Ueda, Otsuka and Yunoki (arXiv 2010.00180) for
+ * low-energy states of the classical Ising Hamiltonian
+ *     H0 = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i                          (Eq. (1))
+ * Each search keeps K+1 product states sorted by energy (Alg. 2); every iteration takes
+ * the first unused kept state as the parent, generates all its single flips X_i and
+ * pair flips X_i X_j (the flip sets of Sec. III, H1 of Eq. (H1)), and keeps the K+1
+ * lowest distinct states (Alg. 3). R independent searches per instance start from R
+ * initial states and their lists are merged at the end (Alg. 4, R = L).
+ *
+ * Conventions shared by every entry point:
+ *  - States are packed bits, W = ceil(n/64) little-endian uint64 words per state; bit i
+ *    is sigma_i of Eq. (4) and sigma_i = 1 means s_i = -1. Bits above n must be zero.
+ *  - Every pointer in this header is a HOST pointer. The caller owns all buffers; the
+ *    library copies what it needs before returning and never keeps a caller pointer.
+ *  - Return value: 0 on success, a negative QIS_ERR_* code on failure. The failing
+ *    call leaves a message for qis_last_error(). A context is used by one host thread
+ *    at a time.
+ *  - Kept lists are ordered by the key (E, stamp): ascending energy, ties broken by
+ *    arrival, which is the order Alg. 2 produces by inserting a new state after every
+ *    kept state of equal energy. stamp = 0 for the initial state and (t << 32) | c for
+ *    candidate c (c = i for the single flip of site i, c = n + rank(i, j) for the pair
+ *    i < j in lexicographic order) generated in iteration t (1-based).
+ *  - Device work runs on the library's own CUDA stream. qis_iterate and qis_reset are
+ *    asynchronous; calls that return data to the host synchronise that stream.
+ */
+#ifndef QIS_H
+#define QIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define QIS_OK 0
+#define QIS_ERR_INVALID_ARG (-1)  /* bad size, K, pointer, non-symmetric J, nonzero diagonal, NaN/Inf, ... */
+#define QIS_ERR_OOM (-2)          /* device allocation failed */
+#define QIS_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define QIS_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define QIS_ERR_CAPACITY (-5)     /* a per-search survivor buffer overflowed (raise survivor_cap) */
+#define QIS_ERR_STATE (-6)        /* call out of order (e.g. iterate before init_states) */
+
+/* Arithmetic of the local fields and candidate energies (precision modes). */
+#define QIS_FP64 0        /* plain form: FP64 fields, energies and comparisons, in the same
+                             evaluation order as the definition in oracle-free terms below */
+#define QIS_SPLIT_BF16 1  /* J fixed-point on the 2^-q grid, split into signed 8-bit digits;
+                             exact integer fields from BF16 digit GEMMs (FP32 accumulate);
+                             FP32 candidate filter with a rigorous error band; exact keys */
+#define QIS_PM1_FP8 2     /* integer couplings |J_ij| <= 15 (e.g. +-J), integer h: one FP8
+                             digit, exact integer fields and energies */
+
+typedef struct qis_ctx qis_ctx; /* opaque, library-owned */
+
+typedef struct {
+  int K;             /* each search keeps K+1 states (Alg. 2 requires 1 <= K < 2^n) */
+  int R;             /* searches (initial states) per instance: L of Alg. 4 */
+  int precision;     /* QIS_FP64 | QIS_SPLIT_BF16 | QIS_PM1_FP8 */
+  int max_n;         /* largest n of any instance added to this context (2 <= n <= 4096) */
+  int max_instances; /* capacity of the instance table */
+  int survivor_cap;  /* per-search candidate buffer (0 = default 4096) */
+  int device;        /* CUDA device ordinal */
+  uint64_t seed;     /* key of the library's SplitMix64 stream for random initial states */
+} qis_config;
+
+/* Create a context and allocate every device buffer it will use (sized by max_n,
+ * max_instances, K, R). Nothing else allocates device memory afterwards. */
+int qis_create(const qis_config* cfg, qis_ctx** out);
+
+/* Free the context and all its device memory. NULL is ignored. */
+void qis_destroy(qis_ctx* ctx);
+
+/* Message of the last failing call on this context (or of the last failed qis_create
+ * when ctx is NULL). Never NULL; valid until the next call on the context. */
+const char* qis_last_error(const qis_ctx* ctx);
+
+/* Add one Ising instance H0 (Eq. (1)).
+ *   n: number of spins, 2 <= n <= cfg.max_n.
+ *   J: n*n FP64 row-major, symmetric (bitwise J_ij == J_ji), zero diagonal, finite.
+ *   h: n FP64 finite.
+ * Instances get consecutive ids from 0. In QIS_SPLIT_BF16 the values are represented on
+ * the grid 2^-q with the smallest q that holds them exactly, capped so that every energy
+ * sum stays below 2^52 * 2^-q; if the cap binds, J and h are rounded to that grid and
+ * qis_instance_info reports it. QIS_PM1_FP8 requires integer J (|J_ij| <= 15) and h.
+ * Synchronises the library stream (validation result). */
+int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id);
+
+/* Remove every instance (ids restart at 0); device buffers stay allocated. */
+int qis_clear_instances(qis_ctx* ctx);
+
+/* Grid exponent q and number of 8-bit digits of an instance, and whether its input had to
+ * be rounded onto the grid (QIS_SPLIT_BF16 / QIS_PM1_FP8; q = -1 in QIS_FP64). */
+int qis_instance_info(qis_ctx* ctx, int instance_id, int* q, int* digits, int* rounded);
+
+/* Set the R initial states of an instance and reset its R searches to the start of
+ * Alg. 3: list = [initial state] followed by K empty slots, nothing used.
+ *   bits: R*W words (search r's state at bits + r*W), or NULL to draw every bit from the
+ *         library's SplitMix64 stream: bit i of search r of instance id is the top bit of
+ *         value (r*n + i) of the stream keyed by key(seed, id), i.e. rand_between(0, 2^n-1)
+ *         of Alg. 4. */
+int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits);
+
+/* Reset every search of every instance to its stored initial state (device-side, no host
+ * copy). */
+int qis_reset(qis_ctx* ctx);
+
+/* Run n_iters iterations of Alg. 3 on every search of every instance (lockstep).
+ * A search whose kept states are all used does nothing in an iteration.
+ *   n_active: if not NULL, receives the number of searches that still have an unused
+ *             state after the last iteration (this synchronises the stream).
+ * Device-side failures (survivor overflow, bounded-wait timeouts) are reported by this
+ * or the next synchronising call. */
+int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active);
+
+/* Kept list of one search r (0 <= r < R) of an instance, in key order (diagnostics,
+ * parity tests, checkpoints). Outputs hold K+1 entries; entries past *count are
+ * undefined. Any output pointer may be NULL. */
+int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double* E,
+                    uint8_t* used, uint64_t* stamp, int* count);
+
+/* Alg. 4 merge of the R lists of an instance followed by FP64 rescoring: the first
+ * min(k, count) states of the union of the R lists (each state at its first occurrence
+ * in search order), ordered by (E, search index, position in that search's list).
+ *   bits_out: k*W words; E_out: k energies recomputed from scratch in FP64 from J, h;
+ *   src_out (may be NULL): (r << 32) | position of each state's first occurrence;
+ *   n_out: number of states written. */
+int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out,
+                    uint64_t* src_out, int* n_out);
+
+/* Alg. 4 merge of every instance on the device, asynchronously, into a library buffer
+ * that the next qis_topk_states reads without merging again. */
+int qis_merge(qis_ctx* ctx);
+
+/* FP64 energies (Eq. (1)) of `count` caller states of an instance, computed on the GPU. */
+int qis_energies(qis_ctx* ctx, int instance_id, int count, const uint64_t* bits, double* E_out);
+
+/* Block until all device work of the context is done; reports deferred device errors. */
+int qis_synchronize(qis_ctx* ctx);
+
+/* Launch statistics: number of kernels this context has launched so far. */
+int qis_kernel_launches(qis_ctx* ctx, uint64_t* count);
+
+/* Candidates evaluated since the context was created: pair flips X_i X_j and single flips
+ * X_i of every parent (n(n-1)/2 and n per active search per iteration, Sec. III flip sets).
+ * Synchronises the stream. */
+int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles);
+
+/* The library's CUDA stream (a cudaStream_t), so callers can order their own work and
+ * CUDA events with respect to the library's kernels. */
+int qis_get_stream(qis_ctx* ctx, void** stream);
+
+/* Kernel timing with CUDA events. While enabled, each kernel launched by qis_iterate is
+ * bracketed by two events on the library stream. qis_profile_query synchronises, returns the
+ * summed device time (ms) and launch count of one kernel class since the last query, and
+ * resets that class. Classes: 0 parent pick, 1 local fields, 2 per-search bound,
+ * 3 candidate scan, 4 exact merge. */
+int qis_profile_enable(qis_ctx* ctx, int on);
+int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QIS_H */

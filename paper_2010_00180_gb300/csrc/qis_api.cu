@@ -1,0 +1,645 @@
+// qis_api.cu -- host side of libqis: the C ABI of include/qis.h, context and device memory,
+// instance preparation and the iteration driver.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "qis_common.cuh"
+
+using namespace qis;
+
+namespace {
+
+std::string g_create_error = "no error";
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct qis_ctx {
+  qis_config cfg{};
+  int K1 = 0, R = 0, mode = 0, NP = 0, Wmax = 0, cap = 0, B = 0, max_inst = 0, digit_planes = 0;
+  long long pool_mat = 0, pool_vec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<InstDesc> inst;
+  std::vector<int> inst_ready;  // init_states called
+  InstDesc* inst_d = nullptr;
+  DevPtrs P{};
+  std::vector<void*> allocs;
+  // owned (non-const) views of the instance pools
+  double* J64 = nullptr;
+  double* h64 = nullptr;
+  long long* Jq = nullptr;
+  float* J4 = nullptr;
+  __nv_bfloat16* D16 = nullptr;
+  long long* hq = nullptr;
+  uint64_t* zob = nullptr;
+  double* stats = nullptr;
+  int4* work = nullptr;
+  int n_work = 0;
+  bool work_dirty = true;
+  bool merged_fresh = false;
+  uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
+  double* scratch_E = nullptr;
+  int scratch_states = 0;
+  uint64_t launches = 0;
+  // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
+  size_t ev_used[8] = {0};
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(qis_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, QIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+#define LAUNCH(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    ++ctx->launches;                                                                          \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, QIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+template <typename T>
+int dalloc(qis_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, QIS_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(*p);
+  cudaMemset(*p, 0, count * sizeof(T));
+  return 0;
+}
+
+#define ALLOC(ptr, count)                     \
+  do {                                        \
+    int rc_ = dalloc(ctx, &(ptr), (count));   \
+    if (rc_) return rc_;                      \
+  } while (0)
+
+// Key of the library's initial-state stream for instance `id` (SplitMix64 chain).
+uint64_t state_key(uint64_t seed, int id) {
+  uint64_t k = splitmix64(seed, 0);
+  k = splitmix64(k ^ (uint64_t)id, 0);
+  k = splitmix64(k ^ 3ull, 0);
+  return k;
+}
+
+int check_status(qis_ctx* ctx) {
+  int st = 0;
+  CK(cudaMemcpy(&st, ctx->P.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & kStatCapacity)
+    return fail(ctx, QIS_ERR_CAPACITY, "a search produced more survivors than survivor_cap; raise survivor_cap");
+  if (st & kStatTimeout) return fail(ctx, QIS_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up");
+  if (st) return fail(ctx, QIS_ERR_STATE, "device reported an inconsistent search state");
+  return 0;
+}
+
+int sync_and_check(qis_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx);
+}
+
+// Record the start event of a timed launch of class `k` (no-op unless profiling).
+cudaError_t prof_begin(qis_ctx* ctx, int k) {
+  if (!ctx->profiling) return cudaSuccess;
+  auto& v = ctx->ev[k];
+  if (ctx->ev_used[k] == v.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    v.emplace_back(a, b);
+  }
+  return cudaEventRecord(v[ctx->ev_used[k]].first, ctx->stream);
+}
+
+cudaError_t prof_end(qis_ctx* ctx, int k) {
+  if (!ctx->profiling) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(ctx->ev[k][ctx->ev_used[k]].second, ctx->stream);
+  ++ctx->ev_used[k];
+  return e;
+}
+
+int build_work(qis_ctx* ctx) {
+  std::vector<int4> w;
+  for (int id = 0; id < (int)ctx->inst.size(); ++id) {
+    const int nb = (ctx->inst[id].n + kTile - 1) / kTile;
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj) w.push_back(make_int4(id, bi, bj, 0));
+  }
+  ctx->n_work = (int)w.size();
+  const size_t cap_items = (size_t)ctx->max_inst * ((ctx->NP / kTile) * (ctx->NP / kTile + 1) / 2);
+  if (w.size() > cap_items) return fail(ctx, QIS_ERR_STATE, "work list overflow");
+  if (!w.empty()) CK(cudaMemcpyAsync(ctx->work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->work_dirty = false;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qis_create(const qis_config* cfg, qis_ctx** out) {
+  qis_ctx* ctx = nullptr;
+  if (!cfg || !out) return fail(nullptr, QIS_ERR_INVALID_ARG, "cfg and out must not be NULL");
+  *out = nullptr;
+  if (cfg->K < 1 || cfg->K + 1 > 4096) return fail(nullptr, QIS_ERR_INVALID_ARG, "K must satisfy 1 <= K and K+1 <= 4096");
+  if (cfg->R < 1 || cfg->R > 65536) return fail(nullptr, QIS_ERR_INVALID_ARG, "R must be in [1, 65536]");
+  if (cfg->max_n < 2 || cfg->max_n > kMaxN) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_n must be in [2, 4096]");
+  if (cfg->max_instances < 1) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_instances must be >= 1");
+  if (cfg->precision != QIS_FP64 && cfg->precision != QIS_SPLIT_BF16 && cfg->precision != QIS_PM1_FP8)
+    return fail(nullptr, QIS_ERR_INVALID_ARG, "unknown precision mode");
+  int cap = cfg->survivor_cap ? cfg->survivor_cap : 4096;
+  if (cap < 4 * (cfg->K + 1) + 64 || cap > 16384)
+    return fail(nullptr, QIS_ERR_INVALID_ARG, "survivor_cap must be in [4(K+1)+64, 16384]");
+  {
+    cudaError_t e = cudaSetDevice(cfg->device);
+    if (e != cudaSuccess) return fail(nullptr, QIS_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  }
+  ctx = new qis_ctx();
+  ctx->cfg = *cfg;
+  ctx->K1 = cfg->K + 1;
+  ctx->R = cfg->R;
+  ctx->mode = cfg->precision;
+  ctx->NP = pad_of(cfg->max_n);
+  ctx->Wmax = words_of(cfg->max_n);
+  ctx->cap = cap;
+  ctx->max_inst = cfg->max_instances;
+  ctx->B = cfg->max_instances * cfg->R;
+  ctx->pool_mat = (long long)ctx->max_inst * ctx->NP * ctx->NP;
+  ctx->pool_vec = (long long)ctx->max_inst * ctx->NP;
+  ctx->digit_planes = (ctx->mode == QIS_FP64) ? 0 : (ctx->mode == QIS_PM1_FP8 ? 1 : kMaxDigits);
+  auto bail = [&](int rc) {
+    g_create_error = ctx->err;
+    qis_destroy(ctx);
+    return rc;
+  };
+  int rc = 0;
+  auto run = [&]() -> int {
+    CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    const size_t B = ctx->B, K1 = ctx->K1, W = ctx->Wmax, NP = ctx->NP;
+    InstDesc* id = nullptr;
+    ALLOC(id, ctx->max_inst);
+    ctx->inst_d = id;
+    ALLOC(ctx->J64, ctx->pool_mat);
+    ALLOC(ctx->h64, ctx->pool_vec);
+    if (ctx->mode != QIS_FP64) {
+      ALLOC(ctx->Jq, ctx->pool_mat);
+      ALLOC(ctx->J4, ctx->pool_mat);
+      ALLOC(ctx->D16, (size_t)ctx->digit_planes * ctx->pool_mat);
+      ALLOC(ctx->hq, ctx->pool_vec);
+    }
+    ALLOC(ctx->zob, kMaxN);
+    ALLOC(ctx->stats, kMaxN + 8);
+    ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2));
+    DevPtrs& P = ctx->P;
+    P.inst = ctx->inst_d;
+    P.n_inst = 0;
+    P.R = ctx->R;
+    P.K1 = ctx->K1;
+    P.Wmax = ctx->Wmax;
+    P.cap = ctx->cap;
+    P.mode = ctx->mode;
+    P.B = 0;
+    P.NP = ctx->NP;
+    P.J64 = ctx->J64;
+    P.Jq = ctx->Jq;
+    P.J4 = ctx->J4;
+    P.D16 = ctx->D16;
+    P.pool_mat = ctx->pool_mat;
+    P.h64 = ctx->h64;
+    P.hq = ctx->hq;
+    P.zob = ctx->zob;
+    ALLOC(P.lst_bits, B * K1 * W);
+    ALLOC(P.lst_E, B * K1);
+    ALLOC(P.lst_stamp, B * K1);
+    ALLOC(P.lst_hash, B * K1);
+    ALLOC(P.lst_used, B * K1);
+    ALLOC(P.lst_ord, B * K1);
+    ALLOC(P.lst_count, B);
+    ALLOC(P.par_bits, B * W);
+    ALLOC(P.par_E, B);
+    ALLOC(P.par_hash, B);
+    ALLOC(P.active, B);
+    ALLOC(P.iter_t, B);
+    if (ctx->mode != QIS_FP64) {
+      ALLOC(P.aq, B * NP);
+      ALLOC(P.a32, B * NP);
+      ALLOC(P.S16, B * NP);
+    } else {
+      ALLOC(P.a64, B * NP);
+    }
+    ALLOC(P.thr32, B);
+    ALLOC(P.thrE, B);
+    ALLOC(P.capE, B);
+    ALLOC(P.surv_cnt, B);
+    ALLOC(P.surv, B * (size_t)ctx->cap);
+    ALLOC(P.init_bits, B * W);
+    ALLOC(P.status, 4);
+    ALLOC(P.cand, 2);
+    ALLOC(P.mrg_ref, (size_t)ctx->max_inst * K1);
+    ALLOC(P.mrg_src, (size_t)ctx->max_inst * K1);
+    ALLOC(P.mrg_count, ctx->max_inst);
+    ctx->scratch_states = 4096;
+    ALLOC(ctx->scratch_bits, (size_t)ctx->scratch_states * W);
+    ALLOC(ctx->scratch_E, ctx->scratch_states);
+    // Zobrist keys of the sites (SplitMix64 stream with a fixed key)
+    std::vector<uint64_t> z(kMaxN);
+    for (int i = 0; i < kMaxN; ++i) z[i] = splitmix64(0x2F0A7B6C5D4E3F21ull, (uint64_t)i);
+    CK(cudaMemcpy(ctx->zob, z.data(), kMaxN * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    // kernel attributes for the large dynamic shared-memory users
+    CK(cudaDeviceSynchronize());
+    return 0;
+  };
+  rc = run();
+  if (rc) return bail(rc);
+  *out = ctx;
+  return 0;
+}
+
+void qis_destroy(qis_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->cfg.device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& v : ctx->ev)
+    for (auto& pr : v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* qis_last_error(const qis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!J || !h) return fail(ctx, QIS_ERR_INVALID_ARG, "J and h must not be NULL");
+  if (n < 2 || n > ctx->cfg.max_n) return fail(ctx, QIS_ERR_INVALID_ARG, "n must be in [2, max_n]");
+  if ((int)ctx->inst.size() >= ctx->max_inst) return fail(ctx, QIS_ERR_INVALID_ARG, "instance table full");
+  if (n < 63 && (uint64_t)ctx->cfg.K >= (1ull << n))
+    return fail(ctx, QIS_ERR_INVALID_ARG, "K must be below 2^n (Alg. 2 requires 1 <= K < 2^N)");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const int id = (int)ctx->inst.size();
+  InstDesc d{};
+  d.n = n;
+  d.n_pad = pad_of(n);
+  d.W = words_of(n);
+  d.first_search = id * ctx->R;
+  d.off_mat = (long long)id * ctx->NP * ctx->NP;
+  d.off_vec = (long long)id * ctx->NP;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->J64 + d.off_mat, 0, sizeof(double) * (size_t)d.n_pad * d.n_pad, s));
+  CK(cudaMemsetAsync(ctx->h64 + d.off_vec, 0, sizeof(double) * d.n_pad, s));
+  CK(cudaMemcpy2DAsync(ctx->J64 + d.off_mat, sizeof(double) * d.n_pad, J, sizeof(double) * n, sizeof(double) * n, n,
+                       cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->h64 + d.off_vec, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  LAUNCH(launch_validate(ctx->P, id, n, d.off_mat, d.off_vec, ctx->stats, s));
+  std::vector<double> st(n + 5);
+  CK(cudaMemcpyAsync(st.data(), ctx->stats, sizeof(double) * (n + 5), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int bad, maxfrac;
+  uint64_t mjb, mhb;
+  memcpy(&bad, &st[0], sizeof(int));
+  memcpy(&maxfrac, &st[1], sizeof(int));
+  memcpy(&mjb, &st[2], 8);
+  memcpy(&mhb, &st[3], 8);
+  double maxJ, maxh;
+  memcpy(&maxJ, &mjb, 8);
+  memcpy(&maxh, &mhb, 8);
+  if (bad & 1) return fail(ctx, QIS_ERR_INVALID_ARG, "J contains NaN or Inf");
+  if (bad & 8) return fail(ctx, QIS_ERR_INVALID_ARG, "h contains NaN or Inf");
+  if (bad & 2) return fail(ctx, QIS_ERR_INVALID_ARG, "J has a nonzero diagonal entry");
+  if (bad & 4) return fail(ctx, QIS_ERR_INVALID_ARG, "J is not symmetric");
+  d.q = -1;
+  d.digits = 0;
+  d.inv_scale = 1.0;
+  d.rounded = 0;
+  d.j4max = 0.f;
+  if (ctx->mode != QIS_FP64) {
+    double S = 0.0;
+    for (int i = 0; i < n; ++i) S += st[4 + i];
+    S += st[4 + n];
+    int qmax = 51;
+    if (S > 0) qmax = 51 - (int)floor(log2(S));
+    int q = maxfrac;
+    if (ctx->mode == QIS_PM1_FP8) {
+      if (maxfrac != 0 || maxJ > 15.0)
+        return fail(ctx, QIS_ERR_INVALID_ARG, "QIS_PM1_FP8 needs integer J with |J_ij| <= 15 and integer h");
+      if (qmax < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "energies exceed 2^52");
+      q = 0;
+    } else if (q > qmax) {
+      q = qmax;
+      d.rounded = 1;
+    }
+    if (q < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "couplings too large for exact 64-bit energies");
+    const double maxJq = ldexp(maxJ, q);
+    int digits = 1;
+    while (digits < kMaxDigits && ldexp(1.0, 8 * digits - 1) <= maxJq + 0.5) ++digits;
+    if (ldexp(1.0, 8 * digits - 1) <= maxJq + 0.5) return fail(ctx, QIS_ERR_INVALID_ARG, "coupling range too wide");
+    if (ctx->mode == QIS_PM1_FP8) digits = 1;
+    d.q = q;
+    d.digits = digits;
+    d.inv_scale = ldexp(1.0, -q);
+    d.j4max = (float)(4.0 * ldexp(rint(maxJq), -q)) * (1.0f + 1e-6f);
+  }
+  CK(cudaMemcpyAsync(ctx->inst_d + id, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+  if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->inst.push_back(d);
+  ctx->inst_ready.push_back(0);
+  ctx->P.n_inst = (int)ctx->inst.size();
+  ctx->P.B = ctx->P.n_inst * ctx->R;
+  ctx->work_dirty = true;
+  ctx->merged_fresh = false;
+  if (instance_id) *instance_id = id;
+  return 0;
+}
+
+int qis_clear_instances(qis_ctx* ctx) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->inst.clear();
+  ctx->inst_ready.clear();
+  ctx->P.n_inst = 0;
+  ctx->P.B = 0;
+  ctx->work_dirty = true;
+  ctx->merged_fresh = false;
+  return 0;
+}
+
+int qis_instance_info(qis_ctx* ctx, int instance_id, int* q, int* digits, int* rounded) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  const InstDesc& d = ctx->inst[instance_id];
+  if (q) *q = d.q;
+  if (digits) *digits = d.digits;
+  if (rounded) *rounded = d.rounded;
+  return 0;
+}
+
+int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const InstDesc& d = ctx->inst[instance_id];
+  const int R = ctx->R, W = d.W, Wm = ctx->Wmax;
+  std::vector<uint64_t> h((size_t)R * Wm, 0ull);
+  const uint64_t top = (d.n % 64) ? ((1ull << (d.n % 64)) - 1) : ~0ull;
+  if (bits) {
+    for (int r = 0; r < R; ++r)
+      for (int w = 0; w < W; ++w) {
+        const uint64_t v = bits[(size_t)r * W + w];
+        if (w == W - 1 && (v & ~top)) return fail(ctx, QIS_ERR_INVALID_ARG, "state bits above n must be zero");
+        h[(size_t)r * Wm + w] = v;
+      }
+  } else {
+    const uint64_t key = state_key(ctx->cfg.seed, instance_id);
+    for (int r = 0; r < R; ++r)
+      for (int i = 0; i < d.n; ++i)
+        if (splitmix64(key, (uint64_t)r * d.n + i) >> 63) h[(size_t)r * Wm + (i >> 6)] |= 1ull << (i & 63);
+  }
+  CK(cudaMemcpyAsync(ctx->P.init_bits + (size_t)d.first_search * Wm, h.data(), h.size() * sizeof(uint64_t),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  LAUNCH(launch_init_search(ctx->P, d.first_search, R, ctx->stream));
+  ctx->inst_ready[instance_id] = 1;
+  ctx->merged_fresh = false;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int qis_reset(qis_ctx* ctx) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  for (size_t i = 0; i < ctx->inst.size(); ++i)
+    if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
+  CK(cudaMemsetAsync(ctx->P.status, 0, sizeof(int), ctx->stream));
+  LAUNCH(launch_init_search(ctx->P, 0, ctx->P.B, ctx->stream));
+  ctx->merged_fresh = false;
+  return 0;
+}
+
+int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_iters < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "n_iters must be >= 0");
+  if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
+  for (size_t i = 0; i < ctx->inst.size(); ++i)
+    if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (ctx->work_dirty) {
+    int rc = build_work(ctx);
+    if (rc) return rc;
+  }
+  cudaStream_t s = ctx->stream;
+  const DevPtrs& P = ctx->P;
+  for (int it = 0; it < n_iters; ++it) {
+    CK(prof_begin(ctx, 0));
+    LAUNCH(launch_pick(P, s));
+    CK(prof_end(ctx, 0));
+    CK(prof_begin(ctx, 1));
+    if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
+    else LAUNCH(launch_fields_exact(P, s));
+    CK(prof_end(ctx, 1));
+    CK(prof_begin(ctx, 2));
+    LAUNCH(launch_bound(P, s));
+    CK(prof_end(ctx, 2));
+    CK(prof_begin(ctx, 3));
+    LAUNCH(launch_scan(P, ctx->work, ctx->n_work, s));
+    CK(prof_end(ctx, 3));
+    CK(prof_begin(ctx, 4));
+    LAUNCH(launch_merge(P, s));
+    CK(prof_end(ctx, 4));
+  }
+  ctx->merged_fresh = false;
+  if (n_active) {
+    int rc = sync_and_check(ctx);
+    if (rc) return rc;
+    std::vector<int> act(P.B);
+    CK(cudaMemcpy(act.data(), P.active, sizeof(int) * P.B, cudaMemcpyDeviceToHost));
+    // a search with every kept state used is inactive from the next pick on; count unused
+    std::vector<int> cnt(P.B);
+    CK(cudaMemcpy(cnt.data(), P.lst_count, sizeof(int) * P.B, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> used((size_t)P.B * P.K1);
+    CK(cudaMemcpy(used.data(), P.lst_used, used.size(), cudaMemcpyDeviceToHost));
+    std::vector<int> ord((size_t)P.B * P.K1);
+    CK(cudaMemcpy(ord.data(), P.lst_ord, ord.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    int na = 0;
+    for (int b = 0; b < P.B; ++b) {
+      if (!act[b]) continue;
+      bool any = false;
+      for (int r = 0; r < cnt[b] && !any; ++r) any = !used[(size_t)b * P.K1 + ord[(size_t)b * P.K1 + r]];
+      na += any;
+    }
+    *n_active = na;
+  }
+  return 0;
+}
+
+int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double* E, uint8_t* used,
+                    uint64_t* stamp, int* count) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  if (r < 0 || r >= ctx->R) return fail(ctx, QIS_ERR_INVALID_ARG, "bad search index");
+  int rc = sync_and_check(ctx);
+  if (rc) return rc;
+  const InstDesc& d = ctx->inst[instance_id];
+  const int K1 = ctx->K1, Wm = ctx->Wmax;
+  const size_t b = (size_t)d.first_search + r;
+  int cnt = 0;
+  CK(cudaMemcpy(&cnt, ctx->P.lst_count + b, sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<int> ord(K1);
+  std::vector<double> e(K1);
+  std::vector<uint64_t> st(K1), bb((size_t)K1 * Wm);
+  std::vector<uint8_t> u(K1);
+  CK(cudaMemcpy(ord.data(), ctx->P.lst_ord + b * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(e.data(), ctx->P.lst_E + b * K1, K1 * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st.data(), ctx->P.lst_stamp + b * K1, K1 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(u.data(), ctx->P.lst_used + b * K1, K1, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bb.data(), ctx->P.lst_bits + b * K1 * Wm, bb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < cnt; ++k) {
+    const int slot = ord[k];
+    if (bits) memcpy(bits + (size_t)k * d.W, &bb[(size_t)slot * Wm], d.W * sizeof(uint64_t));
+    if (E) E[k] = e[slot];
+    if (used) used[k] = u[slot];
+    if (stamp) stamp[k] = st[slot];
+  }
+  if (count) *count = cnt;
+  return 0;
+}
+
+int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out,
+                    int* n_out) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  if (k < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "k must be >= 0");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = ctx->stream;
+  if (!ctx->merged_fresh) {
+    LAUNCH(launch_final_merge(ctx->P, s));
+    ctx->merged_fresh = true;
+  }
+  int rc = sync_and_check(ctx);
+  if (rc) return rc;
+  const InstDesc& d = ctx->inst[instance_id];
+  int cnt = 0;
+  CK(cudaMemcpy(&cnt, ctx->P.mrg_count + instance_id, sizeof(int), cudaMemcpyDeviceToHost));
+  const int m = k < cnt ? k : cnt;
+  for (int off = 0; off < m; off += ctx->scratch_states) {
+    const int c = (m - off < ctx->scratch_states) ? m - off : ctx->scratch_states;
+    // gather rows off..off+c of the merged list
+    DevPtrs Q = ctx->P;
+    Q.mrg_ref = ctx->P.mrg_ref + off;   // shift the view so row 0 is entry `off`
+    LAUNCH(launch_gather_merged(Q, instance_id, d, c, ctx->scratch_bits, s));
+    LAUNCH(launch_rescore(ctx->P, d, ctx->scratch_bits, c, d.W, ctx->scratch_E, s));
+    if (bits_out) CK(cudaMemcpyAsync(bits_out + (size_t)off * d.W, ctx->scratch_bits, sizeof(uint64_t) * c * d.W,
+                                     cudaMemcpyDeviceToHost, s));
+    if (E_out) CK(cudaMemcpyAsync(E_out + off, ctx->scratch_E, sizeof(double) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (src_out && m > 0)
+    CK(cudaMemcpy(src_out, ctx->P.mrg_src + (size_t)instance_id * ctx->K1, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = m;
+  return 0;
+}
+
+int qis_merge(qis_ctx* ctx) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
+  CK(cudaSetDevice(ctx->cfg.device));
+  LAUNCH(launch_final_merge(ctx->P, ctx->stream));
+  ctx->merged_fresh = true;
+  return 0;
+}
+
+int qis_energies(qis_ctx* ctx, int instance_id, int count, const uint64_t* bits, double* E_out) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  if (count < 0 || (count > 0 && (!bits || !E_out))) return fail(ctx, QIS_ERR_INVALID_ARG, "bad buffers");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const InstDesc& d = ctx->inst[instance_id];
+  cudaStream_t s = ctx->stream;
+  for (int off = 0; off < count; off += ctx->scratch_states) {
+    const int c = (count - off < ctx->scratch_states) ? count - off : ctx->scratch_states;
+    CK(cudaMemcpyAsync(ctx->scratch_bits, bits + (size_t)off * d.W, sizeof(uint64_t) * c * d.W, cudaMemcpyHostToDevice, s));
+    LAUNCH(launch_rescore(ctx->P, d, ctx->scratch_bits, c, d.W, ctx->scratch_E, s));
+    CK(cudaMemcpyAsync(E_out + off, ctx->scratch_E, sizeof(double) * c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return 0;
+}
+
+int qis_synchronize(qis_ctx* ctx) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  return sync_and_check(ctx);
+}
+
+int qis_kernel_launches(qis_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  *count = ctx->launches;
+  return 0;
+}
+
+int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long c[2];
+  CK(cudaMemcpy(c, ctx->P.cand, sizeof(c), cudaMemcpyDeviceToHost));
+  if (pairs) *pairs = c[0];
+  if (singles) *singles = c[1];
+  return 0;
+}
+
+int qis_get_stream(qis_ctx* ctx, void** stream) {
+  if (!ctx || !stream) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  *stream = (void*)ctx->stream;
+  return 0;
+}
+
+int qis_profile_enable(qis_ctx* ctx, int on) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->profiling = on != 0;
+  return 0;
+}
+
+int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (kernel_class < 0 || kernel_class >= 5) return fail(ctx, QIS_ERR_INVALID_ARG, "kernel class must be in [0, 5)");
+  CK(cudaStreamSynchronize(ctx->stream));
+  double sum = 0.0;
+  auto& v = ctx->ev[kernel_class];
+  for (size_t k = 0; k < ctx->ev_used[kernel_class]; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, v[k].first, v[k].second));
+    sum += ms;
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = ctx->ev_used[kernel_class];
+  ctx->ev_used[kernel_class] = 0;
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// qis_common.cuh -- types and helpers shared by the CUDA translation units of libqis.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/qis.h"
+
+namespace qis {
+
+constexpr int kTile = 64;        // scan tile edge (sites)
+constexpr int kPad = 128;        // n is padded to a multiple of this (tensor-core M tile)
+constexpr int kMaxDigits = 7;    // 8-bit signed digits of the fixed-point couplings
+constexpr int kMaxN = 4096;
+
+// Device error flags (bit mask in ctx status word).
+constexpr int kStatCapacity = 1;
+constexpr int kStatTimeout = 2;
+constexpr int kStatBadParent = 4;
+
+// Per-instance descriptor (device and host copies).
+struct InstDesc {
+  int n;            // spins
+  int n_pad;        // n rounded up to kPad
+  int W;            // words per state
+  int q;            // fixed-point exponent: Jq = J * 2^q  (-1 in FP64 mode)
+  int digits;       // number of 8-bit digits of Jq
+  int first_search; // global index of search r = 0 of this instance
+  long long off_mat;  // element offset of this instance's n_pad x n_pad matrices
+  long long off_vec;  // element offset of this instance's n_pad vectors
+  double inv_scale;   // 2^-q
+  float j4max;        // max |fl32(4 J_ij)|
+  int rounded;        // input was rounded onto the grid
+};
+
+// Device pointers of one context (passed to kernels by value).
+struct DevPtrs {
+  const InstDesc* inst;
+  int n_inst, R, K1, Wmax, cap, mode, B;
+  int NP;                 // row stride of per-search site arrays (max n_pad)
+  // instance pools
+  const double* J64;      // [off_mat + i*n_pad + j]
+  const long long* Jq;    // fixed-point couplings
+  const float* J4;        // fl32(4 * J)
+  const __nv_bfloat16* D16; // digits [d][off_mat + i*n_pad + k] (digit-major pools of size pool_mat)
+  long long pool_mat;     // elements of one digit plane
+  const double* h64;      // [off_vec + i]
+  const long long* hq;
+  const uint64_t* zob;    // Zobrist keys [kMaxN]
+  // per-search state, search b
+  uint64_t* lst_bits;     // [b][K1][Wmax]
+  double* lst_E;          // [b][K1]
+  uint64_t* lst_stamp;    // [b][K1]
+  uint64_t* lst_hash;     // [b][K1]
+  uint8_t* lst_used;      // [b][K1]
+  int* lst_ord;           // [b][K1] slot of rank r
+  int* lst_count;         // [b]
+  uint64_t* par_bits;     // [b][Wmax]
+  double* par_E;          // [b]
+  uint64_t* par_hash;     // [b]
+  int* active;            // [b]
+  int* iter_t;            // [b] iterations done
+  long long* aq;          // [b][n_pad] exact a_i * 2^q (split modes)
+  float* a32;             // [b][n_pad] fl32(a_i)
+  double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
+  float* thr32;           // [b] scan threshold on dE (split modes)
+  double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
+  double* capE;           // [b] ... and <= capE[b]
+  int* surv_cnt;          // [b]
+  uint32_t* surv;         // [b][cap]
+  __nv_bfloat16* S16;     // [b][n_pad] +-1 spins of the parent (0 past n)
+  uint64_t* init_bits;    // [b][Wmax]
+  int* status;            // [0] error bits
+  unsigned long long* cand;  // [0] pair candidates evaluated, [1] single candidates
+  // final merge (Alg. 4) per instance
+  int* mrg_ref;           // [inst][K1] search*K1 + slot
+  uint64_t* mrg_src;      // [inst][K1]
+  int* mrg_count;         // [inst]
+};
+
+__host__ __device__ inline int words_of(int n) { return (n + 63) >> 6; }
+__host__ __device__ inline int pad_of(int n) { return (n + kPad - 1) / kPad * kPad; }
+
+// candidate index <-> sites: c < n single i = c; c >= n pair (i, j), i < j, lexicographic
+__host__ __device__ inline uint32_t pair_index(int n, int i, int j) {
+  return (uint32_t)n + (uint32_t)((long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1));
+}
+__device__ inline void decode_candidate(int n, uint32_t c, int& i, int& j) {
+  if (c < (uint32_t)n) { i = (int)c; j = -1; return; }
+  long long r = (long long)c - n;
+  // row i holds n-1-i pairs; start(i) = i*n - i*(i+1)/2
+  double nn = 2.0 * n - 1.0;
+  int ii = (int)((nn - sqrt(nn * nn - 8.0 * (double)r)) * 0.5);
+  if (ii < 0) ii = 0;
+  if (ii > n - 2) ii = n - 2;
+  while (ii > 0 && (long long)ii * n - (long long)ii * (ii + 1) / 2 > r) --ii;
+  while (ii < n - 2 && (long long)(ii + 1) * n - (long long)(ii + 1) * (ii + 2) / 2 <= r) ++ii;
+  i = ii;
+  j = (int)(r - ((long long)ii * n - (long long)ii * (ii + 1) / 2)) + ii + 1;
+}
+
+__device__ inline int sigma_of(const uint64_t* bits, int i) { return (int)((bits[i >> 6] >> (i & 63)) & 1ull); }
+
+// SplitMix64 (Steele, Lea and Flood 2014): value number c of the stream started at key.
+__host__ __device__ inline uint64_t splitmix64(uint64_t key, uint64_t c) {
+  uint64_t z = key + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// orderable 64-bit key of a double (ascending doubles -> ascending unsigned)
+__device__ inline unsigned long long dkey(double x) {
+  x = x + 0.0;  // -0.0 -> +0.0
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+// Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
+cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
+                            double* stats, cudaStream_t s);
+cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, __nv_bfloat16* D16, long long* Jq,
+                            float* J4, long long* hq, cudaStream_t s);
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s);
+cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_scan(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s);
+cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_final_merge(const DevPtrs& P, cudaStream_t s);
+size_t merge_smem(int K1, int cap);
+size_t final_merge_smem(int K1);
+cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
+                           double* E_out, cudaStream_t s);
+cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, int k, uint64_t* bits_out,
+                                 cudaStream_t s);
+
+}  // namespace qis

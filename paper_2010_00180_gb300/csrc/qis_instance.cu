@@ -1,0 +1,222 @@
+// qis_instance.cu -- per-instance preparation, search initialisation and FP64 rescoring.
+//
+// Instance data (H0 of Eq. (1)) lives in padded n_pad x n_pad planes:
+//   J64  FP64 couplings as given (zero padding)
+//   Jq   fixed-point couplings Jq = J * 2^q (int64, exact on the 2^-q grid)
+//   J4   fl32(4 * Jq * 2^-q): the candidate filter's coupling term
+//   D16  Jq written in balanced base-256 digits, Jq = sum_d 256^d D_d, D_d in [-128, 127],
+//        one BF16 plane per digit (every digit is an exact BF16 integer)
+#include "qis_common.cuh"
+
+namespace qis {
+
+// ---------------------------------------------------------------- validation
+// stats layout (doubles): [0] bad flags (as bits of an int), [1] max frac bits, [2] max|J| bits,
+// [3] max|h| bits, [4 .. 4+n) row sums sum_{j>i} |J_ij| in j order, [4+n] sum_i |h_i|.
+__device__ inline int frac_bits(double x) {
+  if (x == 0.0) return 0;
+  int ex;
+  double f = frexp(fabs(x), &ex);                 // |x| = f 2^ex, f in [0.5, 1)
+  unsigned long long M = (unsigned long long)ldexp(f, 53);
+  int tz = __ffsll((long long)M) - 1;
+  int fb = 53 - tz - ex;
+  return fb > 0 ? fb : 0;
+}
+
+__global__ void k_validate(const double* J64, const double* h64, int n, int n_pad, double* stats) {
+  int* bad = reinterpret_cast<int*>(stats);
+  int* maxfrac = reinterpret_cast<int*>(stats + 1);
+  unsigned long long* maxJ = reinterpret_cast<unsigned long long*>(stats + 2);
+  unsigned long long* maxh = reinterpret_cast<unsigned long long*>(stats + 3);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double* row = J64 + (long long)i * n_pad;
+    double rs = 0.0;
+    int fb = 0, b = 0;
+    double mj = 0.0;
+    for (int j = 0; j < n; ++j) {
+      double x = row[j];
+      if (!isfinite(x)) b |= 1;
+      if (j == i) {
+        if (x != 0.0) b |= 2;
+        continue;
+      }
+      if (__double_as_longlong(x) != __double_as_longlong(J64[(long long)j * n_pad + i])) b |= 4;
+      fb = max(fb, frac_bits(x));
+      mj = fmax(mj, fabs(x));
+      if (j > i) rs += fabs(x);
+    }
+    double hv = h64[i];
+    if (!isfinite(hv)) b |= 8;
+    fb = max(fb, frac_bits(hv));
+    stats[4 + i] = rs;
+    if (b) atomicOr(bad, b);
+    atomicMax(maxfrac, fb);
+    atomicMax(maxJ, (unsigned long long)__double_as_longlong(mj));
+    atomicMax(maxh, (unsigned long long)__double_as_longlong(fabs(hv)));
+  }
+  if (i == 0) {
+    double sh = 0.0;
+    for (int k = 0; k < n; ++k) sh += fabs(h64[k]);
+    stats[4 + n] = sh;
+  }
+}
+
+cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
+                            double* stats, cudaStream_t s) {
+  (void)inst;
+  cudaMemsetAsync(stats, 0, 4 * sizeof(double), s);
+  const int np = pad_of(n);
+  k_validate<<<(n + 127) / 128, 128, 0, s>>>(P.J64 + off_mat, P.h64 + off_vec, n, np, stats);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fixed point + digits
+__global__ void k_quantize(const double* J64, const double* h64, int n, int n_pad, int q, int digits,
+                           long long plane, __nv_bfloat16* D16, long long* Jq, float* J4, long long* hq) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)n_pad * n_pad;
+  if (e < tot) {
+    const int i = (int)(e / n_pad), j = (int)(e % n_pad);
+    long long v = 0;
+    if (i < n && j < n) v = __double2ll_rn(ldexp(J64[e], q));
+    Jq[e] = v;
+    J4[e] = (float)(4.0 * ldexp((double)v, -q));
+    long long x = v;
+    for (int d = 0; d < digits; ++d) {
+      long long r = x & 255;                  // x mod 256 in [0, 255]
+      if (r >= 128) r -= 256;                 // balanced digit in [-128, 127]
+      D16[d * plane + e] = __float2bfloat16_rn((float)r);
+      x = (x - r) >> 8;                       // exact
+    }
+  }
+  if (e < n_pad) hq[e] = (e < n) ? __double2ll_rn(ldexp(h64[e], q)) : 0;
+}
+
+cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, __nv_bfloat16* D16, long long* Jq,
+                            float* J4, long long* hq, cudaStream_t s) {
+  const long long tot = (long long)d.n_pad * d.n_pad;
+  k_quantize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad,
+                                                          d.q, d.digits, P.pool_mat, D16 + d.off_mat,
+                                                          Jq + d.off_mat, J4 + d.off_mat, hq + d.off_vec);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- search initialisation
+// Alg. 3 initial list: [psi0, K placeholders], E(psi0) from Eq. (1), nothing used.
+// Split modes: E0 = (sum_{i<j} Jq_ij s_i s_j + sum_i hq_i s_i) 2^-q in exact int64.
+// FP64 mode: one thread adds the pair terms i-major, j ascending, then the field terms.
+__global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0) {
+  const int b = b0 + blockIdx.x;
+  const InstDesc d = P.inst[b / P.R];
+  const int n = d.n, np = d.n_pad, W = d.W;
+  __shared__ uint64_t bits[kMaxN / 64];
+  __shared__ long long red[256];
+  for (int w = threadIdx.x; w < W; w += blockDim.x) bits[w] = P.init_bits[(long long)b * P.Wmax + w];
+  __syncthreads();
+  double E0 = 0.0;
+  if (P.mode != QIS_FP64) {
+    long long acc = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const long long* row = P.Jq + d.off_mat + (long long)i * np;
+      const int si = sigma_of(bits, i);
+      long long r = 0;
+      for (int j = i + 1; j < n; ++j) r += (si ^ sigma_of(bits, j)) ? -row[j] : row[j];
+      long long hv = P.hq[d.off_vec + i];
+      acc += r + (si ? -hv : hv);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    E0 = ldexp((double)red[0], -d.q);
+  } else if (threadIdx.x == 0) {
+    double Pp = 0.0, F = 0.0;
+    const double* J = P.J64 + d.off_mat;
+    for (int i = 0; i < n; ++i) {
+      const double si = sigma_of(bits, i) ? -1.0 : 1.0;
+      for (int j = i + 1; j < n; ++j) {
+        const double sj = sigma_of(bits, j) ? -1.0 : 1.0;
+        Pp = __dadd_rn(Pp, J[(long long)i * np + j] * si * sj);
+      }
+    }
+    for (int i = 0; i < n; ++i) F = __dadd_rn(F, P.h64[d.off_vec + i] * (sigma_of(bits, i) ? -1.0 : 1.0));
+    E0 = __dadd_rn(Pp, F);
+  }
+  if (threadIdx.x == 0) {
+    uint64_t hsh = 0;
+    for (int i = 0; i < n; ++i)
+      if (sigma_of(bits, i)) hsh ^= P.zob[i];
+    const long long base = (long long)b * P.K1;
+    for (int w = 0; w < W; ++w) P.lst_bits[base * P.Wmax + w] = bits[w];
+    P.lst_E[base] = E0;
+    P.lst_stamp[base] = 0;
+    P.lst_hash[base] = hsh;
+    for (int k = 0; k < P.K1; ++k) {
+      P.lst_used[base + k] = 0;
+      P.lst_ord[base + k] = (k == 0) ? 0 : -1;
+    }
+    P.lst_count[b] = 1;
+    P.active[b] = 1;
+    P.iter_t[b] = 0;
+    P.surv_cnt[b] = 0;
+  }
+}
+
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s) {
+  if (nb <= 0) return cudaSuccess;
+  k_init_search<<<nb, 256, 0, s>>>(P, b0);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- FP64 rescoring
+// E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i from scratch in FP64 (one block per state;
+// thread t owns rows t, t+256, ...; fixed reduction tree, so the result is reproducible).
+__global__ void __launch_bounds__(256) k_rescore(const double* J64, const double* h64, int n, int n_pad,
+                                                 const uint64_t* states, int Wn, double* E_out) {
+  const uint64_t* bits = states + (long long)blockIdx.x * Wn;
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double* row = J64 + (long long)i * n_pad;
+    double r = 0.0;
+    for (int j = i + 1; j < n; ++j) r += sigma_of(bits, j) ? -row[j] : row[j];
+    r += h64[i];
+    acc += sigma_of(bits, i) ? -r : r;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) E_out[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
+                           double* E_out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_rescore<<<count, 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, bits, Wn, E_out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- merged-list gather
+__global__ void k_gather_merged(DevPtrs P, int inst, int k, int Wn, uint64_t* out) {
+  const int r = blockIdx.x;
+  if (r >= k) return;
+  const int ref = P.mrg_ref[inst * P.K1 + r];
+  const int b = ref / P.K1, slot = ref % P.K1;
+  for (int w = threadIdx.x; w < Wn; w += blockDim.x)
+    out[(long long)r * Wn + w] = P.lst_bits[((long long)b * P.K1 + slot) * P.Wmax + w];
+}
+
+cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, int k, uint64_t* bits_out,
+                                 cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_gather_merged<<<k, 32, 0, s>>>(P, inst, k, d.W, bits_out);
+  return cudaGetLastError();
+}
+
+}  // namespace qis

@@ -1,0 +1,218 @@
+"""Python binding of libqis.so (the C ABI declared in include/qis.h).
+
+Argument marshalling only: every step of the search runs in the library's CUDA kernels.
+Importing this module never builds anything; ``load()`` raises if libqis.so is missing
+(build it with ``paper_2010_00180_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqis.so")
+
+QIS_FP64, QIS_SPLIT_BF16, QIS_PM1_FP8 = 0, 1, 2
+PRECISIONS = {"fp64": QIS_FP64, "split_bf16": QIS_SPLIT_BF16, "pm1_fp8": QIS_PM1_FP8}
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "CAPACITY", -6: "STATE"}
+
+# the entry points of include/qis.h
+SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_clear_instances",
+           "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
+           "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
+           "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query"]
+KERNEL_CLASSES = ["pick", "fields", "bound", "scan", "merge"]
+
+
+class QISError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Config(C.Structure):
+    _fields_ = [("K", C.c_int), ("R", C.c_int), ("precision", C.c_int), ("max_n", C.c_int),
+                ("max_instances", C.c_int), ("survivor_cap", C.c_int), ("device", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+_lib = None
+
+
+def load():
+    """dlopen libqis.so (no GPU needed for loading) and declare the signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2010_00180_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, I, U64 = C.c_void_p, C.c_int, C.c_uint64
+    sig = {
+        "qis_create": (I, [C.POINTER(Config), C.POINTER(P)]),
+        "qis_destroy": (None, [P]),
+        "qis_last_error": (C.c_char_p, [P]),
+        "qis_create_instance": (I, [P, I, P, P, C.POINTER(I)]),
+        "qis_clear_instances": (I, [P]),
+        "qis_instance_info": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+        "qis_init_states": (I, [P, I, P]),
+        "qis_reset": (I, [P]),
+        "qis_iterate": (I, [P, I, C.POINTER(I)]),
+        "qis_search_list": (I, [P, I, I, P, P, P, P, C.POINTER(I)]),
+        "qis_topk_states": (I, [P, I, I, P, P, P, C.POINTER(I)]),
+        "qis_merge": (I, [P]),
+        "qis_energies": (I, [P, I, I, P, P]),
+        "qis_synchronize": (I, [P]),
+        "qis_kernel_launches": (I, [P, C.POINTER(U64)]),
+        "qis_candidate_count": (I, [P, C.POINTER(U64), C.POINTER(U64)]),
+        "qis_get_stream": (I, [P, C.POINTER(P)]),
+        "qis_profile_enable": (I, [P, I]),
+        "qis_profile_query": (I, [P, I, C.POINTER(C.c_double), C.POINTER(U64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def words(n: int) -> int:
+    return (n + 63) // 64
+
+
+class Context:
+    """One qis_ctx: instances, R searches per instance, kept lists of K+1 states."""
+
+    def __init__(self, K: int, R: int, precision="split_bf16", max_n: int = 1024, max_instances: int = 1,
+                 survivor_cap: int = 0, device: int = 0, seed: int = 0):
+        self.lib = load()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.cfg = Config(K, R, prec, max_n, max_instances, survivor_cap, device, seed & 0xFFFFFFFFFFFFFFFF)
+        self.K, self.R = K, R
+        self.h = C.c_void_p()
+        rc = self.lib.qis_create(C.byref(self.cfg), C.byref(self.h))
+        if rc != 0:
+            raise QISError(rc, self.lib.qis_last_error(None).decode())
+        self.n = {}
+
+    # --------------------------------------------------------------- helpers
+    def _check(self, rc):
+        if rc != 0:
+            raise QISError(rc, self.lib.qis_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.lib.qis_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- API
+    def create_instance(self, J, h) -> int:
+        J = np.ascontiguousarray(J, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        n = h.shape[0]
+        assert J.shape == (n, n)
+        iid = C.c_int(-1)
+        self._check(self.lib.qis_create_instance(self.h, n, _ptr(J), _ptr(h), C.byref(iid)))
+        self.n[iid.value] = n
+        return iid.value
+
+    def clear_instances(self):
+        self._check(self.lib.qis_clear_instances(self.h))
+        self.n = {}
+
+    def instance_info(self, iid: int):
+        q, d, r = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.qis_instance_info(self.h, iid, C.byref(q), C.byref(d), C.byref(r)))
+        return q.value, d.value, bool(r.value)
+
+    def init_states(self, iid: int, bits=None):
+        if bits is not None:
+            bits = np.ascontiguousarray(bits, dtype=np.uint64)
+            assert bits.shape == (self.R, words(self.n[iid]))
+        self._check(self.lib.qis_init_states(self.h, iid, _ptr(bits)))
+
+    def reset(self):
+        self._check(self.lib.qis_reset(self.h))
+
+    def iterate(self, n_iters: int, count_active: bool = False):
+        na = C.c_int(-1)
+        self._check(self.lib.qis_iterate(self.h, n_iters, C.byref(na) if count_active else None))
+        return na.value if count_active else None
+
+    def search_list(self, iid: int, r: int) -> dict:
+        n, K1 = self.n[iid], self.K + 1
+        bits = np.zeros((K1, words(n)), np.uint64)
+        E = np.zeros(K1)
+        used = np.zeros(K1, np.uint8)
+        stamp = np.zeros(K1, np.uint64)
+        cnt = C.c_int()
+        self._check(self.lib.qis_search_list(self.h, iid, r, _ptr(bits), _ptr(E), _ptr(used), _ptr(stamp),
+                                             C.byref(cnt)))
+        c = cnt.value
+        return dict(bits=bits[:c], E=E[:c], used=used[:c], stamp=stamp[:c], count=c)
+
+    def topk_states(self, iid: int, k: int) -> dict:
+        n = self.n[iid]
+        bits = np.zeros((max(k, 1), words(n)), np.uint64)
+        E = np.zeros(max(k, 1))
+        src = np.zeros(max(k, 1), np.uint64)
+        cnt = C.c_int()
+        self._check(self.lib.qis_topk_states(self.h, iid, k, _ptr(bits), _ptr(E), _ptr(src), C.byref(cnt)))
+        c = cnt.value
+        return dict(bits=bits[:c], E=E[:c], src=src[:c], count=c)
+
+    def merge(self):
+        self._check(self.lib.qis_merge(self.h))
+
+    def energies(self, iid: int, bits) -> np.ndarray:
+        bits = np.ascontiguousarray(np.atleast_2d(bits), dtype=np.uint64)
+        E = np.zeros(bits.shape[0])
+        self._check(self.lib.qis_energies(self.h, iid, bits.shape[0], _ptr(bits), _ptr(E)))
+        return E
+
+    def synchronize(self):
+        self._check(self.lib.qis_synchronize(self.h))
+
+    def kernel_launches(self) -> int:
+        v = C.c_uint64()
+        self._check(self.lib.qis_kernel_launches(self.h, C.byref(v)))
+        return v.value
+
+    def candidate_count(self):
+        p, s = C.c_uint64(), C.c_uint64()
+        self._check(self.lib.qis_candidate_count(self.h, C.byref(p), C.byref(s)))
+        return p.value, s.value
+
+    def stream_handle(self) -> int:
+        v = C.c_void_p()
+        self._check(self.lib.qis_get_stream(self.h, C.byref(v)))
+        return v.value or 0
+
+    def profile(self, on: bool):
+        self._check(self.lib.qis_profile_enable(self.h, 1 if on else 0))
+
+    def profile_query(self, kernel_class) -> tuple:
+        k = KERNEL_CLASSES.index(kernel_class) if isinstance(kernel_class, str) else int(kernel_class)
+        ms, n = C.c_double(), C.c_uint64()
+        self._check(self.lib.qis_profile_query(self.h, k, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
