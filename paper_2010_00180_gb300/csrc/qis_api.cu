@@ -1,9 +1,11 @@
 // qis_api.cu -- host side of libqis: the C ABI of include/qis.h, context and device memory,
 // instance preparation and the iteration driver.
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -37,12 +39,17 @@ struct qis_ctx {
   double* h64 = nullptr;
   long long* Jq = nullptr;
   float* J4 = nullptr;
-  __nv_bfloat16* D16 = nullptr;
+  __half* D16 = nullptr;
+  int digits_used = 1;     // most digits of any instance (sizes the tensor-core pipeline)
+  bool fields_simt = false;  // QIS_FIELDS_SIMT=1: exact int64 SIMT fields instead of tcgen05
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
   double* stats = nullptr;
-  int4* work = nullptr;
+  int4* work = nullptr;    // FP64 scan: 64 x 64 tiles
   int n_work = 0;
+  int4* tasks = nullptr;   // FP32 scan: warp tasks (instance, strip, first column, chunk width)
+  int n_tasks = 0;
+  size_t tasks_cap = 0;
   bool work_dirty = true;
   bool merged_fresh = false;
   uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
@@ -155,6 +162,14 @@ int build_work(qis_ctx* ctx) {
   const size_t cap_items = (size_t)ctx->max_inst * ((ctx->NP / kTile) * (ctx->NP / kTile + 1) / 2);
   if (w.size() > cap_items) return fail(ctx, QIS_ERR_STATE, "work list overflow");
   if (!w.empty()) CK(cudaMemcpyAsync(ctx->work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  // warp tasks of the FP32 pair scan, widest chunks first (better tail balance)
+  std::vector<int4> t;
+  for (int id = 0; id < (int)ctx->inst.size(); ++id) scan_tasks_for(id, ctx->inst[id].n, t);
+  std::stable_sort(t.begin(), t.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+  if (t.size() > ctx->tasks_cap) return fail(ctx, QIS_ERR_STATE, "task list overflow");
+  ctx->n_tasks = (int)t.size();
+  if (!t.empty()) CK(cudaMemcpyAsync(ctx->tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   ctx->work_dirty = false;
   return 0;
 }
@@ -193,6 +208,10 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   ctx->pool_mat = (long long)ctx->max_inst * ctx->NP * ctx->NP;
   ctx->pool_vec = (long long)ctx->max_inst * ctx->NP;
   ctx->digit_planes = (ctx->mode == QIS_FP64) ? 0 : (ctx->mode == QIS_PM1_FP8 ? 1 : kMaxDigits);
+  {
+    const char* e = getenv("QIS_FIELDS_SIMT");
+    ctx->fields_simt = e && e[0] == '1';
+  }
   auto bail = [&](int rc) {
     g_create_error = ctx->err;
     qis_destroy(ctx);
@@ -216,6 +235,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(ctx->zob, kMaxN);
     ALLOC(ctx->stats, kMaxN + 8);
     ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2));
+    ctx->tasks_cap = (size_t)ctx->max_inst * (NP / 8) * (NP / 32 + 2);
+    ALLOC(ctx->tasks, ctx->tasks_cap);
     DevPtrs& P = ctx->P;
     P.inst = ctx->inst_d;
     P.n_inst = 0;
@@ -248,7 +269,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.iter_t, B);
     if (ctx->mode != QIS_FP64) {
       ALLOC(P.aq, B * NP);
-      ALLOC(P.a32, B * NP);
+      ALLOC(P.as32, B * NP);
       ALLOC(P.S16, B * NP);
     } else {
       ALLOC(P.a64, B * NP);
@@ -360,8 +381,8 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
     if (q < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "couplings too large for exact 64-bit energies");
     const double maxJq = ldexp(maxJ, q);
     int digits = 1;
-    while (digits < kMaxDigits && ldexp(1.0, 8 * digits - 1) <= maxJq + 0.5) ++digits;
-    if (ldexp(1.0, 8 * digits - 1) <= maxJq + 0.5) return fail(ctx, QIS_ERR_INVALID_ARG, "coupling range too wide");
+    while (digits < kMaxDigits && ldexp(1.0, 12 * digits - 1) <= maxJq + 0.5) ++digits;
+    if (ldexp(1.0, 12 * digits - 1) <= maxJq + 0.5) return fail(ctx, QIS_ERR_INVALID_ARG, "coupling range too wide");
     if (ctx->mode == QIS_PM1_FP8) digits = 1;
     d.q = q;
     d.digits = digits;
@@ -369,9 +390,10 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
     d.j4max = (float)(4.0 * ldexp(rint(maxJq), -q)) * (1.0f + 1e-6f);
   }
   CK(cudaMemcpyAsync(ctx->inst_d + id, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
-  if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+  if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, id, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
   CK(cudaStreamSynchronize(s));
   ctx->inst.push_back(d);
+  if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
   ctx->inst_ready.push_back(0);
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
@@ -462,13 +484,15 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
     CK(prof_end(ctx, 0));
     CK(prof_begin(ctx, 1));
     if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
-    else LAUNCH(launch_fields_exact(P, s));
+    else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
+    else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, s));
     CK(prof_end(ctx, 1));
     CK(prof_begin(ctx, 2));
     LAUNCH(launch_bound(P, s));
     CK(prof_end(ctx, 2));
     CK(prof_begin(ctx, 3));
-    LAUNCH(launch_scan(P, ctx->work, ctx->n_work, s));
+    if (ctx->mode == QIS_FP64) LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
+    else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, s));
     CK(prof_end(ctx, 3));
     CK(prof_begin(ctx, 4));
     LAUNCH(launch_merge(P, s));

@@ -1,8 +1,10 @@
 // qis_common.cuh -- types and helpers shared by the CUDA translation units of libqis.
 #pragma once
 #include <cuda_runtime.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
+
+#include <vector>
 
 #include "../../include/qis.h"
 
@@ -10,7 +12,7 @@ namespace qis {
 
 constexpr int kTile = 64;        // scan tile edge (sites)
 constexpr int kPad = 128;        // n is padded to a multiple of this (tensor-core M tile)
-constexpr int kMaxDigits = 7;    // 8-bit signed digits of the fixed-point couplings
+constexpr int kMaxDigits = 5;    // 12-bit signed digits (base 4096) of the fixed-point couplings
 constexpr int kMaxN = 4096;
 
 // Device error flags (bit mask in ctx status word).
@@ -24,7 +26,7 @@ struct InstDesc {
   int n_pad;        // n rounded up to kPad
   int W;            // words per state
   int q;            // fixed-point exponent: Jq = J * 2^q  (-1 in FP64 mode)
-  int digits;       // number of 8-bit digits of Jq
+  int digits;       // number of base-4096 digits of Jq
   int first_search; // global index of search r = 0 of this instance
   long long off_mat;  // element offset of this instance's n_pad x n_pad matrices
   long long off_vec;  // element offset of this instance's n_pad vectors
@@ -42,7 +44,7 @@ struct DevPtrs {
   const double* J64;      // [off_mat + i*n_pad + j]
   const long long* Jq;    // fixed-point couplings
   const float* J4;        // fl32(4 * J)
-  const __nv_bfloat16* D16; // digits [d][off_mat + i*n_pad + k] (digit-major pools of size pool_mat)
+  const __half* D16;      // digit planes [d][inst][i][NP] (row stride NP), plane = pool_mat elements
   long long pool_mat;     // elements of one digit plane
   const double* h64;      // [off_vec + i]
   const long long* hq;
@@ -61,14 +63,14 @@ struct DevPtrs {
   int* active;            // [b]
   int* iter_t;            // [b] iterations done
   long long* aq;          // [b][n_pad] exact a_i * 2^q (split modes)
-  float* a32;             // [b][n_pad] fl32(a_i)
+  float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
   int* surv_cnt;          // [b]
-  uint32_t* surv;         // [b][cap]
-  __nv_bfloat16* S16;     // [b][n_pad] +-1 spins of the parent (0 past n)
+  unsigned long long* surv;  // [b][cap] candidate index (bit 63 clear) or scan hit record (bit 63 set)
+  __half* S16;            // [b][NP] +-1 spins of the parent (0 past n), tensor-core operand
   uint64_t* init_bits;    // [b][Wmax]
   int* status;            // [0] error bits
   unsigned long long* cand;  // [0] pair candidates evaluated, [1] single candidates
@@ -119,14 +121,19 @@ __device__ inline unsigned long long dkey(double x) {
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);
-cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, __nv_bfloat16* D16, long long* Jq,
+cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,
+                             cudaStream_t s);
+int gemm_tile_n(int R, int digits);
+cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
                             float* J4, long long* hq, cudaStream_t s);
 cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s);
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s);
-cudaError_t launch_scan(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s);
+cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, cudaStream_t s);
+cudaError_t launch_scan64(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s);
+void scan_tasks_for(int inst, int n, std::vector<int4>& out);
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_final_merge(const DevPtrs& P, cudaStream_t s);
 size_t merge_smem(int K1, int cap);

@@ -1,0 +1,309 @@
+// qis_gemm.cu -- exact local fields on the 5th-generation tensor cores (tcgen05 + TMA + TMEM).
+//
+// The couplings of an instance are held on a fixed-point grid, Jq = J 2^q (int64), and written
+// in balanced base-4096 digits, Jq = sum_d 4096^d D_d with D_d in [-2048, 2047]; every digit is
+// an exact FP16 integer. With the parent spins S (+-1, FP16) of the R searches of the instance,
+//     F_d = D_d S^T            (one FP16 GEMM per digit, FP32 accumulation in TMEM)
+// is exact: every product is an integer of magnitude <= 2048 and every partial sum stays below
+// 2048 n <= 2^24, so no rounding can occur whatever order the tensor core adds in. The exact
+// field of site i for search r is then fq = hq_i + sum_d 4096^d F_d[i][r] (int64) and the
+// single-flip energy change a_i = -2 s_i f_i (Sec. III) follows exactly.
+//
+// One CTA computes a 128-row tile (TMEM lanes = sites i) x N_T searches for all digits:
+//   warp 0 lane 0 : TMA producer (digit tiles of 128 x 64 and the spin tile N_T x 64 per stage)
+//   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::f16, M=128, N=N_T, K=16), commits free stages
+//   all 4 warps   : epilogue, tcgen05.ld of their 32 TMEM lanes, exact int64 combination.
+// Every wait is bounded (2 s of %globaltimer); on timeout the CTA raises kStatTimeout, drains
+// what it issued (again bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include "qis_common.cuh"
+
+namespace qis {
+
+constexpr int kStages = 3;
+constexpr int kKC = 64;              // K elements per stage (128 bytes of FP16: one swizzle row)
+constexpr int kTileBytesA = 128 * kKC * 2;
+
+struct GemmArgs {
+  int n_inst, R, NP, Wmax, NT, digits_max, stages;
+  long long plane_rows;              // rows of one digit plane in the A tensor map (max_inst * NP)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t t0) {
+  while (!mbar_try(bar, parity)) {
+    if (gtimer() - t0 > 2000000000ull) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// K-major operand tile, 128-byte rows, 128B swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);          // start address
+  d |= (uint64_t)(16u >> 4) << 16;                    // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;                  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                             // fixed 0b001
+  d |= (uint64_t)2 << 61;                             // SWIZZLE_128B
+  return d;
+}
+// kind::f16 instruction descriptor: D = F32, A = B = F16, K-major both, N, M = 128.
+__device__ __forceinline__ uint32_t idesc_f16(int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB, DevPtrs P,
+                                                      GemmArgs G) {
+  const int inst = blockIdx.z;
+  const InstDesc d = P.inst[inst];
+  const int m0 = blockIdx.x * 128;
+  const int n0 = blockIdx.y * G.NT;
+  if (m0 >= d.n_pad || n0 >= G.R) return;               // uniform: before any barrier
+  const int NT = G.NT, D = d.digits, S = G.stages;
+  const int kc_total = d.n_pad / kKC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bytesB = NT * kKC * 2;
+  const int stage_bytes = G.digits_max * kTileBytesA + bytesB;   // same layout for every instance
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  int ncols = 32;
+  while (ncols < D * NT) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint64_t t0 = gtimer();
+
+  if (threadIdx.x == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kc = 0; kc < kc_total; ++kc) {
+      const int s = kc % S;
+      if (kc >= S && !mbar_wait(&empty[s], ((kc / S) + 1) & 1, t0)) {
+        atomicOr(&s_err, 1);
+        break;
+      }
+      if (*(volatile int*)&s_err) break;
+      unsigned char* st = smem + s * stage_bytes;
+      mbar_expect_tx(&full[s], (uint32_t)(D * kTileBytesA + bytesB));
+      for (int dg = 0; dg < D; ++dg)
+        tma_load_2d(st + dg * kTileBytesA, &mapA, kc * kKC,
+                    (int)(dg * G.plane_rows + (long long)inst * G.NP + m0), &full[s]);
+      tma_load_2d(st + G.digits_max * kTileBytesA, &mapB, kc * kKC, d.first_search + n0, &full[s]);
+      ++issued;
+    }
+    // drain: on an error, the last (at most S) issued stages may still be in flight; their
+    // full barriers are in the last phase armed for each stage, so parity waits are exact
+    if (*(volatile int*)&s_err) {
+      for (int kc = max(0, issued - S); kc < issued; ++kc)
+        mbar_wait(&full[kc % S], (kc / S) & 1, gtimer());
+    }
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_f16(NT);
+    int kc = 0;
+    for (; kc < kc_total; ++kc) {
+      const int s = kc % S;
+      if (!mbar_wait(&full[s], (kc / S) & 1, t0)) {
+        atomicOr(&s_err, 2);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      unsigned char* st = smem + s * stage_bytes;
+      const uint32_t b_addr = smem_u32(st + G.digits_max * kTileBytesA);
+      for (int dg = 0; dg < D; ++dg) {
+        const uint32_t a_addr = smem_u32(st + dg * kTileBytesA);
+#pragma unroll
+        for (int k4 = 0; k4 < kKC / 16; ++k4)
+          mma_f16(tmem + dg * NT, sdesc(a_addr + k4 * 32), sdesc(b_addr + k4 * 32), idesc, (kc | k4) != 0);
+      }
+      mma_commit(&empty[s]);   // stage free once these MMAs have read it
+    }
+    mma_commit(&done);         // all issued MMAs complete -> done
+  }
+  // ---------------- epilogue (all warps)
+  const bool ok_done = mbar_wait(&done, 0, t0);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  const bool ok = ok_done && (s_err == 0);
+  if (!ok && threadIdx.x == 0) atomicOr(P.status, kStatTimeout);
+  if (ok) {
+    const int i = m0 + warp * 32 + lane;
+    const long long hq = (i < d.n) ? P.hq[d.off_vec + i] : 0;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      long long acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = hq;
+      long long wdig = 1;
+      for (int dg = 0; dg < D; ++dg) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dg * NT + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] += wdig * (long long)__float2int_rn(__uint_as_float(v[u]));
+        wdig *= 4096;
+      }
+      if (i < d.n_pad) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int r = n0 + c0 + u;
+          if (r >= G.R) continue;
+          const int b = d.first_search + r;
+          if (!P.active[b]) continue;
+          long long aq = 0;
+          float2 as = make_float2(0.f, 0.f);
+          if (i < d.n) {
+            const int sg = (int)((P.par_bits[(long long)b * P.Wmax + (i >> 6)] >> (i & 63)) & 1ull);
+            aq = sg ? 2 * acc[u] : -2 * acc[u];
+            as = make_float2((float)ldexp((double)aq, -d.q), sg ? -1.f : 1.f);
+          }
+          P.aq[(long long)b * P.NP + i] = aq;
+          P.as32[(long long)b * P.NP + i] = as;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encode() {
+  if (g_encode) return cudaSuccess;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return cudaSuccess;
+}
+
+cudaError_t make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kKC, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
+int gemm_tile_n(int R, int digits) {
+  int nt = 16;
+  while (nt < R && nt < 256) nt += 16;
+  while (nt > 16 && digits * nt > 512) nt -= 16;   // all digit accumulators must fit in TMEM
+  return nt;
+}
+
+int gemm_stages(int digits, int nt) {
+  const size_t per = (size_t)digits * kTileBytesA + (size_t)nt * kKC * 2;
+  return (3 * per + 1024 <= 200 * 1024) ? 3 : 2;
+}
+
+size_t gemm_smem(int digits, int nt) {
+  return (size_t)gemm_stages(digits, nt) * (digits * kTileBytesA + nt * kKC * 2) + 1024;
+}
+
+cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,
+                             cudaStream_t s) {
+  cudaError_t e = get_encode();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mA, mB;
+  const long long plane_rows = (long long)max_inst * P.NP;
+  e = make_map(&mA, D16, (uint64_t)P.NP, (uint64_t)(plane_rows * digits_max), 128);
+  if (e != cudaSuccess) return e;
+  GemmArgs G;
+  G.n_inst = P.n_inst;
+  G.R = P.R;
+  G.NP = P.NP;
+  G.Wmax = P.Wmax;
+  G.digits_max = digits_max;
+  G.plane_rows = plane_rows;
+  G.NT = gemm_tile_n(P.R, digits_max);
+  G.stages = gemm_stages(digits_max, G.NT);
+  e = make_map(&mB, S16, (uint64_t)P.NP, (uint64_t)max_inst * P.R, (uint32_t)G.NT);
+  if (e != cudaSuccess) return e;
+  const size_t sm = gemm_smem(digits_max, G.NT);
+  static size_t attr = 0;
+  if (attr < sm) {
+    e = cudaFuncSetAttribute(k_fields_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
+  }
+  dim3 grid(P.NP / 128, (P.R + G.NT - 1) / G.NT, P.n_inst);
+  k_fields_tc<<<grid, 128, sm, s>>>(mA, mB, P, G);
+  return cudaGetLastError();
+}
+
+}  // namespace qis

@@ -4,8 +4,8 @@
 //   J64  FP64 couplings as given (zero padding)
 //   Jq   fixed-point couplings Jq = J * 2^q (int64, exact on the 2^-q grid)
 //   J4   fl32(4 * Jq * 2^-q): the candidate filter's coupling term
-//   D16  Jq written in balanced base-256 digits, Jq = sum_d 256^d D_d, D_d in [-128, 127],
-//        one BF16 plane per digit (every digit is an exact BF16 integer)
+//   D16  Jq written in balanced base-4096 digits, Jq = sum_d 4096^d D_d, D_d in [-2048, 2047],
+//        one FP16 plane per digit (every digit is an exact FP16 integer)
 #include "qis_common.cuh"
 
 namespace qis {
@@ -72,8 +72,9 @@ cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat
 }
 
 // ---------------------------------------------------------------- fixed point + digits
-__global__ void k_quantize(const double* J64, const double* h64, int n, int n_pad, int q, int digits,
-                           long long plane, __nv_bfloat16* D16, long long* Jq, float* J4, long long* hq) {
+// D16 rows use the context-wide stride NP (one 2D tensor map covers every instance and digit).
+__global__ void k_quantize(const double* J64, const double* h64, int n, int n_pad, int NP, int q, int digits,
+                           long long plane, __half* D16, long long* Jq, float* J4, long long* hq) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)n_pad * n_pad;
   if (e < tot) {
@@ -84,21 +85,21 @@ __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pa
     J4[e] = (float)(4.0 * ldexp((double)v, -q));
     long long x = v;
     for (int d = 0; d < digits; ++d) {
-      long long r = x & 255;                  // x mod 256 in [0, 255]
-      if (r >= 128) r -= 256;                 // balanced digit in [-128, 127]
-      D16[d * plane + e] = __float2bfloat16_rn((float)r);
-      x = (x - r) >> 8;                       // exact
+      long long r = x & 4095;                 // x mod 4096 in [0, 4095]
+      if (r >= 2048) r -= 4096;               // balanced digit in [-2048, 2047]
+      D16[d * plane + (long long)i * NP + j] = __float2half_rn((float)r);
+      x = (x - r) >> 12;                      // exact
     }
   }
   if (e < n_pad) hq[e] = (e < n) ? __double2ll_rn(ldexp(h64[e], q)) : 0;
 }
 
-cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, __nv_bfloat16* D16, long long* Jq,
+cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
                             float* J4, long long* hq, cudaStream_t s) {
   const long long tot = (long long)d.n_pad * d.n_pad;
-  k_quantize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad,
-                                                          d.q, d.digits, P.pool_mat, D16 + d.off_mat,
-                                                          Jq + d.off_mat, J4 + d.off_mat, hq + d.off_vec);
+  k_quantize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, P.NP, d.q, d.digits, P.pool_mat,
+      D16 + (long long)inst * P.NP * P.NP, Jq + d.off_mat, J4 + d.off_mat, hq + d.off_vec);
   return cudaGetLastError();
 }
 

@@ -2,10 +2,9 @@
 //
 // Per iteration:
 //   k_pick        parent = first unused kept state in key order (Alg. 3), marked used
-//   k_fields_*    local fields of the parent; a_i = -2 s_i f_i
-//   k_bound       per-search filter threshold (see below)
-//   k_scan*       all single and pair flips, dE_i = a_i, dE_ij = a_i + a_j + 4 s_i s_j J_ij;
-//                 survivors (candidate indices) appended per search
+//   k_fields_*    local fields of the parent; a_i = -2 s_i f_i (energy change of flip i)
+//   k_bound       per-search filter threshold; single flips dE_i = a_i tested here
+//   k_scan_*      pair flips dE_ij = a_i + a_j + 4 s_i s_j J_ij; survivors appended
 //   k_merge       exact energies of the survivors, duplicate removal (Zobrist hash + full
 //                 compare), new list = first K+1 of old list + survivors by (E, stamp)
 //
@@ -15,9 +14,9 @@
 // same list as keeping the K+1 smallest keys (E, stamp) of the old list and of the new,
 // non-duplicate candidates with E < T. The filter may therefore also drop every candidate
 // whose energy exceeds any upper bound U on the (K+1+count)-th smallest candidate energy
-// (at most `count` candidates duplicate a kept state). U is the (K+1+count)-th smallest
-// energy among the single and pair flips of the m sites with the lowest a_i, a subset of the
-// candidates, so U is never below the true order statistic.
+// (at most `count` candidates duplicate a kept state). U is taken as the (K+1+count)-th
+// smallest energy among the single and pair flips of a few sites with the lowest a_i, a
+// subset of the candidates, so it never lies below the true order statistic.
 #include "qis_common.cuh"
 
 namespace qis {
@@ -63,7 +62,7 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
       const uint64_t* src = P.lst_bits + (base + sel) * P.Wmax;
       for (int k = lane; k < d.n_pad; k += 32) {
         float v = (k < d.n) ? (sigma_of(src, k) ? -1.f : 1.f) : 0.f;
-        P.S16[(long long)b * P.NP + k] = __float2bfloat16_rn(v);
+        P.S16[(long long)b * P.NP + k] = __float2half_rn(v);
       }
     }
   }
@@ -75,7 +74,8 @@ cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- fields (exact integers, SIMT)
-// fq_i = hq_i + sum_k Jq_ik s_k in int64 (exact); aq_i = -2 s_i fq_i; a32_i = fl32(aq_i 2^-q).
+// fq_i = hq_i + sum_k Jq_ik s_k in int64 (exact); aq_i = -2 s_i fq_i;
+// as32_i = {fl32(aq_i 2^-q), s_i}.
 constexpr int kFS = 8;  // searches per thread
 __global__ void __launch_bounds__(128) k_fields_exact(DevPtrs P) {
   const int inst = blockIdx.y;
@@ -105,14 +105,16 @@ __global__ void __launch_bounds__(128) k_fields_exact(DevPtrs P) {
     if (!act[s]) continue;
     const int b = d.first_search + s0 + s;
     long long aq = 0;
-    float a32 = 0.f;
+    float a32 = 0.f, s32 = 0.f;
     if (i < d.n) {
+      const int sg = (int)((sb[s][i >> 6] >> (i & 63)) & 1ull);
       const long long fq = acc[s] + P.hq[d.off_vec + i];
-      aq = ((sb[s][i >> 6] >> (i & 63)) & 1ull) ? 2 * fq : -2 * fq;
+      aq = sg ? 2 * fq : -2 * fq;
       a32 = (float)ldexp((double)aq, -d.q);
+      s32 = sg ? -1.f : 1.f;
     }
     P.aq[(long long)b * P.NP + i] = aq;
-    P.a32[(long long)b * P.NP + i] = a32;
+    P.as32[(long long)b * P.NP + i] = make_float2(a32, s32);
   }
 }
 
@@ -144,10 +146,9 @@ __global__ void __launch_bounds__(128) k_fields_fp64(DevPtrs P) {
 #pragma unroll
   for (int s = 0; s < kFS; ++s) acc[s] = 0.0;
   const double* J = P.J64 + d.off_mat;
-  const int ic = min(i, d.n_pad - 1);
   for (int j = 0; j < d.n; ++j) {
     if (j == i) continue;
-    const double v = J[(long long)j * d.n_pad + ic];      // J_ji = J_ij
+    const double v = J[(long long)j * d.n_pad + i];      // J_ji = J_ij
 #pragma unroll
     for (int s = 0; s < kFS; ++s) acc[s] = __dadd_rn(acc[s], ((sb[s][j >> 6] >> (j & 63)) & 1ull) ? -v : v);
   }
@@ -169,240 +170,254 @@ cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- block bitonic sort
-template <typename K>
-__device__ void bitonic_sort(K* key, uint32_t* val, int n2) {
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
-        const int u = t ^ j;
-        if (u > t) {
-          const K a = key[t], c = key[u];
-          const uint32_t va = val[t], vc = val[u];
-          const bool gt = (a > c) || (a == c && va > vc);
-          const bool up = (t & k) == 0;
-          if (gt == up) {
-            key[t] = c; key[u] = a;
-            val[t] = vc; val[u] = va;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
+// ---------------------------------------------------------------- helpers
 __device__ inline int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
   return p;
 }
 
-// candidate energy change in the scan's arithmetic
-__device__ inline float dE32(float ai, float aj, float j4, int flip) {
-  return (ai + aj) + __int_as_float(__float_as_int(j4) ^ (flip << 31));
-}
 __device__ inline double dE64(double ai, double aj, double j, int flip) {
   // (a_i + a_j) + 4 s_i s_j J_ij; the product 4 s_i s_j J_ij is exact
   return __dadd_rn(__dadd_rn(ai, aj), flip ? -4.0 * j : 4.0 * j);
 }
 
-// ---------------------------------------------------------------- per-search bound
-constexpr int kMaxSub = 3968;  // subset values; keeps the padded sort within kMaxN
-// Dynamic shared memory: vals (kMaxN floats/doubles as u64 keys) + idx.
-__global__ void __launch_bounds__(256) k_bound(DevPtrs P) {
-  const int b = blockIdx.x;
-  const InstDesc d = P.inst[b / P.R];
-  const long long base = (long long)b * P.K1;
-  if (!P.active[b]) {
-    if (threadIdx.x == 0) {
-      P.surv_cnt[b] = 0;
-      P.thr32[b] = -INFINITY;
-      P.thrE[b] = -INFINITY;
-      P.capE[b] = -INFINITY;
+__device__ inline unsigned fkey(float x) {
+  x = x + 0.f;
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ inline double dkey_inv(unsigned long long k) {
+  return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Block-wide radix select: the rank-th smallest (0-based) of `cnt` keys in smem, 8 bits per
+// pass from the top. `hist` holds 256 counters. Every thread of the block must call it.
+template <typename K>
+__device__ K radix_select(const K* keys, int cnt, int rank, int* hist) {
+  __shared__ K s_prefix;
+  __shared__ int s_rank;
+  K prefix = 0, mask = 0;
+  constexpr int kBits = 8 * sizeof(K);
+  for (int shift = kBits - 8; shift >= 0; shift -= 8) {
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const K k = keys[t];
+      if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255)], 1);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int r = rank, dgt = 0;
+      for (; dgt < 255; ++dgt) {
+        if (r < hist[dgt]) break;
+        r -= hist[dgt];
+      }
+      s_prefix = prefix | ((K)dgt << shift);
+      s_rank = r;
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    rank = s_rank;
+    mask |= (K)255 << shift;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// ---------------------------------------------------------------- per-search bound
+constexpr int kSubSites = 64;   // at most this many low-a sites in the subset (2080 candidates)
+constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
+
+__global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
+  const int b = blockIdx.x;
+  if (!P.active[b]) {
+    if (threadIdx.x == 0) P.surv_cnt[b] = 0;
     return;
   }
-  extern __shared__ unsigned char smem[];
-  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem);        // [max(npow2, subpow2)]
-  uint32_t* idx = reinterpret_cast<uint32_t*>(key + kMaxN);                      // [same]
-  __shared__ float s_amax;
-  __shared__ uint64_t pb[kMaxN / 64];
+  const InstDesc d = P.inst[b / P.R];
+  const long long base = (long long)b * P.K1;
   const int n = d.n;
   const bool fp64 = P.mode == QIS_FP64;
+  extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
+  __shared__ int hist[256];
+  __shared__ int sites[kSubSites];
+  __shared__ int s_nsites, s_bin;
+  __shared__ float s_amin, s_amax;
+  __shared__ uint64_t pb[kMaxN / 64];
+  __shared__ float s_thr;
+  __shared__ double s_T, s_cap;
   const int cnt = P.lst_count[b];
   const double T = (cnt == P.K1) ? P.lst_E[base + P.lst_ord[base + P.K1 - 1]] : INFINITY;
   const double Ep = P.par_E[b];
   const long long C = (long long)n * (n + 1) / 2;
   const int k = P.K1 + cnt;
-  for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
-  if (threadIdx.x == 0) s_amax = 0.f;
-  __syncthreads();
-  const float* a32 = P.a32 + (long long)b * P.NP;
+  const float2* as = P.as32 + (long long)b * P.NP;
   const double* a64 = P.a64 + (long long)b * P.NP;
-  if (!fp64) {
-    float m = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(a32[i]));
-    atomicMax(reinterpret_cast<int*>(&s_amax), __float_as_int(m));   // non-negative floats order as ints
-  }
-  double U = INFINITY;
-  if (C > k) {
-    // m lowest a_i: sort (a_i, i) ascending
-    const int n2 = next_pow2(n);
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-      key[i] = (i < n) ? dkey(fp64 ? a64[i] : (double)a32[i]) : ~0ull;
-      idx[i] = i;
-    }
-    __syncthreads();
-    bitonic_sort(key, idx, n2);
-    int want = min(4 * k, kMaxSub);
-    int m = 1;
-    while (m < n && m + m * (m - 1) / 2 < want) ++m;
-    const int M = m + m * (m - 1) / 2;
-    // copy the m sites out of idx before key/idx are reused
-    __shared__ int sites[128];
-    const int msafe = min(m, 128);
-    for (int x = threadIdx.x; x < msafe; x += blockDim.x) sites[x] = idx[x];
-    __syncthreads();
-    const int mm = msafe;
-    const int MM = mm + mm * (mm - 1) / 2;
-    const int M2 = next_pow2(MM);
-    for (int t = threadIdx.x; t < M2; t += blockDim.x) {
-      unsigned long long kk = ~0ull;
-      if (t < MM) {
-        int i, j;
-        if (t < mm) {
-          i = sites[t]; j = -1;
-        } else {
-          // pair number r among the mm sites: x < y lexicographic
-          int r = t - mm, x = 0;
-          while (r >= mm - 1 - x) { r -= mm - 1 - x; ++x; }
-          i = sites[x]; j = sites[x + 1 + r];
-          if (i > j) { int tmp = i; i = j; j = tmp; }
-        }
-        if (fp64) {
-          double de;
-          if (j < 0) de = a64[i];
-          else de = dE64(a64[i], a64[j], P.J64[d.off_mat + (long long)i * d.n_pad + j],
-                         sigma_of(pb, i) ^ sigma_of(pb, j));
-          kk = dkey(__dadd_rn(Ep, de));
-        } else {
-          float de;
-          if (j < 0) de = a32[i];
-          else de = dE32(a32[i], a32[j], P.J4[d.off_mat + (long long)i * d.n_pad + j], sigma_of(pb, i) ^ sigma_of(pb, j));
-          kk = dkey((double)de);
-        }
-      }
-      key[t] = kk;
-      idx[t] = t;
-    }
-    __syncthreads();
-    bitonic_sort(key, idx, M2);
-    (void)M;
-    if (k - 1 < MM) {
-      unsigned long long u = key[k - 1];
-      u = (u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u;
-      U = __longlong_as_double((long long)u);
-    }
-  }
-  __syncthreads();   // s_amax complete
+  for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   if (threadIdx.x == 0) {
     P.surv_cnt[b] = 0;
+    s_amin = INFINITY;
+    s_amax = -INFINITY;
+    s_nsites = 0;
+  }
+  __syncthreads();
+  // range of a_i (a ~ fl32 of the exact value in FP64 mode too: only used to bin sites)
+  {
+    float mn = INFINITY, mx = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float a = fp64 ? (float)a64[i] : as[i].x;
+      mn = fminf(mn, a);
+      mx = fmaxf(mx, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float wmn[4], wmx[4];
+    if ((threadIdx.x & 31) == 0) {
+      wmn[threadIdx.x >> 5] = mn;
+      wmx[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = wmn[0], c = wmx[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        a = fminf(a, wmn[w]);
+        c = fmaxf(c, wmx[w]);
+      }
+      s_amin = a;
+      s_amax = c;
+    }
+    __syncthreads();
+  }
+  const float amin = s_amin, amax = s_amax;
+  double U = INFINITY;
+  if (C > k && k <= kSubMax) {
+    // m lowest sites with m + m(m-1)/2 >= min(4k, kSubMax): found with a 256-bin histogram of a
+    const int want = min(4 * k, kSubMax);
+    int m = 1;
+    while (m < n && m + m * (m - 1) / 2 < want) ++m;
+    const float span = fmaxf(amax - amin, 1e-30f);
+    const float scale = 255.99f / span;
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float a = fp64 ? (float)a64[i] : as[i].x;
+      atomicAdd(&hist[min(255, (int)((a - amin) * scale))], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = 0, bin = 0;
+      for (; bin < 256; ++bin) {
+        c += hist[bin];
+        if (c >= m) break;
+      }
+      s_bin = min(bin, 255);
+    }
+    __syncthreads();
+    const int bin = s_bin;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float a = fp64 ? (float)a64[i] : as[i].x;
+      if (min(255, (int)((a - amin) * scale)) <= bin) {
+        const int slot = atomicAdd(&s_nsites, 1);
+        if (slot < kSubSites) sites[slot] = i;
+      }
+    }
+    __syncthreads();
+    const int mm = min(s_nsites, kSubSites);
+    const int M = mm + mm * (mm - 1) / 2;
+    if (M >= k) {
+      // subset candidate energies, in the scan's arithmetic
+      for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        int i, j = -1;
+        if (t < mm) {
+          i = sites[t];
+        } else {
+          int r = t - mm, x = 0;
+          while (r >= mm - 1 - x) { r -= mm - 1 - x; ++x; }
+          i = sites[x];
+          j = sites[x + 1 + r];
+          if (i > j) { const int tmp = i; i = j; j = tmp; }
+        }
+        if (fp64) {
+          double de = a64[i];
+          if (j >= 0) de = dE64(a64[i], a64[j], P.J64[d.off_mat + (long long)i * d.n_pad + j],
+                                sigma_of(pb, i) ^ sigma_of(pb, j));
+          subkey[t] = dkey(__dadd_rn(Ep, de));
+        } else {
+          float de = as[i].x;
+          if (j >= 0) {
+            const float2 vj = as[j];
+            const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
+            de = as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x);
+          }
+          reinterpret_cast<unsigned*>(subkey)[t] = fkey(de);
+        }
+      }
+      __syncthreads();
+      if (fp64) U = dkey_inv(radix_select<unsigned long long>(subkey, M, k - 1, hist));
+      else U = (double)fkey_inv(radix_select<unsigned>(reinterpret_cast<unsigned*>(subkey), M, k - 1, hist));
+    }
+  }
+  if (threadIdx.x == 0) {
     if (fp64) {
+      s_T = T;
+      s_cap = U;
       P.thrE[b] = T;
       P.capE[b] = U;
     } else {
-      // |dE~ - dE| <= delta: a32 and J4 are fl32 of exact values, plus two fl32 additions
-      const double delta = ldexp(2.0 * (double)s_amax + (double)d.j4max, -21);
-      const double t1 = (T == INFINITY) ? INFINITY : (T - Ep) + delta;   // T - Ep is exact
+      // |dE~ - dE| <= delta: a and 4J are fl32 of exact values; the scan adds one FMA
+      // rounding and one subtraction rounding (factor 8 margin in the constant)
+      const double t0 = fmin((T == INFINITY) ? INFINITY : T - Ep, U);   // T - Ep is exact
+      const double big = 3.0 * fmax(fabs((double)amin), fabs((double)amax)) + (double)d.j4max +
+                         (isinf(t0) ? 0.0 : fabs(t0));
+      const double delta = ldexp(big, -21);
+      const double t1 = (T == INFINITY) ? INFINITY : (T - Ep) + delta;
       const double t2 = U + 2.0 * delta;
-      P.thr32[b] = fl32_up(fmin(t1, t2));
+      s_thr = fl32_up(fmin(t1, t2));
+      P.thr32[b] = s_thr;
+    }
+  }
+  __syncthreads();
+  // single flips: dE_i = a_i
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    bool ok;
+    if (fp64) {
+      const double e = __dadd_rn(Ep, a64[i]);
+      ok = (e < s_T) && (e <= s_cap);
+    } else {
+      ok = as[i].x <= s_thr;
+    }
+    if (ok) {
+      const int slot = atomicAdd(P.surv_cnt + b, 1);
+      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = (uint32_t)i;
     }
   }
 }
 
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = (size_t)kMaxN * (8 + 4);
+  const size_t sm = (size_t)kSubMax * 8;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  k_bound<<<P.B, 256, sm, s>>>(P);
+  k_bound<<<P.B, 128, sm, s>>>(P);
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- candidate scan (FP32 filter)
-// One block per 64 x 64 tile (bi <= bj) of one instance; the tile of fl32(4 J) is loaded once
-// and reused for all R searches of the instance. Thread (ty, tx) owns rows 4ty..4ty+3 and
-// columns 4tx..4tx+3 of the tile. Pair (i, j), i < j, survives if dE~ <= thr; on a diagonal
-// tile the i == j positions carry the single flips.
-__global__ void __launch_bounds__(256) k_scan32(DevPtrs P, const int4* work) {
-  const int4 w = work[blockIdx.x];
-  const InstDesc d = P.inst[w.x];
-  const int n = d.n, np = d.n_pad;
-  const int i0 = w.y * kTile, j0 = w.z * kTile;
-  const bool diag = w.y == w.z;
-  __shared__ float Jt[kTile][kTile + 1];
-  __shared__ float ar_s[kTile], ac_s[kTile];
-  const float* J4 = P.J4 + d.off_mat;
-  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-    const int r = e >> 6, c = e & 63;
-    Jt[r][c] = J4[(long long)(i0 + r) * np + j0 + c];
-  }
-  __syncthreads();
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  float jr[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) jr[r][c] = Jt[ty * 4 + r][tx * 4 + c];
-  for (int s = 0; s < P.R; ++s) {
-    const int b = d.first_search + s;
-    __syncthreads();
-    if (!P.active[b]) continue;
-    const float* a = P.a32 + (long long)b * P.NP;
-    if (threadIdx.x < kTile) ar_s[threadIdx.x] = a[i0 + threadIdx.x];
-    else if (threadIdx.x < 2 * kTile) ac_s[threadIdx.x - kTile] = a[j0 + threadIdx.x - kTile];
-    __syncthreads();
-    const float thr = P.thr32[b];
-    const uint64_t wi = P.par_bits[(long long)b * P.Wmax + w.y];
-    const uint64_t wj = P.par_bits[(long long)b * P.Wmax + w.z];
-    const unsigned rs = (unsigned)(wi >> (ty * 4)) & 15u, cs = (unsigned)(wj >> (tx * 4)) & 15u;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = i0 + ty * 4 + r;
-      const float ai = ar_s[ty * 4 + r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int j = j0 + tx * 4 + c;
-        bool ok;
-        uint32_t cid;
-        if (diag && i >= j) {
-          ok = (i == j) && (i < n) && (ai <= thr);
-          cid = (uint32_t)i;
-        } else {
-          const int flip = ((rs >> r) ^ (cs >> c)) & 1;
-          const float y = dE32(ai, ac_s[tx * 4 + c], jr[r][c], flip);
-          ok = (j < n) && (y <= thr);
-          cid = pair_index(n, i, j);
-        }
-        if (ok) {
-          const int slot = atomicAdd(P.surv_cnt + b, 1);
-          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = cid;
-        }
-      }
-    }
-  }
-}
-
-// FP64 plain form: E' = E_p + dE exactly as defined; survivors have E' < T and E' <= cap.
+// ---------------------------------------------------------------- FP64 pair scan
+// Plain form: E' = E_p + dE exactly as defined; survivors have E' < T and E' <= cap.
+// One block per 64 x 64 tile (bi <= bj) of one instance, all R searches.
 __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
   const int4 w = work[blockIdx.x];
   const InstDesc d = P.inst[w.x];
   const int n = d.n, np = d.n_pad;
   const int i0 = w.y * kTile, j0 = w.z * kTile;
-  const bool diag = w.y == w.z;
   __shared__ double Jt[kTile][kTile + 1];
   __shared__ double ar_s[kTile], ac_s[kTile];
   const double* J = P.J64 + d.off_mat;
@@ -429,37 +444,77 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
       const double ai = ar_s[ty * 4 + r];
       for (int c = 0; c < 4; ++c) {
         const int j = j0 + tx * 4 + c;
-        bool ok;
-        uint32_t cid;
-        if (diag && i >= j) {
-          const double e = __dadd_rn(Ep, ai);
-          ok = (i == j) && (i < n) && (e < T) && (e <= cap);
-          cid = (uint32_t)i;
-        } else {
-          const int flip = ((rs >> r) ^ (cs >> c)) & 1;
-          const double e = __dadd_rn(Ep, dE64(ai, ac_s[tx * 4 + c], Jt[ty * 4 + r][tx * 4 + c], flip));
-          ok = (j < n) && (e < T) && (e <= cap);
-          cid = pair_index(n, i, j);
-        }
-        if (ok) {
+        if (j <= i || j >= n) continue;
+        const int flip = ((rs >> r) ^ (cs >> c)) & 1;
+        const double e = __dadd_rn(Ep, dE64(ai, ac_s[tx * 4 + c], Jt[ty * 4 + r][tx * 4 + c], flip));
+        if (e < T && e <= cap) {
           const int slot = atomicAdd(P.surv_cnt + b, 1);
-          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = cid;
+          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = pair_index(n, i, j);
         }
       }
     }
   }
 }
 
-cudaError_t launch_scan(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s) {
+cudaError_t launch_scan64(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s) {
   if (n_work <= 0) return cudaSuccess;
-  if (P.mode == QIS_FP64) k_scan64<<<n_work, 256, 0, s>>>(P, work);
-  else k_scan32<<<n_work, 256, 0, s>>>(P, work);
+  k_scan64<<<n_work, 256, 0, s>>>(P, work);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- exact merge (Alg. 2)
+// Block-wide exclusive scan of 0/1 flags f[0..cnt) into pos[], returns the total.
+__device__ int block_scan_flags(const int* f, int* pos, int cnt, int* tmp /* [blockDim] */) {
+  const int per = (cnt + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per, hi = min(cnt, lo + per);
+  int s = 0;
+  for (int t = lo; t < hi; ++t) s += f[t] ? 1 : 0;
+  tmp[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int v = tmp[t];
+      tmp[t] = acc;
+      acc += v;
+    }
+    tmp[blockDim.x] = acc;
+  }
+  __syncthreads();
+  int p = tmp[threadIdx.x];
+  for (int t = lo; t < hi; ++t) {
+    pos[t] = p;
+    p += f[t] ? 1 : 0;
+  }
+  const int total = tmp[blockDim.x];
+  __syncthreads();
+  return total;
+}
+
+template <typename K>
+__device__ void bitonic_sort(K* key, uint32_t* val, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          const K a = key[t], c = key[u];
+          const uint32_t va = val[t], vc = val[u];
+          const bool gt = (a > c) || (a == c && va > vc);
+          const bool up = (t & k) == 0;
+          if (gt == up) {
+            key[t] = c; key[u] = a;
+            val[t] = vc; val[u] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Shared layout (dynamic): old list [K1] {E, hash, slot}, survivors [P2] {key, cand},
-// rank/slot scratch [K1].
+// occupancy / free list / positions [K1] each.
 __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) return;
@@ -472,16 +527,19 @@ __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
     return;
   }
   extern __shared__ unsigned char smem[];
-  const int P2 = next_pow2(max(S, 1));
+  const int PC = next_pow2(P.cap);                              // sort capacity
   double* oE = reinterpret_cast<double*>(smem);                 // [K1]
   uint64_t* oH = reinterpret_cast<uint64_t*>(oE + K1);          // [K1]
-  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);   // [P2]
-  uint32_t* sc = reinterpret_cast<uint32_t*>(sk + P2);          // [P2]
-  int* oslot = reinterpret_cast<int*>(sc + P2);                 // [K1]
-  int* occ = oslot + K1;                                        // [K1]
-  int* freel = occ + K1;                                        // [K1]
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);   // [PC]
+  uint32_t* sc = reinterpret_cast<uint32_t*>(sk + PC);          // [PC]
+  int* oslot = reinterpret_cast<int*>(sc + PC);                 // [K1]
+  int* occ = oslot + K1;                                        // [K1] rank+1 of the kept old entry in a slot
+  int* freef = occ + K1;                                        // [K1] slot is free
+  int* fpos = freef + K1;                                       // [K1] position among free slots
+  int* freel = fpos + K1;                                       // [K1] free slots in order
   __shared__ uint64_t pb[kMaxN / 64];
-  __shared__ int s_nvalid, s_nfree;
+  __shared__ int s_nvalid, s_nc;
+  __shared__ int tmp[257];
   const int cnt = P.lst_count[b];
   const double T = (cnt == K1) ? P.lst_E[base + P.lst_ord[base + K1 - 1]] : INFINITY;
   const double Ep = P.par_E[b];
@@ -495,15 +553,58 @@ __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
     oH[r] = P.lst_hash[base + slot];
   }
   for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
-  if (threadIdx.x == 0) s_nvalid = 0;
+  if (threadIdx.x == 0) {
+    s_nvalid = 0;
+    s_nc = 0;
+  }
   __syncthreads();
+  // expand scan records into candidate indices, re-applying the scan's FP32 test verbatim
+  {
+    const float2* as = P.as32 + (long long)b * P.NP;
+    const float thr = fp64 ? 0.f : P.thr32[b];
+    for (int t = threadIdx.x; t < S; t += blockDim.x) {
+      const unsigned long long e = P.surv[(long long)b * P.cap + t];
+      if (!(e >> 63)) {
+        const int slot = atomicAdd(&s_nc, 1);
+        if (slot < P.cap) sc[slot] = (uint32_t)e;
+        continue;
+      }
+      const int i0 = (int)(e & 0xffff), jb = (int)((e >> 16) & 0xffff);
+      const int nc = (int)((e >> 32) & 0xf);
+      const unsigned hm = (unsigned)((e >> 36) & 0xff);
+      for (int r = 0; r < 8; ++r) {
+        if (!((hm >> r) & 1u)) continue;
+        const int i = i0 + r;
+        const float2 ri = as[i];
+        const float c = thr - ri.x;
+        for (int k = 0; k < nc; ++k) {
+          const int j = jb + 32 * k;
+          if (j <= i || j >= n) continue;
+          const float2 vj = as[j];
+          const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
+          const float y = fmaf(ri.y < 0.f ? -j4 : j4, vj.y, vj.x);
+          if (y <= c) {
+            const int slot = atomicAdd(&s_nc, 1);
+            if (slot < P.cap) sc[slot] = pair_index(n, i, j);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_nc > P.cap) {
+    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
+    return;
+  }
+  const int NCAND = s_nc;
+  const int P2 = next_pow2(max(NCAND, 1));
   const long long Epq = fp64 ? 0 : __double2ll_rn(ldexp(Ep, d.q));
   const long long Tq = (fp64 || T == INFINITY) ? LLONG_MAX : __double2ll_rn(ldexp(T, d.q));
   for (int t = threadIdx.x; t < P2; t += blockDim.x) {
     unsigned long long kk = ~0ull;
     uint32_t c = 0xffffffffu;
-    if (t < S) {
-      c = P.surv[(long long)b * P.cap + t];
+    if (t < NCAND) {
+      c = sc[t];
       int i, j;
       decode_candidate(n, c, i, j);
       const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
@@ -563,15 +664,14 @@ __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
       if (sk[mid] < ko) lo = mid + 1; else hi = mid;
     }
     const int rank = o + lo;
-    if (rank < K1) occ[oslot[o]] = 1 + rank;   // kept: remember rank + 1
+    if (rank < K1) occ[oslot[o]] = 1 + rank;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int nf = 0;
-    for (int k = 0; k < K1; ++k)
-      if (!occ[k]) freel[nf++] = k;
-    s_nfree = nf;
-  }
+  for (int k = threadIdx.x; k < K1; k += blockDim.x) freef[k] = occ[k] == 0;
+  __syncthreads();
+  block_scan_flags(freef, fpos, K1, tmp);
+  for (int k = threadIdx.x; k < K1; k += blockDim.x)
+    if (freef[k]) freel[fpos[k]] = k;
   __syncthreads();
   const int t_now = P.iter_t[b];
   for (int p = threadIdx.x; p < nv; p += blockDim.x) {
@@ -594,9 +694,7 @@ __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
       if (j >= 0 && (j >> 6) == x) m ^= 1ull << (j & 63);
       dst[x] = pb[x] ^ m;
     }
-    unsigned long long u = kp;
-    u = (u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u;
-    P.lst_E[base + slot] = __longlong_as_double((long long)u);
+    P.lst_E[base + slot] = dkey_inv(kp);
     P.lst_stamp[base + slot] = ((uint64_t)t_now << 32) | c;
     P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
     P.lst_used[base + slot] = 0;
@@ -610,8 +708,9 @@ __global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
 }
 
 size_t merge_smem(int K1, int cap) {
-  const int P2 = [](int x) { int p = 1; while (p < x) p <<= 1; return p; }(cap);
-  return (size_t)K1 * (8 + 8) + (size_t)P2 * (8 + 4) + (size_t)K1 * 4 * 3;
+  int P2 = 1;
+  while (P2 < cap) P2 <<= 1;
+  return (size_t)K1 * (8 + 8) + (size_t)P2 * (8 + 4) + (size_t)K1 * 4 * 5;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
@@ -622,122 +721,6 @@ cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
     attr = sm;
   }
   k_merge<<<P.B, 256, sm, s>>>(P);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- Alg. 4 merge
-// One block per instance. Search 0's list seeds the merged list; the lists of searches
-// 1..R-1 are merged in turn. A state already present is skipped (its first occurrence
-// wins); the rest are ranked by (E, search, position) and the first K+1 kept.
-__global__ void __launch_bounds__(256) k_final_merge(DevPtrs P) {
-  const int inst = blockIdx.x;
-  const InstDesc d = P.inst[inst];
-  const int K1 = P.K1, W = d.W;
-  extern __shared__ unsigned char smem[];
-  // 8-byte arrays first, then 4-byte arrays (keeps every array aligned for any K1)
-  double* aE = reinterpret_cast<double*>(smem);                               // accumulated list
-  unsigned long long* aS = reinterpret_cast<unsigned long long*>(aE + K1);    // src
-  uint64_t* aH = reinterpret_cast<uint64_t*>(aS + K1);
-  double* nE = reinterpret_cast<double*>(aH + K1);                            // incoming list
-  unsigned long long* nS = reinterpret_cast<unsigned long long*>(nE + K1);
-  uint64_t* nH = reinterpret_cast<uint64_t*>(nS + K1);
-  double* tE = reinterpret_cast<double*>(nH + K1);                            // staging
-  unsigned long long* tS = reinterpret_cast<unsigned long long*>(tE + K1);
-  uint64_t* tH = reinterpret_cast<uint64_t*>(tS + K1);
-  int* aR = reinterpret_cast<int*>(tH + K1);                                  // ref = b*K1 + slot
-  int* nR = aR + K1;
-  int* tR = nR + K1;
-  int* nDup = tR + K1;
-  int* nPos = nDup + K1;
-  __shared__ int s_acnt, s_ncnt;
-  for (int r = 0; r < P.R; ++r) {
-    const int b = d.first_search + r;
-    const long long base = (long long)b * K1;
-    const int cnt = P.lst_count[b];
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-      const int slot = P.lst_ord[base + p];
-      nE[p] = P.lst_E[base + slot];
-      nH[p] = P.lst_hash[base + slot];
-      nR[p] = (int)(base + slot);
-      nS[p] = ((unsigned long long)r << 32) | (unsigned)p;
-    }
-    if (r == 0) {
-      __syncthreads();
-      for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-        aE[p] = nE[p]; aH[p] = nH[p]; aR[p] = nR[p]; aS[p] = nS[p];
-      }
-      if (threadIdx.x == 0) s_acnt = cnt;
-      __syncthreads();
-      continue;
-    }
-    __syncthreads();
-    const int acnt = s_acnt;
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-      int dup = 0;
-      for (int a = 0; a < acnt && !dup; ++a) {
-        if (aH[a] != nH[p]) continue;
-        const uint64_t* x = P.lst_bits + (long long)aR[a] * P.Wmax;
-        const uint64_t* y = P.lst_bits + (long long)nR[p] * P.Wmax;
-        bool same = true;
-        for (int w = 0; w < W && same; ++w) same = x[w] == y[w];
-        dup = same;
-      }
-      nDup[p] = dup;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int m = 0;
-      for (int p = 0; p < cnt; ++p) {
-        nPos[p] = nDup[p] ? -1 : m;
-        if (!nDup[p]) ++m;
-      }
-      s_ncnt = m;
-    }
-    __syncthreads();
-    const int m = s_ncnt;
-    // compacted incoming entries go to the tail arrays' "new" view via nPos
-    for (int a = threadIdx.x; a < acnt; a += blockDim.x) {
-      // # incoming non-duplicates with E < aE[a]
-      int less = 0;
-      for (int p = 0; p < cnt; ++p)
-        if (nPos[p] >= 0 && nE[p] < aE[a]) ++less;
-      const int rank = a + less;
-      if (rank < K1) { tE[rank] = aE[a]; tS[rank] = aS[a]; tH[rank] = aH[a]; tR[rank] = aR[a]; }
-    }
-    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-      if (nPos[p] < 0) continue;
-      int le = 0;
-      for (int a = 0; a < acnt; ++a)
-        if (aE[a] <= nE[p]) ++le;
-      const int rank = nPos[p] + le;
-      if (rank < K1) { tE[rank] = nE[p]; tS[rank] = nS[p]; tH[rank] = nH[p]; tR[rank] = nR[p]; }
-    }
-    __syncthreads();
-    const int ncnt = min(K1, acnt + m);
-    for (int a = threadIdx.x; a < ncnt; a += blockDim.x) {
-      aE[a] = tE[a]; aS[a] = tS[a]; aH[a] = tH[a]; aR[a] = tR[a];
-    }
-    if (threadIdx.x == 0) s_acnt = ncnt;
-    __syncthreads();
-  }
-  const int acnt = s_acnt;
-  for (int a = threadIdx.x; a < K1; a += blockDim.x) {
-    P.mrg_ref[inst * K1 + a] = (a < acnt) ? aR[a] : -1;
-    P.mrg_src[inst * K1 + a] = (a < acnt) ? aS[a] : ~0ull;
-  }
-  if (threadIdx.x == 0) P.mrg_count[inst] = acnt;
-}
-
-size_t final_merge_smem(int K1) { return (size_t)K1 * (9 * 8 + 5 * 4); }
-
-cudaError_t launch_final_merge(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = final_merge_smem(P.K1);
-  static size_t attr = 0;
-  if (attr < sm) {
-    cudaFuncSetAttribute(k_final_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = sm;
-  }
-  k_final_merge<<<P.n_inst, 256, sm, s>>>(P);
   return cudaGetLastError();
 }
 

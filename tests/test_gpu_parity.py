@@ -221,3 +221,24 @@ def test_non_grid_inputs_are_rounded_and_flagged():
     ref = O.qi_search(J, h, K, 10, phi[0])
     assert np.array_equal(got["bits"], ref["bits"][: ref["count"]])
     np.testing.assert_allclose(got["E"], ref["E"][: ref["count"]], rtol=1e-9)
+
+
+@pytest.mark.parametrize("ens,prec,n,R", [("gaussian", "split_bf16", 100, 4), ("gaussian", "split_bf16", 600, 64),
+                                          ("pm1", "pm1_fp8", 1024, 128), ("gaussian", "split_bf16", 200, 20),
+                                          ("uniform", "split_bf16", 333, 48)])
+def test_tensor_core_fields_equal_exact_simt_fields(monkeypatch, ens, prec, n, R):
+    """The tcgen05 digit GEMM and the int64 SIMT reference give bit-identical searches."""
+    K, I_ = 30, 6
+    J, h = I.instance(ens, n, seed=n, inst=1)
+    phi = I.random_states(n, R, seed=n + 1)
+    lists = []
+    for simt in ("1", "0"):
+        monkeypatch.setenv("QIS_FIELDS_SIMT", simt)
+        ctx = qis.Context(K=K, R=R, precision=prec, max_n=n)
+        ctx.create_instance(J, h)
+        ctx.init_states(0, phi)
+        ctx.iterate(I_)
+        lists.append([ctx.search_list(0, r) for r in range(R)])
+        ctx.close()
+    for a, b in zip(*lists):
+        assert_list_equal(a, b)
