@@ -258,7 +258,7 @@ def roofline(res, pk):
     clk = pk.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * clk * 1e6 / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan32",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan_pairs",
             "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch}
 
 

@@ -61,7 +61,7 @@ typedef struct {
   int precision;     /* QIS_FP64 | QIS_SPLIT_BF16 | QIS_PM1_FP8 */
   int max_n;         /* largest n of any instance added to this context (2 <= n <= 4096) */
   int max_instances; /* capacity of the instance table */
-  int survivor_cap;  /* per-search candidate buffer (0 = default 4096) */
+  int survivor_cap;  /* per-search candidate buffer (0 = default 2048) */
   int device;        /* CUDA device ordinal */
   uint64_t seed;     /* key of the library's SplitMix64 stream for random initial states */
 } qis_config;

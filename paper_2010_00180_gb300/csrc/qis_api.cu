@@ -188,7 +188,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   if (cfg->max_instances < 1) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_instances must be >= 1");
   if (cfg->precision != QIS_FP64 && cfg->precision != QIS_SPLIT_BF16 && cfg->precision != QIS_PM1_FP8)
     return fail(nullptr, QIS_ERR_INVALID_ARG, "unknown precision mode");
-  int cap = cfg->survivor_cap ? cfg->survivor_cap : 4096;
+  int cap = cfg->survivor_cap ? cfg->survivor_cap : 2048;
   if (cap < 4 * (cfg->K + 1) + 64 || cap > 16384)
     return fail(nullptr, QIS_ERR_INVALID_ARG, "survivor_cap must be in [4(K+1)+64, 16384]");
   {
@@ -275,6 +275,10 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
       ALLOC(P.a64, B * NP);
     }
     ALLOC(P.thr32, B);
+    if (ctx->mode != QIS_FP64) {
+      ALLOC(P.cs32, B * NP);
+      ALLOC(P.sctl, B);
+    }
     ALLOC(P.thrE, B);
     ALLOC(P.capE, B);
     ALLOC(P.surv_cnt, B);

@@ -66,6 +66,8 @@ struct DevPtrs {
   float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
+  float2* cs32;           // [b][NP] {fl32(thr - a_i), s_i}: the scan's per-row bound (split modes)
+  float4* sctl;           // [b] {thr, active, 0, 0}: staged by the scan with the row data
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
   int* surv_cnt;          // [b]
@@ -116,6 +118,21 @@ __device__ inline unsigned long long dkey(double x) {
   x = x + 0.0;  // -0.0 -> +0.0
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
   return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__host__ __device__ inline int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// FP64 energy change of the pair flip (i, j): (a_i + a_j) + 4 s_i s_j J_ij, the product exact
+__device__ inline double dE64(double ai, double aj, double j, int flip) {
+  return __dadd_rn(__dadd_rn(ai, aj), flip ? -4.0 * j : 4.0 * j);
+}
+
+__device__ inline double dkey_inv(unsigned long long k) {
+  return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.

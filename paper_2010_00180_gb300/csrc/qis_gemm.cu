@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CU
           long long aq = 0;
           float2 as = make_float2(0.f, 0.f);
           if (i < d.n) {
-            const int sg = (int)((P.par_bits[(long long)b * P.Wmax + (i >> 6)] >> (i & 63)) & 1ull);
+            const int sg = __half2float(P.S16[(long long)b * P.NP + i]) < 0.f;   // coalesced over i
             aq = sg ? 2 * acc[u] : -2 * acc[u];
             as = make_float2((float)ldexp((double)aq, -d.q), sg ? -1.f : 1.f);
           }
@@ -266,9 +266,11 @@ int gemm_tile_n(int R, int digits) {
   return nt;
 }
 
+// Three stages when two CTAs still fit on an SM, else two (two CTAs per SM let one CTA's
+// epilogue overlap the other's loads).
 int gemm_stages(int digits, int nt) {
   const size_t per = (size_t)digits * kTileBytesA + (size_t)nt * kKC * 2;
-  return (3 * per + 1024 <= 200 * 1024) ? 3 : 2;
+  return (3 * per + 1024 <= 110 * 1024) ? 3 : 2;
 }
 
 size_t gemm_smem(int digits, int nt) {

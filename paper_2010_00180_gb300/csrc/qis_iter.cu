@@ -171,17 +171,6 @@ cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- helpers
-__device__ inline int next_pow2(int x) {
-  int p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
-__device__ inline double dE64(double ai, double aj, double j, int flip) {
-  // (a_i + a_j) + 4 s_i s_j J_ij; the product 4 s_i s_j J_ij is exact
-  return __dadd_rn(__dadd_rn(ai, aj), flip ? -4.0 * j : 4.0 * j);
-}
-
 __device__ inline unsigned fkey(float x) {
   x = x + 0.f;
   const unsigned u = __float_as_uint(x);
@@ -190,8 +179,37 @@ __device__ inline unsigned fkey(float x) {
 __device__ inline float fkey_inv(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
-__device__ inline double dkey_inv(unsigned long long k) {
-  return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+
+// Warp-parallel search of a 256-bin histogram: the bin holding the rank-th element (0-based),
+// and the rank of that element within the bin. Called by one full warp.
+__device__ inline void find_bin(const int* hist, int rank, int& bin, int& within) {
+  const int lane = threadIdx.x & 31;
+  int loc[8], s = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    loc[u] = hist[lane * 8 + u];
+    s += loc[u];
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, incl > rank);
+  const int L = m ? __ffs(m) - 1 : 31;
+  int r = rank - __shfl_sync(0xffffffffu, incl - s, L);
+  int bb = 255;
+  if (lane == L) {
+    int u = 0;
+    for (; u < 7; ++u) {
+      if (r < loc[u]) break;
+      r -= loc[u];
+    }
+    bb = L * 8 + u;
+  }
+  bin = __shfl_sync(0xffffffffu, bb, L);
+  within = __shfl_sync(0xffffffffu, r, L);
 }
 
 // Block-wide radix select: the rank-th smallest (0-based) of `cnt` keys in smem, 8 bits per
@@ -210,14 +228,13 @@ __device__ K radix_select(const K* keys, int cnt, int rank, int* hist) {
       if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255)], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int r = rank, dgt = 0;
-      for (; dgt < 255; ++dgt) {
-        if (r < hist[dgt]) break;
-        r -= hist[dgt];
+    if (threadIdx.x < 32) {
+      int dgt, r;
+      find_bin(hist, rank, dgt, r);
+      if (threadIdx.x == 0) {
+        s_prefix = prefix | ((K)dgt << shift);
+        s_rank = r;
       }
-      s_prefix = prefix | ((K)dgt << shift);
-      s_rank = r;
     }
     __syncthreads();
     prefix = s_prefix;
@@ -235,7 +252,10 @@ constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
 __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) {
-    if (threadIdx.x == 0) P.surv_cnt[b] = 0;
+    if (threadIdx.x == 0) {
+      P.surv_cnt[b] = 0;
+      if (P.mode != QIS_FP64) P.sctl[b] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
+    }
     return;
   }
   const InstDesc d = P.inst[b / P.R];
@@ -310,13 +330,10 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
       atomicAdd(&hist[min(255, (int)((a - amin) * scale))], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int c = 0, bin = 0;
-      for (; bin < 256; ++bin) {
-        c += hist[bin];
-        if (c >= m) break;
-      }
-      s_bin = min(bin, 255);
+    if (threadIdx.x < 32) {
+      int bin, within;
+      find_bin(hist, min(m, n) - 1, bin, within);   // bin of the m-th lowest a_i
+      if (threadIdx.x == 0) s_bin = bin;
     }
     __syncthreads();
     const int bin = s_bin;
@@ -380,9 +397,16 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
       const double t2 = U + 2.0 * delta;
       s_thr = fl32_up(fmin(t1, t2));
       P.thr32[b] = s_thr;
+      P.sctl[b] = make_float4(s_thr, 1.f, 0.f, 0.f);
     }
   }
   __syncthreads();
+  if (!fp64) {
+    // per-row bound of the pair scan: c_i = fl32(thr - a_i), with the row spin
+    float2* cs = P.cs32 + (long long)b * P.NP;
+    for (int i = threadIdx.x; i < d.n_pad; i += blockDim.x)
+      cs[i] = (i < n) ? make_float2(s_thr - as[i].x, as[i].y) : make_float2(0.f, 1.f);
+  }
   // single flips: dE_i = a_i
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     bool ok;
@@ -463,265 +487,4 @@ cudaError_t launch_scan64(const DevPtrs& P, const int4* work, int n_work, cudaSt
 }
 
 // ---------------------------------------------------------------- exact merge (Alg. 2)
-// Block-wide exclusive scan of 0/1 flags f[0..cnt) into pos[], returns the total.
-__device__ int block_scan_flags(const int* f, int* pos, int cnt, int* tmp /* [blockDim] */) {
-  const int per = (cnt + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per, hi = min(cnt, lo + per);
-  int s = 0;
-  for (int t = lo; t < hi; ++t) s += f[t] ? 1 : 0;
-  tmp[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const int v = tmp[t];
-      tmp[t] = acc;
-      acc += v;
-    }
-    tmp[blockDim.x] = acc;
-  }
-  __syncthreads();
-  int p = tmp[threadIdx.x];
-  for (int t = lo; t < hi; ++t) {
-    pos[t] = p;
-    p += f[t] ? 1 : 0;
-  }
-  const int total = tmp[blockDim.x];
-  __syncthreads();
-  return total;
-}
-
-template <typename K>
-__device__ void bitonic_sort(K* key, uint32_t* val, int n2) {
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
-        const int u = t ^ j;
-        if (u > t) {
-          const K a = key[t], c = key[u];
-          const uint32_t va = val[t], vc = val[u];
-          const bool gt = (a > c) || (a == c && va > vc);
-          const bool up = (t & k) == 0;
-          if (gt == up) {
-            key[t] = c; key[u] = a;
-            val[t] = vc; val[u] = va;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Shared layout (dynamic): old list [K1] {E, hash, slot}, survivors [P2] {key, cand},
-// occupancy / free list / positions [K1] each.
-__global__ void __launch_bounds__(256) k_merge(DevPtrs P) {
-  const int b = blockIdx.x;
-  if (!P.active[b]) return;
-  const InstDesc d = P.inst[b / P.R];
-  const int n = d.n, W = d.W, K1 = P.K1;
-  const long long base = (long long)b * K1;
-  const int S = P.surv_cnt[b];
-  if (S > P.cap) {
-    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
-    return;
-  }
-  extern __shared__ unsigned char smem[];
-  const int PC = next_pow2(P.cap);                              // sort capacity
-  double* oE = reinterpret_cast<double*>(smem);                 // [K1]
-  uint64_t* oH = reinterpret_cast<uint64_t*>(oE + K1);          // [K1]
-  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);   // [PC]
-  uint32_t* sc = reinterpret_cast<uint32_t*>(sk + PC);          // [PC]
-  int* oslot = reinterpret_cast<int*>(sc + PC);                 // [K1]
-  int* occ = oslot + K1;                                        // [K1] rank+1 of the kept old entry in a slot
-  int* freef = occ + K1;                                        // [K1] slot is free
-  int* fpos = freef + K1;                                       // [K1] position among free slots
-  int* freel = fpos + K1;                                       // [K1] free slots in order
-  __shared__ uint64_t pb[kMaxN / 64];
-  __shared__ int s_nvalid, s_nc;
-  __shared__ int tmp[257];
-  const int cnt = P.lst_count[b];
-  const double T = (cnt == K1) ? P.lst_E[base + P.lst_ord[base + K1 - 1]] : INFINITY;
-  const double Ep = P.par_E[b];
-  const uint64_t ph = P.par_hash[b];
-  const bool fp64 = P.mode == QIS_FP64;
-  for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
-  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-    const int slot = P.lst_ord[base + r];
-    oslot[r] = slot;
-    oE[r] = P.lst_E[base + slot];
-    oH[r] = P.lst_hash[base + slot];
-  }
-  for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
-  if (threadIdx.x == 0) {
-    s_nvalid = 0;
-    s_nc = 0;
-  }
-  __syncthreads();
-  // expand scan records into candidate indices, re-applying the scan's FP32 test verbatim
-  {
-    const float2* as = P.as32 + (long long)b * P.NP;
-    const float thr = fp64 ? 0.f : P.thr32[b];
-    for (int t = threadIdx.x; t < S; t += blockDim.x) {
-      const unsigned long long e = P.surv[(long long)b * P.cap + t];
-      if (!(e >> 63)) {
-        const int slot = atomicAdd(&s_nc, 1);
-        if (slot < P.cap) sc[slot] = (uint32_t)e;
-        continue;
-      }
-      const int i0 = (int)(e & 0xffff), jb = (int)((e >> 16) & 0xffff);
-      const int nc = (int)((e >> 32) & 0xf);
-      const unsigned hm = (unsigned)((e >> 36) & 0xff);
-      for (int r = 0; r < 8; ++r) {
-        if (!((hm >> r) & 1u)) continue;
-        const int i = i0 + r;
-        const float2 ri = as[i];
-        const float c = thr - ri.x;
-        for (int k = 0; k < nc; ++k) {
-          const int j = jb + 32 * k;
-          if (j <= i || j >= n) continue;
-          const float2 vj = as[j];
-          const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
-          const float y = fmaf(ri.y < 0.f ? -j4 : j4, vj.y, vj.x);
-          if (y <= c) {
-            const int slot = atomicAdd(&s_nc, 1);
-            if (slot < P.cap) sc[slot] = pair_index(n, i, j);
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (s_nc > P.cap) {
-    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
-    return;
-  }
-  const int NCAND = s_nc;
-  const int P2 = next_pow2(max(NCAND, 1));
-  const long long Epq = fp64 ? 0 : __double2ll_rn(ldexp(Ep, d.q));
-  const long long Tq = (fp64 || T == INFINITY) ? LLONG_MAX : __double2ll_rn(ldexp(T, d.q));
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    unsigned long long kk = ~0ull;
-    uint32_t c = 0xffffffffu;
-    if (t < NCAND) {
-      c = sc[t];
-      int i, j;
-      decode_candidate(n, c, i, j);
-      const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
-      double e;
-      bool keep;
-      if (fp64) {
-        const double* a = P.a64 + (long long)b * P.NP;
-        const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
-        e = __dadd_rn(Ep, de);
-        keep = e < T;
-      } else {
-        const long long* aq = P.aq + (long long)b * P.NP;
-        long long de = aq[i];
-        if (j >= 0) {
-          const long long jq = P.Jq[d.off_mat + (long long)i * d.n_pad + j];
-          de += aq[j] + ((si ^ sj) ? -4 * jq : 4 * jq);
-        }
-        const long long eq = Epq + de;
-        keep = eq < Tq;
-        e = ldexp((double)eq, -d.q);
-      }
-      if (keep) {
-        const uint64_t hsh = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
-        for (int r = 0; r < cnt && keep; ++r) {
-          if (oH[r] != hsh) continue;
-          const uint64_t* sbits = P.lst_bits + (base + oslot[r]) * P.Wmax;
-          bool same = true;
-          for (int x = 0; x < W && same; ++x) {
-            uint64_t m = 0;
-            if ((i >> 6) == x) m ^= 1ull << (i & 63);
-            if (j >= 0 && (j >> 6) == x) m ^= 1ull << (j & 63);
-            same = sbits[x] == (pb[x] ^ m);
-          }
-          if (same) keep = false;   // duplicate of a kept state (Alg. 2 binary search hit)
-        }
-      }
-      if (keep) {
-        kk = dkey(e);
-        atomicAdd(&s_nvalid, 1);
-      } else {
-        c = 0xffffffffu;
-      }
-    }
-    sk[t] = kk;
-    sc[t] = c;
-  }
-  __syncthreads();
-  bitonic_sort(sk, sc, P2);
-  const int nv = s_nvalid;
-  // ranks: old entry o -> o + #(new with E < E_o); new entry p -> p + #(old with E <= E_p)
-  // (new stamps exceed every old stamp, and among new entries c orders the stamps)
-  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
-    const unsigned long long ko = dkey(oE[o]);
-    int lo = 0, hi = nv;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (sk[mid] < ko) lo = mid + 1; else hi = mid;
-    }
-    const int rank = o + lo;
-    if (rank < K1) occ[oslot[o]] = 1 + rank;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < K1; k += blockDim.x) freef[k] = occ[k] == 0;
-  __syncthreads();
-  block_scan_flags(freef, fpos, K1, tmp);
-  for (int k = threadIdx.x; k < K1; k += blockDim.x)
-    if (freef[k]) freel[fpos[k]] = k;
-  __syncthreads();
-  const int t_now = P.iter_t[b];
-  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
-    const unsigned long long kp = sk[p];
-    int lo = 0, hi = cnt;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (dkey(oE[mid]) <= kp) lo = mid + 1; else hi = mid;
-    }
-    const int rank = p + lo;
-    if (rank >= K1) continue;
-    const int slot = freel[p];   // new entries kept are exactly the first ones in sorted order
-    const uint32_t c = sc[p];
-    int i, j;
-    decode_candidate(n, c, i, j);
-    uint64_t* dst = P.lst_bits + (base + slot) * P.Wmax;
-    for (int x = 0; x < W; ++x) {
-      uint64_t m = 0;
-      if ((i >> 6) == x) m ^= 1ull << (i & 63);
-      if (j >= 0 && (j >> 6) == x) m ^= 1ull << (j & 63);
-      dst[x] = pb[x] ^ m;
-    }
-    P.lst_E[base + slot] = dkey_inv(kp);
-    P.lst_stamp[base + slot] = ((uint64_t)t_now << 32) | c;
-    P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
-    P.lst_used[base + slot] = 0;
-    P.lst_ord[base + rank] = slot;
-  }
-  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
-    const int slot = oslot[o];
-    if (occ[slot]) P.lst_ord[base + occ[slot] - 1] = slot;
-  }
-  if (threadIdx.x == 0) P.lst_count[b] = min(K1, cnt + nv);
-}
-
-size_t merge_smem(int K1, int cap) {
-  int P2 = 1;
-  while (P2 < cap) P2 <<= 1;
-  return (size_t)K1 * (8 + 8) + (size_t)P2 * (8 + 4) + (size_t)K1 * 4 * 5;
-}
-
-cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = merge_smem(P.K1, P.cap);
-  static size_t attr = 0;
-  if (attr < sm) {
-    cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = sm;
-  }
-  k_merge<<<P.B, 256, sm, s>>>(P);
-  return cudaGetLastError();
-}
-
 }  // namespace qis

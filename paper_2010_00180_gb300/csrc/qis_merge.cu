@@ -1,0 +1,297 @@
+// qis_merge.cu -- the exact list update of one iteration (Alg. 2), one block per search.
+//
+// Input: the survivor buffer of the search (single flips from k_bound, pair-hit records from
+// the FP32 scan, or plain pair indices from the FP64 scan). Output: the new kept list.
+//
+//  1. Records are expanded with the scan's own FP32 test, so exactly the pairs the filter
+//     passed become candidates.
+//  2. Every candidate gets its exact energy: in the split modes from exact fixed-point
+//     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), in the FP64 mode with the
+//     defining FP64 arithmetic. Candidates with E' >= T (the last kept energy, Alg. 2: strict
+//     <) are dropped, as are duplicates of a kept state (Zobrist hash table + full compare:
+//     the binary search of Alg. 2).
+//  3. New list = first K+1 of (old list, new candidates) by (E, stamp): old entries precede
+//     new ones of equal energy (they arrived earlier), new ones are ordered by candidate
+//     index c (the order of the Alg. 3 loop). Slots of evicted entries are reused.
+#include "qis_common.cuh"
+
+namespace qis {
+
+__device__ inline uint32_t hmix(uint64_t h) { return (uint32_t)(h ^ (h >> 29) ^ (h >> 47)); }
+
+// exclusive prefix sum of one int per thread over the block (blockDim multiple of 32)
+__device__ int block_exclusive_sum(int v, int* wsum /* [33] */, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) wsum[lane] = w;   // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+  *total = wsum[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+template <typename K>
+__device__ void bitonic_sort(K* key, uint32_t* val, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          const K a = key[t], c = key[u];
+          const uint32_t va = val[t], vc = val[u];
+          const bool gt = (a > c) || (a == c && va > vc);
+          const bool up = (t & k) == 0;
+          if (gt == up) {
+            key[t] = c; key[u] = a;
+            val[t] = vc; val[u] = va;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ inline uint64_t flip_mask(int x, int i, int j) {
+  uint64_t m = 0;
+  if ((i >> 6) == x) m ^= 1ull << (i & 63);
+  if (j >= 0 && (j >> 6) == x) m ^= 1ull << (j & 63);
+  return m;
+}
+
+constexpr int kMergeThreads = 256;
+
+__global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
+  const int b = blockIdx.x;
+  if (!P.active[b]) return;
+  const InstDesc d = P.inst[b / P.R];
+  const int n = d.n, W = d.W, K1 = P.K1;
+  const long long base = (long long)b * K1;
+  const int S = P.surv_cnt[b];
+  if (S > P.cap) {
+    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
+    return;
+  }
+  const int PC = next_pow2(P.cap);
+  const int HT = next_pow2(2 * K1);
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* okey = reinterpret_cast<unsigned long long*>(smem);   // [K1]
+  uint64_t* oH = reinterpret_cast<uint64_t*>(okey + K1);                    // [K1]
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);  // [PC]
+  uint32_t* sc = reinterpret_cast<uint32_t*>(sk + PC);                      // [PC]
+  int* oslot = reinterpret_cast<int*>(sc + PC);                             // [K1]
+  int* occ = oslot + K1;                                                    // [K1]
+  int* freel = occ + K1;                                                    // [K1]
+  int* htab = freel + K1;                                                   // [HT]
+  __shared__ uint64_t pb[kMaxN / 64];
+  __shared__ int s_nc, s_nvalid, wsum[33], s_total;
+  const int cnt = P.lst_count[b];
+  const double T = (cnt == K1) ? P.lst_E[base + P.lst_ord[base + K1 - 1]] : INFINITY;
+  const double Ep = P.par_E[b];
+  const uint64_t ph = P.par_hash[b];
+  const bool fp64 = P.mode == QIS_FP64;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
+  for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = -1;
+  for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
+  if (threadIdx.x == 0) {
+    s_nc = 0;
+    s_nvalid = 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    const int slot = P.lst_ord[base + r];
+    oslot[r] = slot;
+    okey[r] = dkey(P.lst_E[base + slot]);
+    const uint64_t h = P.lst_hash[base + slot];
+    oH[r] = h;
+    uint32_t pos = hmix(h) & (HT - 1);
+    while (atomicCAS(&htab[pos], -1, r) != -1) pos = (pos + 1) & (HT - 1);
+  }
+  // ---- 1. expand scan records into candidates (the scan's FP32 test, verbatim)
+  {
+    const float2* as = P.as32 + (long long)b * P.NP;
+    const unsigned long long* sv = P.surv + (long long)b * P.cap;
+    for (int t = threadIdx.x; t < S; t += blockDim.x) {
+      const unsigned long long e = sv[t];
+      if (!(e >> 63)) {
+        const int slot = atomicAdd(&s_nc, 1);
+        if (slot < PC) sc[slot] = (uint32_t)e;
+        continue;
+      }
+      // record: rows i0 + r for the bits r of hm; columns jb + 32k, k < nc
+      const int i0 = (int)(e & 0xffff), jb = (int)((e >> 16) & 0xffff);
+      const int nc = (int)((e >> 32) & 0x1f);
+      unsigned hm = (unsigned)((e >> 37) & 0xff);
+      const float2* cs = P.cs32 + (long long)b * P.NP;
+      while (hm) {
+        const int r = __ffs(hm) - 1;
+        hm &= hm - 1;
+        const int i = i0 + r;
+        const float2 ri = cs[i];                 // {thr - a_i, s_i}, the scan's row bound
+        const float* J4row = P.J4 + d.off_mat + (long long)i * d.n_pad;
+        float y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int j = jb + 32 * k;
+          y[k] = __int_as_float(0x7fc00000);   // NaN: never <= c, even when c = +inf
+          if (k < nc && j > i && j < n) {
+            const float2 vj = as[j];
+            const float j4 = J4row[j];
+            y[k] = fmaf(ri.y < 0.f ? -j4 : j4, vj.y, vj.x);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (y[k] <= ri.x) {
+            const int slot = atomicAdd(&s_nc, 1);
+            if (slot < PC) sc[slot] = pair_index(n, i, jb + 32 * k);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int NCAND = s_nc;
+  if (NCAND > PC) {
+    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
+    return;
+  }
+  const int P2 = next_pow2(max(NCAND, 1));
+  // ---- 2. exact energies, threshold, duplicates
+  const long long Epq = fp64 ? 0 : __double2ll_rn(ldexp(Ep, d.q));
+  const long long Tq = (fp64 || T == INFINITY) ? LLONG_MAX : __double2ll_rn(ldexp(T, d.q));
+  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+    unsigned long long kk = ~0ull;
+    uint32_t c = 0xffffffffu;
+    if (t < NCAND) {
+      c = sc[t];
+      int i, j;
+      decode_candidate(n, c, i, j);
+      const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
+      double e;
+      bool keep;
+      if (fp64) {
+        const double* a = P.a64 + (long long)b * P.NP;
+        const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
+        e = __dadd_rn(Ep, de);
+        keep = e < T;
+      } else {
+        const long long* aq = P.aq + (long long)b * P.NP;
+        long long de = aq[i];
+        if (j >= 0) {
+          const long long jq = P.Jq[d.off_mat + (long long)i * d.n_pad + j];
+          de += aq[j] + ((si ^ sj) ? -4 * jq : 4 * jq);
+        }
+        const long long eq = Epq + de;
+        keep = eq < Tq;
+        e = ldexp((double)eq, -d.q);
+      }
+      if (keep) {
+        const uint64_t hsh = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
+        uint32_t pos = hmix(hsh) & (HT - 1);
+        for (int r = htab[pos]; r >= 0 && keep; pos = (pos + 1) & (HT - 1), r = htab[pos]) {
+          if (oH[r] != hsh) continue;
+          const uint64_t* sbits = P.lst_bits + (base + oslot[r]) * P.Wmax;
+          bool same = true;
+          for (int x = 0; x < W && same; ++x) same = sbits[x] == (pb[x] ^ flip_mask(x, i, j));
+          if (same) keep = false;   // duplicate of a kept state (Alg. 2 binary search hit)
+        }
+      }
+      if (keep) {
+        kk = dkey(e);
+        atomicAdd(&s_nvalid, 1);
+      } else {
+        c = 0xffffffffu;
+      }
+    }
+    sk[t] = kk;
+    sc[t] = c;
+  }
+  __syncthreads();
+  // ---- 3. order and truncate
+  bitonic_sort(sk, sc, P2);
+  const int nv = s_nvalid;
+  // old entry o -> rank o + #(new with E < E_o); new entry p -> p + #(old with E <= E_p)
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    const unsigned long long ko = okey[o];
+    int lo = 0, hi = nv;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sk[mid] < ko) lo = mid + 1; else hi = mid;
+    }
+    const int rank = o + lo;
+    if (rank < K1) occ[oslot[o]] = 1 + rank;
+  }
+  __syncthreads();
+  // free slots in slot order (contiguous chunk per thread)
+  const int per = (K1 + blockDim.x - 1) / blockDim.x;
+  const int lo_k = threadIdx.x * per, hi_k = min(K1, lo_k + per);
+  int nfree = 0;
+  for (int k = lo_k; k < hi_k; ++k) nfree += occ[k] == 0;
+  int pos = block_exclusive_sum(nfree, wsum, &s_total);
+  for (int k = lo_k; k < hi_k; ++k)
+    if (occ[k] == 0) freel[pos++] = k;
+  __syncthreads();
+  const int t_now = P.iter_t[b];
+  for (int p = threadIdx.x; p < nv; p += blockDim.x) {
+    const unsigned long long kp = sk[p];
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (okey[mid] <= kp) lo = mid + 1; else hi = mid;
+    }
+    const int rank = p + lo;
+    if (rank >= K1) continue;
+    const int slot = freel[p];   // the new entries kept are the first ones in sorted order
+    const uint32_t c = sc[p];
+    int i, j;
+    decode_candidate(n, c, i, j);
+    uint64_t* dst = P.lst_bits + (base + slot) * P.Wmax;
+    for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
+    P.lst_E[base + slot] = dkey_inv(kp);
+    P.lst_stamp[base + slot] = ((uint64_t)t_now << 32) | c;
+    P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
+    P.lst_used[base + slot] = 0;
+    P.lst_ord[base + rank] = slot;
+  }
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    const int slot = oslot[o];
+    if (occ[slot]) P.lst_ord[base + occ[slot] - 1] = slot;
+  }
+  if (threadIdx.x == 0) P.lst_count[b] = min(K1, cnt + nv);
+}
+
+size_t merge_smem(int K1, int cap) {
+  const int PC = next_pow2(cap), HT = next_pow2(2 * K1);
+  return (size_t)K1 * 16 + (size_t)PC * 12 + (size_t)K1 * 12 + (size_t)HT * 4;
+}
+
+cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
+  const size_t sm = merge_smem(P.K1, P.cap);
+  static size_t attr = 0;
+  if (attr < sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
+  }
+  k_merge<<<P.B, kMergeThreads, sm, s>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace qis

@@ -2,24 +2,27 @@
 //
 // Pair candidates (i, j), i < j, of one parent: dE_ij = a_i + a_j + 4 s_i s_j J_ij (Sec. III,
 // energy change from the couplings of the flipped sites). A pair survives the filter when
-// dE~_ij <= thr (per search; k_bound derives thr and the error band it carries).
+//     y_ij = a_j + (s_i s_j) 4J~_ij  <=  c_i = thr - a_i
+// where k_bound derives thr with its error band and writes c_i per site.
 //
 // Work unit = one block task: 32 consecutive rows i (4 warps x 8 rows) and a chunk of 32*NC
 // columns j of one instance, for all R searches of that instance. Each lane keeps its 8 x NC
 // couplings 4J~_ij in registers and reuses them for every search; lane l owns columns
-// c0 + 32k + l. The per-search data -- {a_j, s_j} of the chunk's columns and of the block's
-// rows -- is staged into shared memory with cp.async, one search ahead (double buffer).
+// c0 + 32k + l, so every coupling load is a coalesced 128-byte row segment. Per search the
+// block stages {a_j, s_j} of the chunk's columns, {c_i, s_i} of its rows and {thr, active} with
+// cp.async, two searches ahead (triple buffer, one block barrier per search).
 //
-// Per search and row i (warp-uniform), each lane evaluates
-//     y_ij = a_j + (s_i s_j) 4J~_ij  = fma(+-4J~_ij, s_j, a_j)
-// where the row spin picks the sign of the coupling operand (uniform branch), reduces
-// min_j y_ij with three-input minima and tests it against thr - a_i. Pairs that must not be
+// Per search and row (warp-uniform) each lane computes y_ij = fma(+-4J~_ij, s_j, a_j) -- the
+// row spin, taken from a ballot so the branch is provably uniform, picks the operand sign --
+// reduces min_j y_ij with three-input minima and compares it with c_i. Pairs that must not be
 // evaluated (j <= i, j >= n) hold NaN couplings: the FMA propagates NaN and min ignores it.
-// A lane whose rows hit appends one record {rows, its columns, row mask}; the merge expands
-// it with the same FP32 test, so the filter decision is identical in both places.
+// A lane whose rows hit appends one record {rows, its columns, row mask}; the merge expands it
+// with the same FP32 test, so the filter decision is identical in both places.
 #include "qis_common.cuh"
 
 namespace qis {
+
+constexpr int kBufs = 3;   // staging depth: search s is computed while s+1, s+2 land
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
@@ -37,9 +40,7 @@ __device__ __forceinline__ float rowmin(const float (&y)[NC]) {
     return min3f(y[0], y[1], fminf(y[2], y[3]));
   } else {
     static_assert(NC == 8, "chunk widths 32, 64, 128, 256");
-    const float t0 = min3f(y[0], y[1], y[2]);
-    const float t1 = min3f(y[3], y[4], y[5]);
-    return min3f(t0, t1, fminf(y[6], y[7]));
+    return min3f(min3f(y[0], y[1], y[2]), min3f(y[3], y[4], y[5]), fminf(y[6], y[7]));
   }
 }
 
@@ -52,20 +53,29 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Record layout of a scan hit (bit 63 set): bits 0-15 first row of the lane's 8 rows,
-// bits 16-31 column of k = 0, bits 32-35 NC, bits 36-43 mask of the rows that hit.
+// Record layout of a scan hit (bit 63 set): bits 0-15 first of the lane's 8 rows, bits 16-31
+// the lane's first column jb (its columns are jb + 32k, k < NC), bits 32-36 NC, bits 37-44
+// mask of the rows that hit.
 __host__ __device__ inline unsigned long long make_record(int i0, int jb, int nc, unsigned hm) {
   return (1ull << 63) | (unsigned long long)(unsigned)i0 | ((unsigned long long)(unsigned)jb << 16) |
-         ((unsigned long long)(unsigned)nc << 32) | ((unsigned long long)(hm & 0xffu) << 36);
+         ((unsigned long long)(unsigned)nc << 32) | ((unsigned long long)(hm & 0xffu) << 37);
 }
 
+struct ScanSmem {
+  float2 col[kBufs][256];   // {a_j, s_j}
+  float2 row[kBufs][32];    // {c_i, s_i}
+  float4 ctl[kBufs];        // {thr, active, -, -}
+};
+
 template <int NC>
-__device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, int row0, int c0) {
-  __shared__ __align__(16) float2 colbuf[2][256];
-  __shared__ __align__(16) float2 rowbuf[2][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = d.n, np = d.n_pad;
+__device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, int row0, int c0, ScanSmem& sm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+  const int n = d.n, np = d.n_pad, R = P.R, NPs = P.NP, cap = P.cap;
+  const int b0 = d.first_search;
   const float* J4 = P.J4 + d.off_mat;
+  const float2* as_base = P.as32;
+  const float2* cs_base = P.cs32;
+  const float4* ctl_base = P.sctl;
   const float qnan = __int_as_float(0x7fc00000);
   const int i0 = row0 + warp * 8;
   float J[8][NC];
@@ -78,32 +88,32 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       J[r][k] = (i < n && j < n && j > i) ? J4[(long long)i * np + j] : qnan;
     }
   }
-  // stage search s into buffer s & 1 (columns: 16 bytes = 2 sites per thread; rows: 16 threads)
-  auto stage = [&](int s) {
-    const int b = d.first_search + s;
-    const float2* as = P.as32 + (long long)b * P.NP;
-    const int t = threadIdx.x;
-    if (t < 16 * NC) {
-      const int col = c0 + 2 * t;
-      cp_async16(&colbuf[s & 1][2 * t], as + min(col, P.NP - 2), col < P.NP);
-    }
-    if (t < 16) cp_async16(&rowbuf[s & 1][2 * t], as + row0 + 2 * t, true);
+  // stage search s into buffer q: columns (16 bytes = 2 sites per thread), rows (16 threads),
+  // {thr, active} (one thread)
+  const int col = c0 + 2 * t;
+  auto stage = [&](int s, int q) {
+    const long long b = b0 + s;
+    if (t < 16 * NC) cp_async16(&sm.col[q][2 * t], as_base + b * NPs + min(col, NPs - 2), col < NPs);
+    if (t < 16) cp_async16(&sm.row[q][2 * t], cs_base + b * NPs + row0 + 2 * t, true);
+    if (t == 16) cp_async16(&sm.ctl[q], ctl_base + b, true);
     cp_async_commit();
   };
-  stage(0);
-  for (int s = 0; s < P.R; ++s) {
-    const int b = d.first_search + s;
-    if (s + 1 < P.R) {
-      stage(s + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+  stage(0, 0);
+  if (R > 1) stage(1, 1);
+  int q = 0;
+  for (int s = 0; s < R; ++s) {
+    // own copies of search s complete (s+1 may still be in flight); the barrier makes every
+    // thread's copies visible and guarantees that all warps have left iteration s-1, whose
+    // buffer (s+2) % 3 is restaged right after
+    if (s + 1 < R) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncthreads();
-    if (P.active[b]) {
-      const float thr = P.thr32[b];
-      const float2* cb = colbuf[s & 1];
-      const float2* rb = rowbuf[s & 1] + warp * 8;
+    if (s + 2 < R) stage(s + 2, q == 0 ? 2 : q - 1);
+    const float4 ctl = sm.ctl[q];
+    if (__any_sync(0xffffffffu, ctl.y != 0.f)) {   // vote result: uniform branch
+      const float2* cb = sm.col[q];
+      const float2 rv = sm.row[q][warp * 8 + (lane & 7)];
+      const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
       float aj[NC], sj[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -114,41 +124,44 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       unsigned hm = 0;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 ri = rb[r];                 // {a_i, s_i}, same for every lane
+        const float c = __shfl_sync(0xffffffffu, rv.x, r);
         float y[NC];
-        if (ri.y < 0.f) {
+        if ((smask >> r) & 1u) {
 #pragma unroll
           for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], aj[k]);
         } else {
 #pragma unroll
           for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
         }
-        if (rowmin<NC>(y) <= thr - ri.x) hm |= 1u << r;
+        if (rowmin<NC>(y) <= c) hm |= 1u << r;
       }
       const unsigned hit = __ballot_sync(0xffffffffu, hm != 0);
       if (hit) {
+        const int b = b0 + s;
+        const int leader = __ffs(hit) - 1;
         int base = 0;
-        if (lane == __ffs(hit) - 1) base = atomicAdd(P.surv_cnt + b, __popc(hit));
-        base = __shfl_sync(0xffffffffu, base, __ffs(hit) - 1);
+        if (lane == leader) base = atomicAdd(P.surv_cnt + b, __popc(hit));
+        base = __shfl_sync(0xffffffffu, base, leader);
         if (hm) {
           const int slot = base + __popc(hit & ((1u << lane) - 1));
-          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = make_record(i0, c0 + lane, NC, hm);
+          if (slot < cap) P.surv[(long long)b * cap + slot] = make_record(i0, c0 + lane, NC, hm);
         }
       }
     }
-    __syncthreads();   // buffer s & 1 is restaged by iteration s + 1
+    q = (q == kBufs - 1) ? 0 : q + 1;
   }
 }
 
 // task.x = instance, task.y = first row of the 32-row block, task.z = first column, task.w = NC
 __global__ void __launch_bounds__(128, 4) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks) {
+  __shared__ __align__(16) ScanSmem sm;
   const int4 w = tasks[blockIdx.x];
   const InstDesc d = P.inst[w.x];
   switch (w.w) {
-    case 8: scan_task<8>(P, d, w.y, w.z); break;
-    case 4: scan_task<4>(P, d, w.y, w.z); break;
-    case 2: scan_task<2>(P, d, w.y, w.z); break;
-    default: scan_task<1>(P, d, w.y, w.z); break;
+    case 8: scan_task<8>(P, d, w.y, w.z, sm); break;
+    case 4: scan_task<4>(P, d, w.y, w.z, sm); break;
+    case 2: scan_task<2>(P, d, w.y, w.z, sm); break;
+    default: scan_task<1>(P, d, w.y, w.z, sm); break;
   }
 }
 
