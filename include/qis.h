@@ -160,6 +160,32 @@ int qis_get_stream(qis_ctx* ctx, void** stream);
 int qis_profile_enable(qis_ctx* ctx, int on);
 int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches);
 
+/* ------------------------------------------------------------------------------------------
+ * Allocation-free candidate selection (the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory when they need the work done: code running
+ * while a stream is being captured into a CUDA graph, real-time loops that must not block in
+ * the driver's allocator, plugins whose process owns device memory through another pool).
+ *
+ * For one parent state psi of an n-spin instance it evaluates every single flip and every
+ * pair flip with the library's FP64 arithmetic (E' = E(psi) + dE, as in QIS_FP64) and writes
+ * the k candidates of lowest (E', c), ascending, c the candidate index of the conventions
+ * above. Unlike every other entry point, all pointers here are DEVICE pointers owned by the
+ * caller:
+ *   J      n*n FP64 row-major (symmetric, zero diagonal; not validated here)
+ *   h      n FP64
+ *   bits   ceil(n/64) words of the parent state
+ *   E_out  k FP64 energies, c_out k candidate indices, Ep_out (may be NULL) E(psi)
+ *   stream a cudaStream_t (NULL = legacy default stream); the call is asynchronous on it.
+ * Limits: 2 <= n <= 512, 1 <= k <= min(128, n(n+1)/2); larger sizes return
+ * QIS_ERR_INVALID_ARG (message in qis_last_error(NULL)). No device memory is allocated:
+ * the scratch space (about 100 KB) is a static array of the library that every GPU which
+ * loads the library holds until the process exits. The first call on a device looks up that
+ * array's device address, so make the first call before any stream capture. All calls on a
+ * device share the array; calls whose kernels may overlap on the GPU must be ordered by the
+ * caller (same stream or events), or they race. */
+int qis_select_candidates_noalloc(int n, const double* J, const double* h, const uint64_t* bits, int k,
+                                  double* E_out, uint32_t* c_out, double* Ep_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

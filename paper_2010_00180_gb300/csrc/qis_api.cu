@@ -176,6 +176,8 @@ int build_work(qis_ctx* ctx) {
 
 }  // namespace
 
+void qis::set_global_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 int qis_create(const qis_config* cfg, qis_ctx** out) {

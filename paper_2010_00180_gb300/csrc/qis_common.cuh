@@ -135,6 +135,9 @@ __device__ inline double dkey_inv(unsigned long long k) {
   return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
+// Message returned by qis_last_error(NULL) (calls that have no context).
+void set_global_error(const char* msg);
+
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);

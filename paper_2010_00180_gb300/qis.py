@@ -22,7 +22,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "C
 SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_clear_instances",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
-           "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query"]
+           "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
+           "qis_select_candidates_noalloc"]
 KERNEL_CLASSES = ["pick", "fields", "bound", "scan", "merge"]
 
 
@@ -71,6 +72,7 @@ def load():
         "qis_get_stream": (I, [P, C.POINTER(P)]),
         "qis_profile_enable": (I, [P, I]),
         "qis_profile_query": (I, [P, I, C.POINTER(C.c_double), C.POINTER(U64)]),
+        "qis_select_candidates_noalloc": (I, [I, P, P, P, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -86,6 +88,17 @@ def _ptr(a):
 
 def words(n: int) -> int:
     return (n + 63) // 64
+
+
+def select_candidates_noalloc(n: int, J_ptr: int, h_ptr: int, bits_ptr: int, k: int, E_ptr: int, c_ptr: int,
+                              Ep_ptr: int = 0, stream: int = 0) -> None:
+    """qis_select_candidates_noalloc: all pointers are device addresses owned by the caller;
+    the library allocates nothing (its scratch is a static device array)."""
+    lib = load()
+    rc = lib.qis_select_candidates_noalloc(n, J_ptr, h_ptr, bits_ptr, k, E_ptr, c_ptr, Ep_ptr or None,
+                                           stream or None)
+    if rc != 0:
+        raise QISError(rc, lib.qis_last_error(None).decode())
 
 
 class Context:
