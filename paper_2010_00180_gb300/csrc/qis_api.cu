@@ -58,6 +58,8 @@ struct qis_ctx {
   uint64_t launches = 0;
   // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
   bool profiling = false;
+  bool use_graph = true;                    // QIS_NO_GRAPH=1 launches the kernels one by one
+  cudaGraphExec_t graph_exec = nullptr;     // one iteration, captured for the current instances
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
   size_t ev_used[8] = {0};
   std::string err = "no error";
@@ -151,6 +153,35 @@ cudaError_t prof_end(qis_ctx* ctx, int k) {
   return e;
 }
 
+// The five kernels of one iteration of Alg. 3 (each bracketed by timing events when profiling).
+int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
+  const DevPtrs& P = ctx->P;
+  CK(prof_begin(ctx, 0));
+  LAUNCH(launch_pick(P, s));
+  CK(prof_end(ctx, 0));
+  CK(prof_begin(ctx, 1));
+  if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
+  else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
+  else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, s));
+  CK(prof_end(ctx, 1));
+  CK(prof_begin(ctx, 2));
+  LAUNCH(launch_bound(P, s));
+  CK(prof_end(ctx, 2));
+  CK(prof_begin(ctx, 3));
+  if (ctx->mode == QIS_FP64) LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
+  else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, s));
+  CK(prof_end(ctx, 3));
+  CK(prof_begin(ctx, 4));
+  LAUNCH(launch_merge(P, s));
+  CK(prof_end(ctx, 4));
+  return 0;
+}
+
+void drop_graph(qis_ctx* ctx) {
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  ctx->graph_exec = nullptr;
+}
+
 int build_work(qis_ctx* ctx) {
   std::vector<int4> w;
   for (int id = 0; id < (int)ctx->inst.size(); ++id) {
@@ -213,6 +244,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   {
     const char* e = getenv("QIS_FIELDS_SIMT");
     ctx->fields_simt = e && e[0] == '1';
+    const char* g = getenv("QIS_NO_GRAPH");
+    ctx->use_graph = !(g && g[0] == '1');
   }
   auto bail = [&](int rc) {
     g_create_error = ctx->err;
@@ -318,6 +351,7 @@ void qis_destroy(qis_ctx* ctx) {
       cudaEventDestroy(pr.second);
     }
   for (void* p : ctx->allocs) cudaFree(p);
+  drop_graph(ctx);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -404,6 +438,7 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
   ctx->work_dirty = true;
+  drop_graph(ctx);
   ctx->merged_fresh = false;
   if (instance_id) *instance_id = id;
   return 0;
@@ -417,6 +452,7 @@ int qis_clear_instances(qis_ctx* ctx) {
   ctx->P.n_inst = 0;
   ctx->P.B = 0;
   ctx->work_dirty = true;
+  drop_graph(ctx);
   ctx->merged_fresh = false;
   return 0;
 }
@@ -484,25 +520,31 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
   }
   cudaStream_t s = ctx->stream;
   const DevPtrs& P = ctx->P;
-  for (int it = 0; it < n_iters; ++it) {
-    CK(prof_begin(ctx, 0));
-    LAUNCH(launch_pick(P, s));
-    CK(prof_end(ctx, 0));
-    CK(prof_begin(ctx, 1));
-    if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
-    else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
-    else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, s));
-    CK(prof_end(ctx, 1));
-    CK(prof_begin(ctx, 2));
-    LAUNCH(launch_bound(P, s));
-    CK(prof_end(ctx, 2));
-    CK(prof_begin(ctx, 3));
-    if (ctx->mode == QIS_FP64) LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
-    else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, s));
-    CK(prof_end(ctx, 3));
-    CK(prof_begin(ctx, 4));
-    LAUNCH(launch_merge(P, s));
-    CK(prof_end(ctx, 4));
+  if (!ctx->profiling && ctx->use_graph) {
+    // one iteration = five kernels, captured once into a CUDA graph and replayed
+    if (!ctx->graph_exec) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_iteration(ctx, s);
+      cudaError_t ec = cudaStreamEndCapture(s, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      CK(ec);
+      ec = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(ec);
+    }
+    for (int it = 0; it < n_iters; ++it) {
+      CK(cudaGraphLaunch(ctx->graph_exec, s));
+      ctx->launches += 5;
+    }
+  } else {
+    for (int it = 0; it < n_iters; ++it) {
+      const int rc = launch_iteration(ctx, s);
+      if (rc) return rc;
+    }
   }
   ctx->merged_fresh = false;
   if (n_active) {
