@@ -245,6 +245,78 @@ def run_ours(args, rank, world, device):
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec)
 
 
+def run_warmstart(args, device=0):
+    """Learned warm start vs random initial states (BASELINE config 5): train the network on the
+    best states the search finds for `n_train` generated n=300 Gaussian instances, then run the
+    search from learned and from random initial states on 120 held-out instances for a sweep of
+    iteration counts, and report time-to-ground-state for each (reference: the best energy of
+    all runs, not certified)."""
+    import torch
+    from paper_2010_00180_gb300 import build as B, qis as Q
+    from paper_2010_00180_gb300 import inputs as I
+    B.build()
+    n, K, R, n_train, n_test = 300, 120, 32, args.ws_train, 120
+    t0 = time.perf_counter()
+    net = Q.MLP(hidden=256, max_sites=n * n_train, batch=4096, max_n=n, device=device, seed=args.seed)
+    chunk = 250
+    for c0 in range(0, n_train, chunk):
+        m = min(chunk, n_train - c0)
+        ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=m, device=device)
+        data = []
+        for k in range(m):
+            J, h = I.instance("gaussian", n, seed=args.seed + 50, inst=c0 + k)
+            ctx.create_instance(J, h)
+            ctx.init_states(k, I.random_states(n, R, seed=args.seed + 51, inst=c0 + k))
+            data.append((J, h))
+        ctx.iterate(K)
+        for k, (J, h) in enumerate(data):
+            net.add_example(J, h, ctx.topk_states(k, 1)["bits"][0])
+        ctx.close()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = net.train(args.ws_epochs, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    test = [I.instance("gaussian", n, seed=args.seed + 90, inst=k) for k in range(n_test)]
+    ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=n_test, device=device)
+    for J, h in test:
+        ctx.create_instance(J, h)
+    stream = torch.cuda.ExternalStream(ctx.stream_handle(), device=device)
+    sweep = [15, 30, 60, 120, 240]
+    results = {}
+    best = np.full(n_test, np.inf)
+    for mode in ("random", "learned"):
+        for iters in sweep:
+            for k in range(n_test):
+                if mode == "learned":
+                    ctx.init_states_learned(k, net)
+                else:
+                    ctx.init_states(k, I.random_states(n, R, seed=args.seed + 91, inst=k))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            ctx.iterate(iters)
+            ctx.merge()
+            ev1.record(stream)
+            ctx.synchronize()
+            E = np.array([ctx.topk_states(k, 1)["E"][0] for k in range(n_test)])
+            results[(mode, iters)] = (ev0.elapsed_time(ev1) / 1e3, E)
+            best = np.minimum(best, E)
+    rows = []
+    for (mode, iters), (t, E) in results.items():
+        p1 = float(np.mean(np.abs(E - best) <= 1e-9 * np.abs(best)))
+        tts = 0.0 if p1 >= 1 else (math.inf if p1 <= 0 else math.log(0.01) / math.log(1 - p1) * t)
+        rows.append({"init": mode, "iterations": iters, "seconds": round(t, 5), "p1": round(p1, 4), "tts_s": tts})
+    finite = [r for r in rows if math.isfinite(r["tts_s"]) and r["tts_s"] > 0]
+    best_tts = {m: min((r["tts_s"] for r in finite if r["init"] == m), default=math.inf) for m in ("random", "learned")}
+    line = {"metric": "time-to-ground-state, learned vs random initial states, N=300", "unit": "s",
+            "value": best_tts["learned"], "higher_is_better": False, "baseline_random_tts_s": best_tts["random"],
+            "config": {"workload": "warmstart_gaussian_n300", "n": n, "K": K, "R": R, "train_instances": n_train,
+                       "test_instances": n_test, "epochs": args.ws_epochs, "final_train_loss": round(loss, 5),
+                       "data_gen_s": round(t_data, 2), "train_s": round(t_train, 2)},
+            "sweep": rows, "reference": "best energy of all runs in this sweep (not certified)",
+            "data": "synthetic"}
+    print(json.dumps(line))
+
+
 def roofline(res, pk):
     """Candidate scan (dominant kernel) against the SM issue rate."""
     ms, nl = res["prof"]["scan"]
@@ -274,8 +346,14 @@ def main():
     ap.add_argument("--cpu-searches", type=int, default=0, help="oracle sample size (0 = one per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-ground-state reference run")
+    ap.add_argument("--warmstart", action="store_true", help="learned vs random warm start (n=300) instead")
+    ap.add_argument("--ws-train", type=int, default=2000, help="training instances of the warm-start run")
+    ap.add_argument("--ws-epochs", type=int, default=20)
     args = ap.parse_args()
 
+    if args.warmstart:
+        run_warmstart(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -161,6 +161,48 @@ int qis_profile_enable(qis_ctx* ctx, int on);
 int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches);
 
 /* ------------------------------------------------------------------------------------------
+ * Learned warm start. Alg. 4 starts every search from rand_between(0, 2^N - 1); a per-site
+ * network can propose the initial states instead. Features of site i (FP64, then FP32):
+ * h_i, sum_j J_ij / sqrt(n), sum_j |J_ij| / n, sqrt(sum_j J_ij^2 / n), max_{j!=i} J_ij,
+ * min_{j!=i} J_ij, sum_j J_ij h_j / sqrt(n), sum_j J_ij sign(h_j) / sqrt(n). Network:
+ * 8 -> hidden -> hidden -> hidden -> 1 with ReLU, BF16 weights (rounded from an FP32 master
+ * copy), FP32 accumulation; output z_i = logit of P(s_i = +1); loss: mean binary
+ * cross-entropy; training: Adam (beta 0.9 / 0.999, eps 1e-8) on the GPU. Parameters are
+ * flattened as W1 (8 x H, row-major), b1 (H), W2 (H x H), b2, W3 (H x H), b3, w4 (H), b4 (1).
+ * Pointers are host pointers. */
+typedef struct qis_mlp qis_mlp;
+typedef struct {
+  int hidden;     /* H, multiple of 16 in [16, 1024] */
+  int max_sites;  /* capacity of the training set (sites, summed over examples) */
+  int batch;      /* training batch (sites) */
+  int max_n;      /* largest instance */
+  int device;
+  uint64_t seed;  /* SplitMix64 key of the He initialisation */
+} qis_mlp_config;
+int qis_mlp_create(const qis_mlp_config* cfg, qis_mlp** out);
+void qis_mlp_destroy(qis_mlp* m);
+const char* qis_mlp_last_error(const qis_mlp* m);
+int qis_mlp_num_params(qis_mlp* m, int* count);
+int qis_mlp_get_params(qis_mlp* m, float* flat);
+int qis_mlp_set_params(qis_mlp* m, const float* flat);           /* also resets Adam state */
+/* features of the n sites of (J, h): X_out n x 8 */
+int qis_mlp_features(qis_mlp* m, int n, const double* J, const double* h, float* X_out);
+/* one training example: the sites of (J, h) labelled by the state `bits` (y_i = 1 <=> s_i = +1) */
+int qis_mlp_add_example(qis_mlp* m, int n, const double* J, const double* h, const uint64_t* bits);
+int qis_mlp_clear_examples(qis_mlp* m);
+/* logits of M feature rows (M <= max(batch, max_n)) */
+int qis_mlp_forward(qis_mlp* m, int M, const float* X, float* z_out);
+/* mean loss and its gradient (flattened as above) on M labelled rows; no update */
+int qis_mlp_loss_grad(qis_mlp* m, int M, const float* X, const float* y, double* loss, float* grad_out);
+/* `epochs` passes over the training set in batches; final_loss = mean batch loss of the last */
+int qis_mlp_train(qis_mlp* m, int epochs, float lr, double* final_loss);
+/* Initial states of the R searches of an instance from the network (replacing Alg. 4's
+ * rand_between): search 0 takes s_i = +1 iff z_i >= 0; search r >= 1 sets s_i = +1 with
+ * probability sigmoid(z_i), drawing value (r*n + i) of the SplitMix64 stream keyed by
+ * splitmix64(key(seed, id) ^ 5, 0) (key of qis_init_states). Then as qis_init_states. */
+int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m);
+
+/* ------------------------------------------------------------------------------------------
  * Allocation-free candidate selection (the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory when they need the work done: code running
  * while a stream is being captured into a CUDA graph, real-time loops that must not block in

@@ -73,19 +73,24 @@ int fail(qis_ctx* c, int code, const std::string& msg) {
   return code;
 }
 
+// On failure the runtime's last-error state is consumed, so a later call does not report it.
 #define CK(call)                                                                              \
   do {                                                                                        \
     cudaError_t e_ = (call);                                                                  \
-    if (e_ != cudaSuccess)                                                                    \
+    if (e_ != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                     \
       return fail(ctx, QIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                         \
   } while (0)
 
 #define LAUNCH(call)                                                                          \
   do {                                                                                        \
     cudaError_t e_ = (call);                                                                  \
     ++ctx->launches;                                                                          \
-    if (e_ != cudaSuccess)                                                                    \
+    if (e_ != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                     \
       return fail(ctx, QIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    }                                                                                         \
   } while (0)
 
 template <typename T>
@@ -491,6 +496,26 @@ int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
   CK(cudaMemcpyAsync(ctx->P.init_bits + (size_t)d.first_search * Wm, h.data(), h.size() * sizeof(uint64_t),
                      cudaMemcpyHostToDevice, ctx->stream));
   LAUNCH(launch_init_search(ctx->P, d.first_search, R, ctx->stream));
+  ctx->inst_ready[instance_id] = 1;
+  ctx->merged_fresh = false;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!m) return fail(ctx, QIS_ERR_INVALID_ARG, "network is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  const InstDesc& d = ctx->inst[instance_id];
+  if (d.n > mlp_max_n(m)) return fail(ctx, QIS_ERR_INVALID_ARG, "instance larger than the network's max_n");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const uint64_t key = splitmix64(state_key(ctx->cfg.seed, instance_id) ^ 5ull, 0);
+  CK(cudaMemsetAsync(ctx->P.init_bits + (size_t)d.first_search * ctx->Wmax, 0,
+                     sizeof(uint64_t) * (size_t)ctx->R * ctx->Wmax, ctx->stream));
+  CK(mlp_propose_states(m, ctx->J64 + d.off_mat, d.n_pad, ctx->h64 + d.off_vec, d.n, ctx->R, key,
+                        ctx->P.init_bits + (size_t)d.first_search * ctx->Wmax, ctx->Wmax, ctx->stream));
+  ctx->launches += 5;
+  LAUNCH(launch_init_search(ctx->P, d.first_search, ctx->R, ctx->stream));
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   CK(cudaStreamSynchronize(ctx->stream));

@@ -138,6 +138,11 @@ __device__ inline double dkey_inv(unsigned long long k) {
 // Message returned by qis_last_error(NULL) (calls that have no context).
 void set_global_error(const char* msg);
 
+// Learned warm start (qis_mlp.cu): R initial states of one instance into init_bits.
+cudaError_t mlp_propose_states(qis_mlp* m, const double* J64, long long stride, const double* h64, int n, int R,
+                               uint64_t key, uint64_t* init_bits, int Wstride, cudaStream_t s);
+int mlp_max_n(const qis_mlp* m);
+
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);

@@ -23,7 +23,10 @@ SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
-           "qis_select_candidates_noalloc"]
+           "qis_select_candidates_noalloc",
+           "qis_mlp_create", "qis_mlp_destroy", "qis_mlp_last_error", "qis_mlp_num_params", "qis_mlp_get_params",
+           "qis_mlp_set_params", "qis_mlp_features", "qis_mlp_add_example", "qis_mlp_clear_examples",
+           "qis_mlp_forward", "qis_mlp_loss_grad", "qis_mlp_train", "qis_init_states_learned"]
 KERNEL_CLASSES = ["pick", "fields", "bound", "scan", "merge"]
 
 
@@ -32,6 +35,11 @@ class QISError(RuntimeError):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
         self.name = ERRORS.get(code, str(code))
+
+
+class MLPConfig(C.Structure):
+    _fields_ = [("hidden", C.c_int), ("max_sites", C.c_int), ("batch", C.c_int), ("max_n", C.c_int),
+                ("device", C.c_int), ("seed", C.c_uint64)]
 
 
 class Config(C.Structure):
@@ -73,6 +81,19 @@ def load():
         "qis_profile_enable": (I, [P, I]),
         "qis_profile_query": (I, [P, I, C.POINTER(C.c_double), C.POINTER(U64)]),
         "qis_select_candidates_noalloc": (I, [I, P, P, P, I, P, P, P, P]),
+        "qis_mlp_create": (I, [C.POINTER(MLPConfig), C.POINTER(P)]),
+        "qis_mlp_destroy": (None, [P]),
+        "qis_mlp_last_error": (C.c_char_p, [P]),
+        "qis_mlp_num_params": (I, [P, C.POINTER(I)]),
+        "qis_mlp_get_params": (I, [P, P]),
+        "qis_mlp_set_params": (I, [P, P]),
+        "qis_mlp_features": (I, [P, I, P, P, P]),
+        "qis_mlp_add_example": (I, [P, I, P, P, P]),
+        "qis_mlp_clear_examples": (I, [P]),
+        "qis_mlp_forward": (I, [P, I, P, P]),
+        "qis_mlp_loss_grad": (I, [P, I, P, P, C.POINTER(C.c_double), P]),
+        "qis_mlp_train": (I, [P, I, C.c_float, C.POINTER(C.c_double)]),
+        "qis_init_states_learned": (I, [P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -229,3 +250,85 @@ class Context:
         ms, n = C.c_double(), C.c_uint64()
         self._check(self.lib.qis_profile_query(self.h, k, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def init_states_learned(self, iid: int, mlp: "MLP"):
+        """Initial states of instance iid proposed by the network (qis_init_states_learned)."""
+        self._check(self.lib.qis_init_states_learned(self.h, iid, mlp.h))
+
+
+class MLP:
+    """The warm-start network (qis_mlp_*): features -> 3 hidden ReLU layers -> logit of s_i = +1."""
+
+    N_FEATURES = 8
+
+    def __init__(self, hidden=256, max_sites=1 << 20, batch=4096, max_n=1024, device=0, seed=0):
+        self.lib = load()
+        self.cfg = MLPConfig(hidden, max_sites, batch, max_n, device, seed & 0xFFFFFFFFFFFFFFFF)
+        self.h = C.c_void_p()
+        rc = self.lib.qis_mlp_create(C.byref(self.cfg), C.byref(self.h))
+        if rc != 0:
+            raise QISError(rc, self.lib.qis_last_error(None).decode())
+        cnt = C.c_int()
+        self._check(self.lib.qis_mlp_num_params(self.h, C.byref(cnt)))
+        self.n_params = cnt.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise QISError(rc, self.lib.qis_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            self.lib.qis_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.qis_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.n_params
+        self._check(self.lib.qis_mlp_set_params(self.h, _ptr(flat)))
+
+    def features(self, J, h) -> np.ndarray:
+        J = np.ascontiguousarray(J, np.float64)
+        h = np.ascontiguousarray(h, np.float64)
+        n = h.shape[0]
+        out = np.zeros((n, self.N_FEATURES), np.float32)
+        self._check(self.lib.qis_mlp_features(self.h, n, _ptr(J), _ptr(h), _ptr(out)))
+        return out
+
+    def add_example(self, J, h, bits):
+        J = np.ascontiguousarray(J, np.float64)
+        h = np.ascontiguousarray(h, np.float64)
+        bits = np.ascontiguousarray(bits, np.uint64).reshape(-1)
+        self._check(self.lib.qis_mlp_add_example(self.h, h.shape[0], _ptr(J), _ptr(h), _ptr(bits)))
+
+    def clear_examples(self):
+        self._check(self.lib.qis_mlp_clear_examples(self.h))
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        z = np.zeros(X.shape[0], np.float32)
+        self._check(self.lib.qis_mlp_forward(self.h, X.shape[0], _ptr(X), _ptr(z)))
+        return z
+
+    def loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        L = C.c_double()
+        self._check(self.lib.qis_mlp_loss_grad(self.h, X.shape[0], _ptr(X), _ptr(y), C.byref(L), _ptr(g)))
+        return L.value, g
+
+    def train(self, epochs: int, lr: float = 1e-3) -> float:
+        L = C.c_double()
+        self._check(self.lib.qis_mlp_train(self.h, epochs, lr, C.byref(L)))
+        return L.value
