@@ -95,6 +95,10 @@ int qis_clear_instances(qis_ctx* ctx);
  * be rounded onto the grid (QIS_SPLIT_BF16 / QIS_PM1_FP8; q = -1 in QIS_FP64). */
 int qis_instance_info(qis_ctx* ctx, int instance_id, int* q, int* digits, int* rounded);
 
+/* Number of spins n of an instance (e.g. after qis_load); QIS_ERR_INVALID_ARG for an id
+ * that does not exist. */
+int qis_instance_n(qis_ctx* ctx, int instance_id, int* n);
+
 /* Set the R initial states of an instance and reset its R searches to the start of
  * Alg. 3: list = [initial state] followed by K empty slots, nothing used.
  *   bits: R*W words (search r's state at bits + r*W), or NULL to draw every bit from the
@@ -120,6 +124,30 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active);
  * undefined. Any output pointer may be NULL. */
 int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double* E,
                     uint8_t* used, uint64_t* stamp, int* count);
+
+/* Replace the kept list of search r of an instance (the inverse of qis_search_list): used
+ * to merge lists computed elsewhere (another process or GPU running other searches of the
+ * same instance) with the device's Alg. 4 merge, and by qis_load.
+ *   count: entries, 1 <= count <= K+1; bits: count*W words (bit i = sigma_i, bits above n
+ *   zero), states distinct; E: count finite energies, nondecreasing (the list order of
+ *   Alg. 2); used: count flags (l of Alg. 3) or NULL for all false; stamp: count arrival
+ *   keys (t << 32 | candidate index) or NULL for 0..count-1; t: iterations already done.
+ * The search becomes active when some entry is unused. The energies are taken as given.
+ * Synchronises; QIS_ERR_INVALID_ARG on any violated condition, the list then unchanged. */
+int qis_set_search_list(qis_ctx* ctx, int instance_id, int r, int count, const uint64_t* bits,
+                        const double* E, const uint8_t* used, const uint64_t* stamp, int t);
+
+/* Checkpoint of the whole search state: every instance (J, h), its R initial states and
+ * every search's kept list with its used flags, stamps, iteration counter and active flag,
+ * followed by a 64-bit FNV-1a checksum. Synchronises. A failed write removes the file. */
+int qis_save(qis_ctx* ctx, const char* path);
+
+/* Resume from a qis_save file into a context that has no instances yet and was created
+ * with the same K, R and precision (max_n and max_instances large enough). Iterating the
+ * loaded context continues the saved searches exactly as the saved context would have.
+ * QIS_ERR_INVALID_ARG for a missing, truncated or corrupted file (checksum) or a config
+ * mismatch; QIS_ERR_STATE if the context already holds instances. */
+int qis_load(qis_ctx* ctx, const char* path);
 
 /* Alg. 4 merge of the R lists of an instance followed by FP64 rescoring: the first
  * min(k, count) states of the union of the R lists (each state at its first occurrence
@@ -147,6 +175,34 @@ int qis_kernel_launches(qis_ctx* ctx, uint64_t* count);
  * X_i of every parent (n(n-1)/2 and n per active search per iteration, Sec. III flip sets).
  * Synchronises the stream. */
 int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles);
+
+/* Launch shapes of the iteration. None of them changes any result (the candidate sets, the
+ * survivor decisions and the exact keys are the same for every setting); they only trade
+ * parallelism against reuse.
+ *   scan_chunk_nc: the pair scan covers each 32-row block with column chunks of 32*NC sites,
+ *                  NC <= scan_chunk_nc (1..8; default 8);
+ *   scan_search_group: searches of an instance per scan task (0 = all R; smaller groups
+ *                  give more, shorter tasks for few instances);
+ *   gemm_tile_searches: searches per tensor-core tile of the local-field GEMM (multiple of
+ *                  16, at most 256, digits * it <= 512; 0 = automatic). */
+typedef struct {
+  int scan_chunk_nc;
+  int scan_search_group;
+  int gemm_tile_searches;
+} qis_tuning;
+
+/* Current launch shapes (automatic values resolved). */
+int qis_get_tuning(qis_ctx* ctx, qis_tuning* out);
+
+/* Set the launch shapes for the current and later instances. QIS_ERR_INVALID_ARG for values
+ * out of range or a scan task list larger than the context holds (the setting is unchanged). */
+int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t);
+
+/* Autotuner: times `iters` iterations from the initial states for candidate launch shapes
+ * (coordinate search over chunk width, search group and GEMM tile, each timed after one
+ * untimed run) and keeps the fastest. Every search is reset to its initial state afterwards
+ * (as qis_reset). best / best_ms (may be NULL) receive the choice and its time. */
+int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms);
 
 /* The library's CUDA stream (a cudaStream_t), so callers can order their own work and
  * CUDA events with respect to the library's kernels. */

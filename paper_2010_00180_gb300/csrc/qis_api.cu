@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,10 @@ struct qis_ctx {
   double* scratch_E = nullptr;
   int scratch_states = 0;
   uint64_t launches = 0;
+  uint64_t cand_acc[2] = {0, 0};
+  // tunables (results never depend on them): scan chunk width 32 * tune_nc columns, searches
+  // per scan task (0 = all R of the instance), searches per GEMM tile (0 = automatic)
+  qis_tuning tune{8, 0, 0};  // candidates of instances removed by qis_clear_instances
   // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
   bool profiling = false;
   bool use_graph = true;                    // QIS_NO_GRAPH=1 launches the kernels one by one
@@ -136,6 +141,23 @@ int sync_and_check(qis_ctx* ctx) {
   return check_status(ctx);
 }
 
+// Candidates of the current instances: every productive iteration of a search of an n-spin
+// instance evaluates n(n-1)/2 pairs and n singles.
+int count_candidates(qis_ctx* ctx, uint64_t c[2]) {
+  c[0] = c[1] = 0;
+  if (ctx->P.B == 0) return 0;
+  std::vector<int> np(ctx->P.B);
+  CK(cudaMemcpy(np.data(), ctx->P.nprod, sizeof(int) * np.size(), cudaMemcpyDeviceToHost));
+  for (size_t id = 0; id < ctx->inst.size(); ++id) {
+    const uint64_t n = (uint64_t)ctx->inst[id].n;
+    uint64_t it = 0;
+    for (int r = 0; r < ctx->R; ++r) it += (uint64_t)np[(size_t)ctx->inst[id].first_search + r];
+    c[0] += it * (n * (n - 1) / 2);
+    c[1] += it * n;
+  }
+  return 0;
+}
+
 // Record the start event of a timed launch of class `k` (no-op unless profiling).
 cudaError_t prof_begin(qis_ctx* ctx, int k) {
   if (!ctx->profiling) return cudaSuccess;
@@ -167,14 +189,14 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   CK(prof_begin(ctx, 1));
   if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
   else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
-  else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, s));
+  else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, ctx->tune.gemm_tile_searches, s));
   CK(prof_end(ctx, 1));
   CK(prof_begin(ctx, 2));
   LAUNCH(launch_bound(P, s));
   CK(prof_end(ctx, 2));
   CK(prof_begin(ctx, 3));
   if (ctx->mode == QIS_FP64) LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
-  else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, s));
+  else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R, s));
   CK(prof_end(ctx, 3));
   CK(prof_begin(ctx, 4));
   LAUNCH(launch_merge(P, s));
@@ -200,9 +222,12 @@ int build_work(qis_ctx* ctx) {
   if (!w.empty()) CK(cudaMemcpyAsync(ctx->work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
   // warp tasks of the FP32 pair scan, widest chunks first (better tail balance)
   std::vector<int4> t;
-  for (int id = 0; id < (int)ctx->inst.size(); ++id) scan_tasks_for(id, ctx->inst[id].n, t);
-  std::stable_sort(t.begin(), t.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
-  if (t.size() > ctx->tasks_cap) return fail(ctx, QIS_ERR_STATE, "task list overflow");
+  const int RG = ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R;
+  for (int id = 0; id < (int)ctx->inst.size(); ++id)
+    scan_tasks_for(id, ctx->inst[id].n, ctx->tune.scan_chunk_nc, ctx->R, RG, t);
+  std::stable_sort(t.begin(), t.end(), [](const int4& a, const int4& b) { return (a.w & 0xff) > (b.w & 0xff); });
+  if (t.size() > ctx->tasks_cap)
+    return fail(ctx, QIS_ERR_INVALID_ARG, "too many scan tasks for this tuning (wider chunks or larger search groups)");
   ctx->n_tasks = (int)t.size();
   if (!t.empty()) CK(cudaMemcpyAsync(ctx->tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -325,7 +350,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.surv, B * (size_t)ctx->cap);
     ALLOC(P.init_bits, B * W);
     ALLOC(P.status, 4);
-    ALLOC(P.cand, 2);
+    ALLOC(P.nprod, B);
     ALLOC(P.mrg_ref, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_src, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_count, ctx->max_inst);
@@ -452,6 +477,14 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
 int qis_clear_instances(qis_ctx* ctx) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
   CK(cudaStreamSynchronize(ctx->stream));
+  {
+    uint64_t c[2];
+    int rc = count_candidates(ctx, c);
+    if (rc) return rc;
+    ctx->cand_acc[0] += c[0];
+    ctx->cand_acc[1] += c[1];
+    if (ctx->P.B > 0) CK(cudaMemset(ctx->P.nprod, 0, sizeof(int) * (size_t)ctx->P.B));
+  }
   ctx->inst.clear();
   ctx->inst_ready.clear();
   ctx->P.n_inst = 0;
@@ -469,6 +502,13 @@ int qis_instance_info(qis_ctx* ctx, int instance_id, int* q, int* digits, int* r
   if (q) *q = d.q;
   if (digits) *digits = d.digits;
   if (rounded) *rounded = d.rounded;
+  return 0;
+}
+
+int qis_instance_n(qis_ctx* ctx, int instance_id, int* n) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  if (n) *n = ctx->inst[instance_id].n;
   return 0;
 }
 
@@ -628,6 +668,286 @@ int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double
   return 0;
 }
 
+namespace {
+
+// Write one search's kept list (entries in key order) into the device list of search b. The
+// caller has validated the arguments; hashes are computed on the device from the bits.
+int import_search(qis_ctx* ctx, int b, int W, int count, const uint64_t* bits, const double* E,
+                  const uint8_t* used, const uint64_t* stamp, int t) {
+  const int K1 = ctx->K1, Wm = ctx->Wmax;
+  const size_t base = (size_t)b * K1;
+  std::vector<uint64_t> lb((size_t)K1 * Wm, 0ull), st(K1, 0ull);
+  std::vector<double> e(K1, INFINITY);
+  std::vector<uint8_t> u(K1, 0);
+  std::vector<int> ord(K1, -1);
+  int act = 0;
+  for (int k = 0; k < count; ++k) {
+    memcpy(&lb[(size_t)k * Wm], bits + (size_t)k * W, W * sizeof(uint64_t));
+    e[k] = E[k];
+    u[k] = used ? (used[k] != 0) : 0;
+    st[k] = stamp ? stamp[k] : (uint64_t)k;
+    ord[k] = k;
+    act |= !u[k];
+  }
+  const int one[4] = {count, act, t, 0};
+  cudaStream_t s = ctx->stream;
+  const DevPtrs& P = ctx->P;
+  CK(cudaMemcpyAsync(P.lst_bits + base * Wm, lb.data(), lb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_E + base, e.data(), K1 * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_stamp + base, st.data(), K1 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_used + base, u.data(), K1, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_ord + base, ord.data(), K1 * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_count + b, &one[0], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.active + b, &one[1], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.iter_t + b, &one[2], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.surv_cnt + b, &one[3], sizeof(int), cudaMemcpyHostToDevice, s));
+  LAUNCH(launch_hash_list(P, b, count, s));
+  CK(cudaStreamSynchronize(s));   // the host vectors above are the copies' sources
+  return 0;
+}
+
+// Checks of an imported list: 1 <= count <= K+1, no bits above n, finite nondecreasing E,
+// distinct states.
+int check_list(qis_ctx* ctx, int n, int count, const uint64_t* bits, const double* E) {
+  const int W = words_of(n);
+  if (count < 1 || count > ctx->K1) return fail(ctx, QIS_ERR_INVALID_ARG, "list length must be in [1, K+1]");
+  if (!bits || !E) return fail(ctx, QIS_ERR_INVALID_ARG, "bits and E must not be NULL");
+  const uint64_t top = (n % 64) ? ((1ull << (n % 64)) - 1) : ~0ull;
+  std::vector<std::vector<uint64_t>> v;
+  for (int k = 0; k < count; ++k) {
+    if (bits[(size_t)k * W + W - 1] & ~top) return fail(ctx, QIS_ERR_INVALID_ARG, "state bits above n must be zero");
+    if (!std::isfinite(E[k])) return fail(ctx, QIS_ERR_INVALID_ARG, "list energies must be finite");
+    if (k > 0 && E[k] < E[k - 1]) return fail(ctx, QIS_ERR_INVALID_ARG, "list energies must be nondecreasing");
+    v.emplace_back(bits + (size_t)k * W, bits + (size_t)(k + 1) * W);
+  }
+  std::sort(v.begin(), v.end());
+  if (std::adjacent_find(v.begin(), v.end()) != v.end())
+    return fail(ctx, QIS_ERR_INVALID_ARG, "list states must be distinct");
+  return 0;
+}
+
+}  // namespace
+
+int qis_set_search_list(qis_ctx* ctx, int instance_id, int r, int count, const uint64_t* bits, const double* E,
+                        const uint8_t* used, const uint64_t* stamp, int t) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
+  if (r < 0 || r >= ctx->R) return fail(ctx, QIS_ERR_INVALID_ARG, "bad search index");
+  if (t < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "iteration counter must be >= 0");
+  const InstDesc& d = ctx->inst[instance_id];
+  int rc = check_list(ctx, d.n, count, bits, E);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->cfg.device));
+  rc = sync_and_check(ctx);
+  if (rc) return rc;
+  rc = import_search(ctx, d.first_search + r, d.W, count, bits, E, used, stamp, t);
+  if (rc) return rc;
+  ctx->merged_fresh = false;
+  return 0;
+}
+
+// ---------------------------------------------------------------- checkpoint / resume
+// File layout (little endian): "QISCKPT1", int32 {version, K, R, precision, n_instances, 0},
+// uint64 seed; per instance: int32 {n, ready}, J (n*n FP64 row major), h (n FP64), the R
+// initial states (R*W uint64); per search of the instance: int32 {count, t, active, 0}, then
+// count entries {W uint64 bits, FP64 E, uint64 stamp, uint64 used}; last, the FNV-1a 64-bit
+// hash of every byte before it.
+namespace {
+
+constexpr char kCkptMagic[8] = {'Q', 'I', 'S', 'C', 'K', 'P', 'T', '1'};
+constexpr int kCkptVersion = 1;
+
+struct Fnv1a {
+  uint64_t h = 0xcbf29ce484222325ull;
+  void add(const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= c[i];
+      h *= 0x100000001b3ull;
+    }
+  }
+};
+
+struct Writer {
+  FILE* f;
+  Fnv1a sum;
+  bool ok = true;
+  void put(const void* p, size_t n) {
+    if (n == 0) return;
+    ok = ok && fwrite(p, 1, n, f) == n;
+    sum.add(p, n);
+  }
+};
+
+struct Reader {
+  std::vector<unsigned char> data;
+  size_t pos = 0;
+  bool get(void* p, size_t n) {
+    if (pos + n > data.size()) return false;
+    memcpy(p, data.data() + pos, n);
+    pos += n;
+    return true;
+  }
+};
+
+}  // namespace
+
+int qis_save(qis_ctx* ctx, const char* path) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!path) return fail(ctx, QIS_ERR_INVALID_ARG, "path is NULL");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = sync_and_check(ctx);
+  if (rc) return rc;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, QIS_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
+  Writer w{f};
+  const int K1 = ctx->K1, Wm = ctx->Wmax, R = ctx->R;
+  const int hdr[6] = {kCkptVersion, ctx->cfg.K, R, ctx->mode, (int)ctx->inst.size(), 0};
+  w.put(kCkptMagic, 8);
+  w.put(hdr, sizeof(hdr));
+  w.put(&ctx->cfg.seed, 8);
+  auto bail = [&](int code) {   // the message is already in ctx->err
+    fclose(f);
+    remove(path);
+    return code;
+  };
+  for (size_t id = 0; id < ctx->inst.size(); ++id) {
+    const InstDesc& d = ctx->inst[id];
+    const int n = d.n, W = d.W;
+    const int ih[2] = {n, ctx->inst_ready[id]};
+    w.put(ih, sizeof(ih));
+    std::vector<double> J((size_t)n * n), h(n);
+    cudaError_t e = cudaMemcpy2D(J.data(), sizeof(double) * n, ctx->J64 + d.off_mat, sizeof(double) * d.n_pad,
+                                 sizeof(double) * n, n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), ctx->h64 + d.off_vec, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    std::vector<uint64_t> ib((size_t)R * Wm);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ib.data(), ctx->P.init_bits + (size_t)d.first_search * Wm, ib.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(ctx, QIS_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e)));
+    }
+    w.put(J.data(), J.size() * 8);
+    w.put(h.data(), h.size() * 8);
+    for (int r = 0; r < R; ++r) w.put(&ib[(size_t)r * Wm], W * 8);
+    std::vector<uint64_t> bits((size_t)K1 * W), stamp(K1);
+    std::vector<double> E(K1);
+    std::vector<uint8_t> used(K1);
+    for (int r = 0; r < R; ++r) {
+      const int b = d.first_search + r;
+      int cnt = 0, t = 0, act = 0;
+      rc = qis_search_list(ctx, (int)id, r, bits.data(), E.data(), used.data(), stamp.data(), &cnt);
+      if (rc) return bail(rc);
+      e = cudaMemcpy(&t, ctx->P.iter_t + b, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(&act, ctx->P.active + b, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(ctx, QIS_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e)));
+      }
+      const int sh[4] = {cnt, t, act, 0};
+      w.put(sh, sizeof(sh));
+      for (int k = 0; k < cnt; ++k) {
+        const uint64_t u = used[k];
+        w.put(&bits[(size_t)k * W], W * 8);
+        w.put(&E[k], 8);
+        w.put(&stamp[k], 8);
+        w.put(&u, 8);
+      }
+    }
+  }
+  const uint64_t sum = w.sum.h;
+  w.put(&sum, 8);
+  const bool ok = w.ok && fclose(f) == 0;
+  if (!ok) {
+    remove(path);
+    return fail(ctx, QIS_ERR_INVALID_ARG, std::string("write to ") + path + " failed");
+  }
+  return 0;
+}
+
+int qis_load(qis_ctx* ctx, const char* path) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (!path) return fail(ctx, QIS_ERR_INVALID_ARG, "path is NULL");
+  if (!ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "qis_load needs a context without instances");
+  Reader rd;
+  {
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(ctx, QIS_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    unsigned char buf[1 << 16];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof(buf), f)) > 0) rd.data.insert(rd.data.end(), buf, buf + got);
+    fclose(f);
+  }
+  const auto corrupt = [&](const char* what) {
+    return fail(ctx, QIS_ERR_INVALID_ARG, std::string("checkpoint ") + path + ": " + what);
+  };
+  if (rd.data.size() < 8 + 24 + 8 + 8) return corrupt("file too short");
+  {
+    Fnv1a s;
+    s.add(rd.data.data(), rd.data.size() - 8);
+    uint64_t stored;
+    memcpy(&stored, rd.data.data() + rd.data.size() - 8, 8);
+    if (s.h != stored) return corrupt("checksum mismatch");
+  }
+  char magic[8];
+  int hdr[6];
+  uint64_t seed;
+  rd.get(magic, 8);
+  rd.get(hdr, sizeof(hdr));
+  rd.get(&seed, 8);
+  if (memcmp(magic, kCkptMagic, 8) != 0) return corrupt("not a checkpoint");
+  if (hdr[0] != kCkptVersion) return corrupt("unsupported version");
+  if (hdr[1] != ctx->cfg.K || hdr[2] != ctx->R || hdr[3] != ctx->mode)
+    return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint K, R or precision differ from the context's");
+  const int n_inst = hdr[4], R = ctx->R;
+  if (n_inst < 0 || n_inst > ctx->max_inst) return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint has too many instances");
+  const size_t end = rd.data.size() - 8;
+  for (int id = 0; id < n_inst; ++id) {
+    int ih[2];
+    if (!rd.get(ih, sizeof(ih))) return corrupt("truncated");
+    const int n = ih[0];
+    if (n < 2 || n > ctx->cfg.max_n) return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint instance larger than max_n");
+    const int W = words_of(n);
+    std::vector<double> J((size_t)n * n), h(n);
+    if (!rd.get(J.data(), J.size() * 8) || !rd.get(h.data(), h.size() * 8)) return corrupt("truncated");
+    std::vector<uint64_t> ib((size_t)R * W);
+    if (!rd.get(ib.data(), ib.size() * 8)) return corrupt("truncated");
+    int got = -1;
+    int rc = qis_create_instance(ctx, n, J.data(), h.data(), &got);
+    if (rc) return rc;
+    const InstDesc& d = ctx->inst[got];
+    if (ih[1]) {
+      rc = qis_init_states(ctx, got, ib.data());
+      if (rc) return rc;
+    }
+    for (int r = 0; r < R; ++r) {
+      int sh[4];
+      if (!rd.get(sh, sizeof(sh))) return corrupt("truncated");
+      const int cnt = sh[0];
+      if (cnt < 0 || cnt > ctx->K1) return corrupt("bad list length");
+      std::vector<uint64_t> bits((size_t)cnt * W), stamp(cnt);
+      std::vector<double> E(cnt);
+      std::vector<uint8_t> used(cnt);
+      for (int k = 0; k < cnt; ++k) {
+        uint64_t u;
+        if (!rd.get(&bits[(size_t)k * W], W * 8) || !rd.get(&E[k], 8) || !rd.get(&stamp[k], 8) || !rd.get(&u, 8))
+          return corrupt("truncated");
+        used[k] = (uint8_t)(u != 0);
+      }
+      if (!ih[1]) continue;   // lists of an instance without initial states are not restored
+      rc = check_list(ctx, n, cnt, bits.data(), E.data());
+      if (rc) return rc;
+      rc = import_search(ctx, d.first_search + r, W, cnt, bits.data(), E.data(), used.data(), stamp.data(), sh[1]);
+      if (rc) return rc;
+      const int act = sh[2];
+      CK(cudaMemcpy(ctx->P.active + d.first_search + r, &act, sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
+  if (rd.pos != end) return corrupt("trailing bytes");
+  ctx->merged_fresh = false;
+  return 0;
+}
+
 int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out,
                     int* n_out) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
@@ -700,13 +1020,126 @@ int qis_kernel_launches(qis_ctx* ctx, uint64_t* count) {
   return 0;
 }
 
+
 int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
   CK(cudaStreamSynchronize(ctx->stream));
-  unsigned long long c[2];
-  CK(cudaMemcpy(c, ctx->P.cand, sizeof(c), cudaMemcpyDeviceToHost));
-  if (pairs) *pairs = c[0];
-  if (singles) *singles = c[1];
+  uint64_t c[2];
+  int rc = count_candidates(ctx, c);
+  if (rc) return rc;
+  if (pairs) *pairs = ctx->cand_acc[0] + c[0];
+  if (singles) *singles = ctx->cand_acc[1] + c[1];
+  return 0;
+}
+
+int qis_get_tuning(qis_ctx* ctx, qis_tuning* out) {
+  if (!ctx || !out) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  *out = ctx->tune;
+  if (out->scan_search_group == 0) out->scan_search_group = ctx->R;
+  if (out->gemm_tile_searches == 0) out->gemm_tile_searches = gemm_tile_n(ctx->R, ctx->digits_used);
+  return 0;
+}
+
+int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t) {
+  if (!ctx || !t) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  if (t->scan_chunk_nc < 1 || t->scan_chunk_nc > 8) return fail(ctx, QIS_ERR_INVALID_ARG, "scan_chunk_nc must be in [1, 8]");
+  if (t->scan_search_group < 0 || t->scan_search_group > ctx->R)
+    return fail(ctx, QIS_ERR_INVALID_ARG, "scan_search_group must be in [0, R]");
+  const int nt = t->gemm_tile_searches;
+  if (nt != 0 && (nt % 16 != 0 || nt < 16 || nt > 256 || ctx->digits_used * nt > 512))
+    return fail(ctx, QIS_ERR_INVALID_ARG, "gemm_tile_searches must be a multiple of 16 in [16, 256] with digits * it <= 512");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const qis_tuning old = ctx->tune;
+  ctx->tune = *t;
+  ctx->work_dirty = true;
+  drop_graph(ctx);
+  if (!ctx->inst.empty()) {
+    const int rc = build_work(ctx);
+    if (rc) {
+      ctx->tune = old;
+      ctx->work_dirty = true;
+      return rc;
+    }
+  }
+  return 0;
+}
+
+int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (iters < 1) return fail(ctx, QIS_ERR_INVALID_ARG, "iters must be >= 1");
+  if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
+  for (size_t i = 0; i < ctx->inst.size(); ++i)
+    if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // time of `iters` iterations from the initial states (the first replay builds the graph, so
+  // every candidate runs once untimed)
+  auto trial = [&](const qis_tuning& t, double* ms) -> int {
+    int rc = qis_set_tuning(ctx, &t);
+    if (rc) return rc;
+    for (int rep = 0; rep < 2; ++rep) {
+      rc = qis_reset(ctx);
+      if (rc) return rc;
+      CK(cudaEventRecord(e0, ctx->stream));
+      rc = qis_iterate(ctx, iters, nullptr);
+      if (rc) return rc;
+      CK(cudaEventRecord(e1, ctx->stream));
+      rc = sync_and_check(ctx);
+      if (rc) return rc;
+    }
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, e0, e1));
+    *ms = f;
+    return 0;
+  };
+  qis_tuning cur = ctx->tune;
+  cur.scan_search_group = cur.scan_search_group ? cur.scan_search_group : ctx->R;
+  double cur_ms = 0.0;
+  int rc = trial(cur, &cur_ms);
+  // a candidate the instance set cannot take (QIS_ERR_INVALID_ARG) is skipped; any other
+  // failure ends the search
+  auto consider = [&](const qis_tuning& t) {
+    if (rc) return;
+    double ms = 0.0;
+    const int r = trial(t, &ms);
+    if (r == 0 && ms < cur_ms) {
+      cur = t;
+      cur_ms = ms;
+    } else if (r != 0 && r != QIS_ERR_INVALID_ARG) {
+      rc = r;
+    }
+  };
+  // coordinate search: chunk width, search group, GEMM tile, each with the others fixed
+  for (int nc : {8, 6, 4, 2}) {
+    qis_tuning t = cur;
+    t.scan_chunk_nc = nc;
+    if (nc != cur.scan_chunk_nc) consider(t);
+  }
+  for (int div = 2; div <= 16; div *= 2) {
+    qis_tuning t = cur;
+    t.scan_search_group = (ctx->R + div - 1) / div;
+    if (t.scan_search_group >= 4 && t.scan_search_group != cur.scan_search_group) consider(t);
+  }
+  if (ctx->mode != QIS_FP64) {
+    for (int nt = 16; nt <= 256; nt *= 2) {
+      if (ctx->digits_used * nt > 512 || nt > ((ctx->R + 15) / 16) * 16) continue;
+      qis_tuning t = cur;
+      t.gemm_tile_searches = nt;
+      if (nt != cur.gemm_tile_searches) consider(t);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = qis_set_tuning(ctx, &cur);
+  if (rc) return rc;
+  rc = qis_reset(ctx);
+  if (rc) return rc;
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
   return 0;
 }
 

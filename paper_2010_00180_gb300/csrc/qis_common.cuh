@@ -71,11 +71,11 @@ struct DevPtrs {
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
   int* surv_cnt;          // [b]
-  unsigned long long* surv;  // [b][cap] candidate index (bit 63 clear) or scan hit record (bit 63 set)
+  unsigned long long* surv;  // [b][cap] survivor entries {c, i, j} (surv_entry)
   __half* S16;            // [b][NP] +-1 spins of the parent (0 past n), tensor-core operand
   uint64_t* init_bits;    // [b][Wmax]
   int* status;            // [0] error bits
-  unsigned long long* cand;  // [0] pair candidates evaluated, [1] single candidates
+  int* nprod;             // [b] productive iterations (a parent was expanded) of search b
   // final merge (Alg. 4) per instance
   int* mrg_ref;           // [inst][K1] search*K1 + slot
   uint64_t* mrg_src;      // [inst][K1]
@@ -89,6 +89,19 @@ __host__ __device__ inline int pad_of(int n) { return (n + kPad - 1) / kPad * kP
 __host__ __device__ inline uint32_t pair_index(int n, int i, int j) {
   return (uint32_t)n + (uint32_t)((long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1));
 }
+// Survivor entry written by the candidate filters (singles by k_bound, pairs by the scans):
+// bits 0-31 candidate index c, bits 32-43 site i, bits 44-55 site j, bit 56 set for a single
+// flip (no j). n <= 4096 keeps i and j in 12 bits.
+__host__ __device__ inline unsigned long long surv_entry(uint32_t c, int i, int j) {
+  return (unsigned long long)c | ((unsigned long long)(unsigned)i << 32) |
+         (j < 0 ? (1ull << 56) : ((unsigned long long)(unsigned)j << 44));
+}
+__host__ __device__ inline void surv_decode(unsigned long long e, uint32_t& c, int& i, int& j) {
+  c = (uint32_t)e;
+  i = (int)((e >> 32) & 0xfffu);
+  j = ((e >> 56) & 1u) ? -1 : (int)((e >> 44) & 0xfffu);
+}
+
 __device__ inline void decode_candidate(int n, uint32_t c, int& i, int& j) {
   if (c < (uint32_t)n) { i = (int)c; j = -1; return; }
   long long r = (long long)c - n;
@@ -147,18 +160,19 @@ int mlp_max_n(const qis_mlp* m);
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,
-                             cudaStream_t s);
+                             int nt, cudaStream_t s);
 int gemm_tile_n(int R, int digits);
 cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
                             float* J4, long long* hq, cudaStream_t s);
 cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s);
+cudaError_t launch_hash_list(const DevPtrs& P, int b, int count, cudaStream_t s);
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s);
-cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, cudaStream_t s);
+cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, int RG, cudaStream_t s);
 cudaError_t launch_scan64(const DevPtrs& P, const int4* work, int n_work, cudaStream_t s);
-void scan_tasks_for(int inst, int n, std::vector<int4>& out);
+void scan_tasks_for(int inst, int n, int nc_max, int R, int RG, std::vector<int4>& out);
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_final_merge(const DevPtrs& P, cudaStream_t s);
 size_t merge_smem(int K1, int cap);

@@ -12,6 +12,8 @@
 // One CTA computes a 128-row tile (TMEM lanes = sites i) x N_T searches for all digits:
 //   warp 0 lane 0 : TMA producer (digit tiles of 128 x 64 and the spin tile N_T x 64 per stage)
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::f16, M=128, N=N_T, K=16), commits free stages
+//   warps 2-3     : stage the parent spins and active flags of the tile's searches in shared
+//                   memory meanwhile, so the epilogue issues no dependent global loads
 //   all 4 warps   : epilogue, tcgen05.ld of their 32 TMEM lanes, exact int64 combination.
 // Every wait is bounded (2 s of %globaltimer); on timeout the CTA raises kStatTimeout, drains
 // what it issued (again bounded), frees its TMEM and returns.
@@ -110,6 +112,8 @@ __global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CU
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
+  __shared__ uint64_t s_pw[256][2];   // parent spin words of the tile's rows, per search of the tile
+  __shared__ int s_act[256];          // active flag per search of the tile
   int ncols = 32;
   while (ncols < D * NT) ncols <<= 1;
 
@@ -156,6 +160,17 @@ __global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CU
     if (*(volatile int*)&s_err) {
       for (int kc = max(0, issued - S); kc < issued; ++kc)
         mbar_wait(&full[kc % S], (kc / S) & 1, gtimer());
+    }
+  } else if (warp >= 2) {
+    // ---------------- warps 2-3: stage the epilogue's per-search inputs while the GEMM runs
+    const int w0 = m0 >> 6;
+    for (int t = threadIdx.x - 64; t < NT; t += 64) {
+      const int r = n0 + t;
+      const long long b = d.first_search + r;
+      const bool valid = r < G.R;
+      s_act[t] = valid ? P.active[b] : 0;
+      s_pw[t][0] = valid ? P.par_bits[b * G.Wmax + w0] : 0ull;
+      s_pw[t][1] = (valid && w0 + 1 < G.Wmax) ? P.par_bits[b * G.Wmax + w0 + 1] : 0ull;
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer
@@ -208,21 +223,21 @@ __global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CU
         wdig *= 4096;
       }
       if (i < d.n_pad) {
+        const int row = i - m0;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const int r = n0 + c0 + u;
-          if (r >= G.R) continue;
-          const int b = d.first_search + r;
-          if (!P.active[b]) continue;
+          const int t = c0 + u;
+          if (n0 + t >= G.R || !s_act[t]) continue;
+          const long long b = d.first_search + n0 + t;
           long long aq = 0;
           float2 as = make_float2(0.f, 0.f);
           if (i < d.n) {
-            const int sg = __half2float(P.S16[(long long)b * P.NP + i]) < 0.f;   // coalesced over i
+            const int sg = (int)((s_pw[t][row >> 6] >> (row & 63)) & 1ull);   // sigma_i of the parent
             aq = sg ? 2 * acc[u] : -2 * acc[u];
-            as = make_float2((float)ldexp((double)aq, -d.q), sg ? -1.f : 1.f);
+            as = make_float2((float)((double)aq * d.inv_scale), sg ? -1.f : 1.f);   // 2^-q: exact
           }
-          P.aq[(long long)b * P.NP + i] = aq;
-          P.as32[(long long)b * P.NP + i] = as;
+          P.aq[b * P.NP + i] = aq;
+          P.as32[b * P.NP + i] = as;
         }
       }
     }
@@ -277,8 +292,9 @@ size_t gemm_smem(int digits, int nt) {
   return (size_t)gemm_stages(digits, nt) * (digits * kTileBytesA + nt * kKC * 2) + 1024;
 }
 
+// nt: searches per tile (multiple of 16, digits_max * nt <= 512), or 0 for gemm_tile_n's choice.
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,
-                             cudaStream_t s) {
+                             int nt, cudaStream_t s) {
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
@@ -292,7 +308,7 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
   G.Wmax = P.Wmax;
   G.digits_max = digits_max;
   G.plane_rows = plane_rows;
-  G.NT = gemm_tile_n(P.R, digits_max);
+  G.NT = nt > 0 ? nt : gemm_tile_n(P.R, digits_max);
   G.stages = gemm_stages(digits_max, G.NT);
   e = make_map(&mB, S16, (uint64_t)P.NP, (uint64_t)max_inst * P.R, (uint32_t)G.NT);
   if (e != cudaSuccess) return e;

@@ -220,4 +220,25 @@ cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- imported lists
+// Zobrist hash of the first `count` slots of search b's list (the bits were copied in by the
+// host): the same key the merge and the dedup use for states generated on the device.
+__global__ void k_hash_list(DevPtrs P, int b, int count) {
+  const InstDesc d = P.inst[b / P.R];
+  const long long base = (long long)b * P.K1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const uint64_t* bits = P.lst_bits + (base + k) * P.Wmax;
+    uint64_t h = 0;
+    for (int i = 0; i < d.n; ++i)
+      if ((bits[i >> 6] >> (i & 63)) & 1ull) h ^= P.zob[i];
+    P.lst_hash[base + k] = h;
+  }
+}
+
+cudaError_t launch_hash_list(const DevPtrs& P, int b, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_hash_list<<<(count + 127) / 128, 128, 0, s>>>(P, b, count);
+  return cudaGetLastError();
+}
+
 }  // namespace qis

@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
       P.lst_used[base + sel] = 1;
       P.par_E[b] = P.lst_E[base + sel];
       P.par_hash[b] = P.lst_hash[base + sel];
-      atomicAdd(P.cand, (unsigned long long)d.n * (d.n - 1) / 2);
-      atomicAdd(P.cand + 1, (unsigned long long)d.n);
+      P.nprod[b] += 1;   // n(n-1)/2 pair and n single candidates, counted on query
     }
   }
   if (sel >= 0) {
@@ -223,9 +222,17 @@ __device__ K radix_select(const K* keys, int cnt, int rank, int* hist) {
   for (int shift = kBits - 8; shift >= 0; shift -= 8) {
     for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      const K k = keys[t];
-      if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255)], 1);
+    // warp-aggregated: the lanes of a warp that fall into one bin add once (most keys share
+    // their leading bits, so plain atomics would serialise on one counter)
+    for (int t0 = 0; t0 < cnt; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      const bool in = t < cnt && (keys[t] & mask) == prefix;
+      const unsigned act = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int bin = (int)((keys[t] >> shift) & 255);
+        const unsigned peers = __match_any_sync(act, bin);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+      }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -354,10 +361,17 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
         if (t < mm) {
           i = sites[t];
         } else {
-          int r = t - mm, x = 0;
-          while (r >= mm - 1 - x) { r -= mm - 1 - x; ++x; }
+          // pair rank r -> (x, y), x < y < mm: row x starts at x mm - x(x+1)/2 (closed form,
+          // then corrected by one step either way)
+          const int r = t - mm;
+          const float q = 2.f * mm - 1.f;
+          int x = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)r, 0.f))) * 0.5f);
+          x = max(0, min(x, mm - 2));
+          while (x > 0 && x * mm - x * (x + 1) / 2 > r) --x;
+          while (x < mm - 2 && (x + 1) * mm - (x + 1) * (x + 2) / 2 <= r) ++x;
+          const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
           i = sites[x];
-          j = sites[x + 1 + r];
+          j = sites[y];
           if (i > j) { const int tmp = i; i = j; j = tmp; }
         }
         if (fp64) {
@@ -397,7 +411,9 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
       const double t2 = U + 2.0 * delta;
       s_thr = fl32_up(fmin(t1, t2));
       P.thr32[b] = s_thr;
-      P.sctl[b] = make_float4(s_thr, 1.f, 0.f, 0.f);
+      // lower bound of every pair term y_ij = fl(a_j +- 4J~_ij) of the scan (|4J~| <= j4max,
+      // rounding monotone): rows with c_i below it are skipped
+      P.sctl[b] = make_float4(s_thr, 1.f, __fsub_rd(amin, d.j4max), 0.f);
     }
   }
   __syncthreads();
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     }
     if (ok) {
       const int slot = atomicAdd(P.surv_cnt + b, 1);
-      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = (uint32_t)i;
+      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry((uint32_t)i, i, -1);
     }
   }
 }
@@ -473,7 +489,7 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
         const double e = __dadd_rn(Ep, dE64(ai, ac_s[tx * 4 + c], Jt[ty * 4 + r][tx * 4 + c], flip));
         if (e < T && e <= cap) {
           const int slot = atomicAdd(P.surv_cnt + b, 1);
-          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = pair_index(n, i, j);
+          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(pair_index(n, i, j), i, j);
         }
       }
     }

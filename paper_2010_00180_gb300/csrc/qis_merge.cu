@@ -1,15 +1,15 @@
 // qis_merge.cu -- the exact list update of one iteration (Alg. 2), one block per search.
 //
-// Input: the survivor buffer of the search (single flips from k_bound, pair-hit records from
-// the FP32 scan, or plain pair indices from the FP64 scan). Output: the new kept list.
+// Input: the survivor buffer of the search (entries {c, i, j} of the single flips from k_bound
+// and of the pairs that passed the scan's filter). Output: the new kept list.
 //
-//  1. Records are expanded with the scan's own FP32 test, so exactly the pairs the filter
-//     passed become candidates.
-//  2. Every candidate gets its exact energy: in the split modes from exact fixed-point
+//  1. Every candidate gets its exact energy: in the split modes from exact fixed-point
 //     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), in the FP64 mode with the
 //     defining FP64 arithmetic. Candidates with E' >= T (the last kept energy, Alg. 2: strict
 //     <) are dropped, as are duplicates of a kept state (Zobrist hash table + full compare:
 //     the binary search of Alg. 2).
+//  2. The kept candidates are sorted by (E, c) (bitonic network: in registers and shuffles for
+//     up to 256 candidates, in shared memory beyond).
 //  3. New list = first K+1 of (old list, new candidates) by (E, stamp): old entries precede
 //     new ones of equal energy (they arrived earlier), new ones are ordered by candidate
 //     index c (the order of the Alg. 3 loop). Slots of evicted entries are reused.
@@ -46,26 +46,59 @@ __device__ int block_exclusive_sum(int v, int* wsum /* [33] */, int* total) {
   return before;
 }
 
-template <typename K>
-__device__ void bitonic_sort(K* key, uint32_t* val, int n2) {
+// (key, c) order of candidates: energy key, ties by candidate index c (the Alg. 3 loop order).
+__device__ __forceinline__ bool kc_less(unsigned long long ka, unsigned long long ea, unsigned long long kb,
+                                        unsigned long long eb) {
+  return ka < kb || (ka == kb && (uint32_t)ea < (uint32_t)eb);
+}
+
+// Ascending bitonic sort of n2 (power of two) (key, entry) pairs in shared memory, any size.
+__device__ void bitonic_sort_smem(unsigned long long* key, unsigned long long* ent, int n2) {
   for (int k = 2; k <= n2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int t = threadIdx.x; t < n2; t += blockDim.x) {
         const int u = t ^ j;
         if (u > t) {
-          const K a = key[t], c = key[u];
-          const uint32_t va = val[t], vc = val[u];
-          const bool gt = (a > c) || (a == c && va > vc);
+          const unsigned long long a = key[t], c = key[u], va = ent[t], vc = ent[u];
           const bool up = (t & k) == 0;
-          if (gt == up) {
+          if (kc_less(c, vc, a, va) == up) {
             key[t] = c; key[u] = a;
-            val[t] = vc; val[u] = va;
+            ent[t] = vc; ent[u] = va;
           }
         }
       }
       __syncthreads();
     }
   }
+}
+
+// Ascending bitonic sort of n2 <= blockDim.x pairs (32 <= n2, power of two), one per thread in
+// registers: partners closer than 32 are exchanged with shuffles, farther ones through shared
+// memory. Every thread of the block calls it (barriers); warps at or beyond n2 only pass them.
+__device__ void bitonic_sort_regs(unsigned long long& key, unsigned long long& ent, int n2,
+                                  unsigned long long* xk, unsigned long long* xe) {
+  const int t = threadIdx.x;
+  const bool on = t < n2;   // warp-uniform: n2 is a multiple of 32
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      unsigned long long ko, eo;
+      if (j >= 32) {
+        __syncthreads();
+        if (on) { xk[t] = key; xe[t] = ent; }
+        __syncthreads();
+        if (on) { ko = xk[t ^ j]; eo = xe[t ^ j]; }
+      } else if (on) {
+        ko = __shfl_xor_sync(0xffffffffu, key, j);
+        eo = __shfl_xor_sync(0xffffffffu, ent, j);
+      }
+      if (on) {
+        const bool want_min = ((t & j) == 0) == ((t & k) == 0);
+        const bool take = want_min ? kc_less(ko, eo, key, ent) : kc_less(key, ent, ko, eo);
+        if (take) { key = ko; ent = eo; }
+      }
+    }
+  }
+  __syncthreads();
 }
 
 __device__ inline uint64_t flip_mask(int x, int i, int j) {
@@ -81,26 +114,27 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) return;
   const InstDesc d = P.inst[b / P.R];
-  const int n = d.n, W = d.W, K1 = P.K1;
+  const int W = d.W, K1 = P.K1;
+  const int lane = threadIdx.x & 31;
   const long long base = (long long)b * K1;
   const int S = P.surv_cnt[b];
   if (S > P.cap) {
     if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
     return;
   }
-  const int PC = next_pow2(P.cap);
+  const int PC = next_pow2(max(P.cap, kMergeThreads));
   const int HT = next_pow2(2 * K1);
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* okey = reinterpret_cast<unsigned long long*>(smem);   // [K1]
   uint64_t* oH = reinterpret_cast<uint64_t*>(okey + K1);                    // [K1]
-  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);  // [PC]
-  uint32_t* sc = reinterpret_cast<uint32_t*>(sk + PC);                      // [PC]
-  int* oslot = reinterpret_cast<int*>(sc + PC);                             // [K1]
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);  // [PC] keys of valid candidates
+  unsigned long long* se = sk + PC;                                         // [PC] their survivor entries
+  int* oslot = reinterpret_cast<int*>(se + PC);                             // [K1]
   int* occ = oslot + K1;                                                    // [K1]
   int* freel = occ + K1;                                                    // [K1]
   int* htab = freel + K1;                                                   // [HT]
   __shared__ uint64_t pb[kMaxN / 64];
-  __shared__ int s_nc, s_nvalid, wsum[33], s_total;
+  __shared__ int s_nv, wsum[33], s_total;
   const int cnt = P.lst_count[b];
   const double T = (cnt == K1) ? P.lst_E[base + P.lst_ord[base + K1 - 1]] : INFINITY;
   const double Ep = P.par_E[b];
@@ -109,10 +143,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = -1;
   for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
-  if (threadIdx.x == 0) {
-    s_nc = 0;
-    s_nvalid = 0;
-  }
+  if (threadIdx.x == 0) s_nv = 0;
   __syncthreads();
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const int slot = P.lst_ord[base + r];
@@ -123,69 +154,24 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     uint32_t pos = hmix(h) & (HT - 1);
     while (atomicCAS(&htab[pos], -1, r) != -1) pos = (pos + 1) & (HT - 1);
   }
-  // ---- 1. expand scan records into candidates (the scan's FP32 test, verbatim)
-  {
-    const float2* as = P.as32 + (long long)b * P.NP;
-    const unsigned long long* sv = P.surv + (long long)b * P.cap;
-    for (int t = threadIdx.x; t < S; t += blockDim.x) {
-      const unsigned long long e = sv[t];
-      if (!(e >> 63)) {
-        const int slot = atomicAdd(&s_nc, 1);
-        if (slot < PC) sc[slot] = (uint32_t)e;
-        continue;
-      }
-      // record: rows i0 + r for the bits r of hm; columns jb + 32k, k < nc
-      const int i0 = (int)(e & 0xffff), jb = (int)((e >> 16) & 0xffff);
-      const int nc = (int)((e >> 32) & 0x1f);
-      unsigned hm = (unsigned)((e >> 37) & 0xff);
-      const float2* cs = P.cs32 + (long long)b * P.NP;
-      while (hm) {
-        const int r = __ffs(hm) - 1;
-        hm &= hm - 1;
-        const int i = i0 + r;
-        const float2 ri = cs[i];                 // {thr - a_i, s_i}, the scan's row bound
-        const float* J4row = P.J4 + d.off_mat + (long long)i * d.n_pad;
-        float y[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = jb + 32 * k;
-          y[k] = __int_as_float(0x7fc00000);   // NaN: never <= c, even when c = +inf
-          if (k < nc && j > i && j < n) {
-            const float2 vj = as[j];
-            const float j4 = J4row[j];
-            y[k] = fmaf(ri.y < 0.f ? -j4 : j4, vj.y, vj.x);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (y[k] <= ri.x) {
-            const int slot = atomicAdd(&s_nc, 1);
-            if (slot < PC) sc[slot] = pair_index(n, i, jb + 32 * k);
-          }
-        }
-      }
-    }
-  }
   __syncthreads();
-  const int NCAND = s_nc;
-  if (NCAND > PC) {
-    if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
-    return;
-  }
-  const int P2 = next_pow2(max(NCAND, 1));
-  // ---- 2. exact energies, threshold, duplicates
+  // ---- 1. exact energy of every survivor of the filter; keep E' < T (strict, Alg. 2) that
+  //         is not a kept state (Zobrist hash table + full compare: the binary search of
+  //         Alg. 2); compact the kept ones (warp-aggregated)
   const long long Epq = fp64 ? 0 : __double2ll_rn(ldexp(Ep, d.q));
   const long long Tq = (fp64 || T == INFINITY) ? LLONG_MAX : __double2ll_rn(ldexp(T, d.q));
-  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
-    unsigned long long kk = ~0ull;
-    uint32_t c = 0xffffffffu;
-    if (t < NCAND) {
-      c = sc[t];
+  const unsigned long long* sv = P.surv + (long long)b * P.cap;
+  for (int t0 = 0; t0 < S; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    bool keep = false;
+    unsigned long long kk = 0, ent = 0;
+    if (t < S) {
+      ent = sv[t];
+      uint32_t c;
       int i, j;
-      decode_candidate(n, c, i, j);
+      surv_decode(ent, c, i, j);
       const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
       double e;
-      bool keep;
       if (fp64) {
         const double* a = P.a64 + (long long)b * P.NP;
         const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
@@ -210,24 +196,53 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
           const uint64_t* sbits = P.lst_bits + (base + oslot[r]) * P.Wmax;
           bool same = true;
           for (int x = 0; x < W && same; ++x) same = sbits[x] == (pb[x] ^ flip_mask(x, i, j));
-          if (same) keep = false;   // duplicate of a kept state (Alg. 2 binary search hit)
+          if (same) keep = false;   // duplicate of a kept state
         }
       }
+      kk = dkey(e);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (bal) {
+      int wb = 0;
+      if (lane == 0) wb = atomicAdd(&s_nv, __popc(bal));
+      wb = __shfl_sync(0xffffffffu, wb, 0);
       if (keep) {
-        kk = dkey(e);
-        atomicAdd(&s_nvalid, 1);
-      } else {
-        c = 0xffffffffu;
+        const int slot = wb + __popc(bal & ((1u << lane) - 1));
+        sk[slot] = kk;          // slot < S <= cap <= PC
+        se[slot] = ent;
       }
     }
-    sk[t] = kk;
-    sc[t] = c;
   }
   __syncthreads();
-  // ---- 3. order and truncate
-  bitonic_sort(sk, sc, P2);
-  const int nv = s_nvalid;
-  // old entry o -> rank o + #(new with E < E_o); new entry p -> p + #(old with E <= E_p)
+  const int nv = s_nv;
+  // ---- 2. order the kept candidates by (E, c)
+  if (nv > 1) {
+    const int n2 = max(32, next_pow2(nv));
+    if (n2 <= (int)blockDim.x) {
+      unsigned long long key = ~0ull, ent = ~0ull;   // padding sorts last
+      if ((int)threadIdx.x < nv) {
+        key = sk[threadIdx.x];
+        ent = se[threadIdx.x];
+      }
+      __syncthreads();
+      bitonic_sort_regs(key, ent, n2, sk, se);
+      if ((int)threadIdx.x < nv) {
+        sk[threadIdx.x] = key;
+        se[threadIdx.x] = ent;
+      }
+    } else {
+      const int m2 = next_pow2(nv);
+      for (int t = nv + threadIdx.x; t < m2; t += blockDim.x) {
+        sk[t] = ~0ull;
+        se[t] = ~0ull;
+      }
+      __syncthreads();
+      bitonic_sort_smem(sk, se, m2);
+    }
+  }
+  __syncthreads();
+  // ---- 3. merge with the old list: old entry o -> rank o + #(new with E < E_o) (old entries
+  //         precede new ones of equal energy); new entry p -> p + #(old with E <= E_p)
   for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
     const unsigned long long ko = okey[o];
     int lo = 0, hi = nv;
@@ -259,9 +274,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     const int rank = p + lo;
     if (rank >= K1) continue;
     const int slot = freel[p];   // the new entries kept are the first ones in sorted order
-    const uint32_t c = sc[p];
+    uint32_t c;
     int i, j;
-    decode_candidate(n, c, i, j);
+    surv_decode(se[p], c, i, j);
     uint64_t* dst = P.lst_bits + (base + slot) * P.Wmax;
     for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
     P.lst_E[base + slot] = dkey_inv(kp);
@@ -278,8 +293,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
 }
 
 size_t merge_smem(int K1, int cap) {
-  const int PC = next_pow2(cap), HT = next_pow2(2 * K1);
-  return (size_t)K1 * 16 + (size_t)PC * 12 + (size_t)K1 * 12 + (size_t)HT * 4;
+  const int PC = next_pow2(cap > kMergeThreads ? cap : kMergeThreads), HT = next_pow2(2 * K1);
+  return (size_t)K1 * 16 + (size_t)PC * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {

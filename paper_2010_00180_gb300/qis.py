@@ -21,6 +21,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "C
 # the entry points of include/qis.h
 SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_clear_instances",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
+           "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
+           "qis_get_tuning", "qis_set_tuning", "qis_autotune",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
            "qis_select_candidates_noalloc",
@@ -40,6 +42,10 @@ class QISError(RuntimeError):
 class MLPConfig(C.Structure):
     _fields_ = [("hidden", C.c_int), ("max_sites", C.c_int), ("batch", C.c_int), ("max_n", C.c_int),
                 ("device", C.c_int), ("seed", C.c_uint64)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("scan_chunk_nc", C.c_int), ("scan_search_group", C.c_int), ("gemm_tile_searches", C.c_int)]
 
 
 class Config(C.Structure):
@@ -71,6 +77,13 @@ def load():
         "qis_reset": (I, [P]),
         "qis_iterate": (I, [P, I, C.POINTER(I)]),
         "qis_search_list": (I, [P, I, I, P, P, P, P, C.POINTER(I)]),
+        "qis_set_search_list": (I, [P, I, I, I, P, P, P, P, I]),
+        "qis_save": (I, [P, C.c_char_p]),
+        "qis_instance_n": (I, [P, I, C.POINTER(I)]),
+        "qis_get_tuning": (I, [P, C.POINTER(Tuning)]),
+        "qis_set_tuning": (I, [P, C.POINTER(Tuning)]),
+        "qis_autotune": (I, [P, I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
+        "qis_load": (I, [P, C.c_char_p]),
         "qis_topk_states": (I, [P, I, I, P, P, P, C.POINTER(I)]),
         "qis_merge": (I, [P]),
         "qis_energies": (I, [P, I, I, P, P]),
@@ -204,6 +217,47 @@ class Context:
                                              C.byref(cnt)))
         c = cnt.value
         return dict(bits=bits[:c], E=E[:c], used=used[:c], stamp=stamp[:c], count=c)
+
+    def set_search_list(self, iid: int, r: int, bits, E, used=None, stamp=None, t: int = 0):
+        """Replace the kept list of search r (entries in list order), e.g. with a list computed
+        by another process, before qis_merge / topk_states."""
+        n = self.n[iid]
+        bits = np.ascontiguousarray(bits, np.uint64).reshape(-1, words(n))
+        E = np.ascontiguousarray(E, np.float64)
+        cnt = bits.shape[0]
+        if E.shape != (cnt,):
+            raise ValueError("E must have one energy per state")
+        u = None if used is None else np.ascontiguousarray(used, np.uint8)
+        st = None if stamp is None else np.ascontiguousarray(stamp, np.uint64)
+        self._check(self.lib.qis_set_search_list(self.h, iid, r, cnt, _ptr(bits), _ptr(E),
+                                                 _ptr(u) if u is not None else None,
+                                                 _ptr(st) if st is not None else None, int(t)))
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.lib.qis_get_tuning(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def set_tuning(self, scan_chunk_nc: int = 8, scan_search_group: int = 0, gemm_tile_searches: int = 0):
+        t = Tuning(scan_chunk_nc, scan_search_group, gemm_tile_searches)
+        self._check(self.lib.qis_set_tuning(self.h, C.byref(t)))
+
+    def autotune(self, iters: int = 8) -> dict:
+        """Pick the fastest launch shapes for the current instances (resets every search)."""
+        t, ms = Tuning(), C.c_double()
+        self._check(self.lib.qis_autotune(self.h, iters, C.byref(t), C.byref(ms)))
+        return {k: getattr(t, k) for k, _ in Tuning._fields_} | {"ms": ms.value, "iters": iters}
+
+    def save(self, path: str):
+        self._check(self.lib.qis_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Restore a qis_save checkpoint into this (empty) context."""
+        self._check(self.lib.qis_load(self.h, os.fsencode(path)))
+        self.n = {}
+        n = C.c_int()
+        while self.lib.qis_instance_n(self.h, len(self.n), C.byref(n)) == 0:
+            self.n[len(self.n)] = n.value
 
     def topk_states(self, iid: int, k: int) -> dict:
         n = self.n[iid]
