@@ -204,6 +204,13 @@ int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t);
  * (as qis_reset). best / best_ms (may be NULL) receive the choice and its time. */
 int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms);
 
+/* Pair terms the candidate scan evaluated one by one since the context was created: in the
+ * split modes the scan skips every row whose bound c_i = thr - a_i lies below a lower bound
+ * of all its pair terms, and counts (rows evaluated) x (chunk width, masked entries
+ * included); in QIS_FP64 every pair is evaluated (the qis_candidate_count pairs). The pairs
+ * of qis_candidate_count are all decided exactly either way. Synchronises the stream. */
+int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs);
+
 /* The library's CUDA stream (a cudaStream_t), so callers can order their own work and
  * CUDA events with respect to the library's kernels. */
 int qis_get_stream(qis_ctx* ctx, void** stream);

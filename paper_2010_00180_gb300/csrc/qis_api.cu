@@ -341,7 +341,6 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     }
     ALLOC(P.thr32, B);
     if (ctx->mode != QIS_FP64) {
-      ALLOC(P.cs32, B * NP);
       ALLOC(P.sctl, B);
     }
     ALLOC(P.thrE, B);
@@ -351,6 +350,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.init_bits, B * W);
     ALLOC(P.status, 4);
     ALLOC(P.nprod, B);
+    ALLOC(P.eval_cnt, 64);
     ALLOC(P.mrg_ref, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_src, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_count, ctx->max_inst);
@@ -1029,6 +1029,24 @@ int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
   if (rc) return rc;
   if (pairs) *pairs = ctx->cand_acc[0] + c[0];
   if (singles) *singles = ctx->cand_acc[1] + c[1];
+  return 0;
+}
+
+int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs) {
+  if (!ctx || !pairs) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->mode == QIS_FP64) {   // the plain form evaluates every pair
+    uint64_t c[2];
+    int rc = count_candidates(ctx, c);
+    if (rc) return rc;
+    *pairs = ctx->cand_acc[0] + c[0];
+    return 0;
+  }
+  unsigned long long v[64];
+  CK(cudaMemcpy(v, ctx->P.eval_cnt, sizeof(v), cudaMemcpyDeviceToHost));
+  uint64_t t = 0;
+  for (int k = 0; k < 64; ++k) t += v[k];
+  *pairs = t;
   return 0;
 }
 

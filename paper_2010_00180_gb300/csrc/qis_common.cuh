@@ -66,7 +66,6 @@ struct DevPtrs {
   float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
-  float2* cs32;           // [b][NP] {fl32(thr - a_i), s_i}: the scan's per-row bound (split modes)
   float4* sctl;           // [b] {thr, active, 0, 0}: staged by the scan with the row data
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
@@ -76,6 +75,7 @@ struct DevPtrs {
   uint64_t* init_bits;    // [b][Wmax]
   int* status;            // [0] error bits
   int* nprod;             // [b] productive iterations (a parent was expanded) of search b
+  unsigned long long* eval_cnt;  // [64] pair terms the FP32 scan evaluated (live rows x chunk width)
   // final merge (Alg. 4) per instance
   int* mrg_ref;           // [inst][K1] search*K1 + slot
   uint64_t* mrg_src;      // [inst][K1]
@@ -146,6 +146,79 @@ __device__ inline double dE64(double ai, double aj, double j, int flip) {
 
 __device__ inline double dkey_inv(unsigned long long k) {
   return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Warp-parallel search of a 256-bin histogram: the bin holding the rank-th element (0-based),
+// and the rank of that element within the bin. Called by one full warp.
+__device__ inline void find_bin(const int* hist, int rank, int& bin, int& within) {
+  const int lane = threadIdx.x & 31;
+  int loc[8], s = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    loc[u] = hist[lane * 8 + u];
+    s += loc[u];
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, incl > rank);
+  const int L = m ? __ffs(m) - 1 : 31;
+  int r = rank - __shfl_sync(0xffffffffu, incl - s, L);
+  int bb = 255;
+  if (lane == L) {
+    int u = 0;
+    for (; u < 7; ++u) {
+      if (r < loc[u]) break;
+      r -= loc[u];
+    }
+    bb = L * 8 + u;
+  }
+  bin = __shfl_sync(0xffffffffu, bb, L);
+  within = __shfl_sync(0xffffffffu, r, L);
+}
+
+// Block-wide radix select: the rank-th smallest (0-based) of `cnt` keys in smem, 8 bits per
+// pass from the top. `hist` holds 256 counters. Every thread of the block must call it.
+template <typename K>
+__device__ K radix_select(const K* keys, int cnt, int rank, int* hist) {
+  __shared__ K s_prefix;
+  __shared__ int s_rank;
+  K prefix = 0, mask = 0;
+  constexpr int kBits = 8 * sizeof(K);
+  for (int shift = kBits - 8; shift >= 0; shift -= 8) {
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    // warp-aggregated: the lanes of a warp that fall into one bin add once (most keys share
+    // their leading bits, so plain atomics would serialise on one counter)
+    for (int t0 = 0; t0 < cnt; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      const bool in = t < cnt && (keys[t] & mask) == prefix;
+      const unsigned act = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int bin = (int)((keys[t] >> shift) & 255);
+        const unsigned peers = __match_any_sync(act, bin);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      int dgt, r;
+      find_bin(hist, rank, dgt, r);
+      if (threadIdx.x == 0) {
+        s_prefix = prefix | ((K)dgt << shift);
+        s_rank = r;
+      }
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    rank = s_rank;
+    mask |= (K)255 << shift;
+    __syncthreads();
+  }
+  return prefix;
 }
 
 // Message returned by qis_last_error(NULL) (calls that have no context).

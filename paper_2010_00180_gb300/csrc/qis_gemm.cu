@@ -9,12 +9,15 @@
 // field of site i for search r is then fq = hq_i + sum_d 4096^d F_d[i][r] (int64) and the
 // single-flip energy change a_i = -2 s_i f_i (Sec. III) follows exactly.
 //
-// One CTA computes a 128-row tile (TMEM lanes = sites i) x N_T searches for all digits:
-//   warp 0 lane 0 : TMA producer (digit tiles of 128 x 64 and the spin tile N_T x 64 per stage)
-//   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::f16, M=128, N=N_T, K=16), commits free stages
-//   warps 2-3     : stage the parent spins and active flags of the tile's searches in shared
-//                   memory meanwhile, so the epilogue issues no dependent global loads
-//   all 4 warps   : epilogue, tcgen05.ld of their 32 TMEM lanes, exact int64 combination.
+// Persistent kernel, one CTA per SM, walking 128-row x NT-search tiles of all instances:
+//   warp 0 lane 0 : TMA producer (digit tiles of 128 x 64 and the spin tile NT x 64 per stage),
+//                   one ring of stages running across tile boundaries
+//   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::f16, M=128, N=NT, K=16); tile number lt
+//                   accumulates into TMEM buffer lt % 2, so one tile's epilogue overlaps the
+//                   next tile's loads and MMAs
+//   warps 2-5     : epilogue, each on its TMEM lane quarter: stage the tile's parent spins and
+//                   active flags in shared memory, tcgen05.ld the accumulators, exact int64
+//                   combination of the digits, a_i = -2 s_i f_i; release the buffer.
 // Every wait is bounded (2 s of %globaltimer); on timeout the CTA raises kStatTimeout, drains
 // what it issued (again bounded), frees its TMEM and returns.
 #include <cuda.h>
@@ -25,12 +28,12 @@
 
 namespace qis {
 
-constexpr int kStages = 3;
+constexpr int kStages = 6;         // most stages of the smem ring
 constexpr int kKC = 64;              // K elements per stage (128 bytes of FP16: one swizzle row)
 constexpr int kTileBytesA = 128 * kKC * 2;
 
 struct GemmArgs {
-  int n_inst, R, NP, Wmax, NT, digits_max, stages;
+  int n_inst, R, NP, Wmax, NT, digits_max, stages, nbuf;
   long long plane_rows;              // rows of one digit plane in the A tensor map (max_inst * NP)
 };
 
@@ -93,34 +96,48 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CUtensorMap mapA,
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Barrier of the four epilogue warps that also ORs a flag over them: every epilogue thread gets
+// the same answer, so they all leave their loop at the same tile (no one is left at a barrier).
+__device__ __forceinline__ bool epi_vote(bool flag) {
+  uint32_t any;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(any) : "r"((uint32_t)flag) : "memory");
+  return any != 0;
+}
+
+// Persistent: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; tile t is
+// (instance t / tpi, 128-row block, NT-search block), tpi = (NP / 128) * ceil(R / NT); row blocks
+// at or past an instance's n_pad are skipped by every role alike.
+__global__ void __launch_bounds__(192, 1) k_fields_tc(const __grid_constant__ CUtensorMap mapA,
                                                       const __grid_constant__ CUtensorMap mapB, DevPtrs P,
                                                       GemmArgs G) {
-  const int inst = blockIdx.z;
-  const InstDesc d = P.inst[inst];
-  const int m0 = blockIdx.x * 128;
-  const int n0 = blockIdx.y * G.NT;
-  if (m0 >= d.n_pad || n0 >= G.R) return;               // uniform: before any barrier
-  const int NT = G.NT, D = d.digits, S = G.stages;
-  const int kc_total = d.n_pad / kKC;
+  const int NT = G.NT, S = G.stages, Dm = G.digits_max, nbuf = G.nbuf;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bytesB = NT * kKC * 2;
-  const int stage_bytes = G.digits_max * kTileBytesA + bytesB;   // same layout for every instance
+  const int stage_bytes = Dm * kTileBytesA + bytesB;   // same layout for every instance
+  const int n_mt = G.NP / 128, n_nt = (G.R + NT - 1) / NT, tpi = n_mt * n_nt;
+  const int n_tiles = G.n_inst * tpi;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], done;
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
   __shared__ uint64_t s_pw[256][2];   // parent spin words of the tile's rows, per search of the tile
   __shared__ int s_act[256];          // active flag per search of the tile
   int ncols = 32;
-  while (ncols < D * NT) ncols <<= 1;
+  while (ncols < nbuf * Dm * NT) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);   // one arrival per epilogue warp
     }
     mbar_init(&done, 1);
     s_err = 0;
@@ -138,112 +155,148 @@ __global__ void __launch_bounds__(128, 1) k_fields_tc(const __grid_constant__ CU
   const uint64_t t0 = gtimer();
 
   if (threadIdx.x == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int kc = 0; kc < kc_total; ++kc) {
-      const int s = kc % S;
-      if (kc >= S && !mbar_wait(&empty[s], ((kc / S) + 1) & 1, t0)) {
-        atomicOr(&s_err, 1);
-        break;
+    // ---------------- TMA producer: the k-blocks of every tile, one stage ring across tiles
+    int it = 0;
+    for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int*)&s_err; tile += gridDim.x) {
+      const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128, n0 = (tile % n_nt) * NT;
+      const InstDesc d = P.inst[inst];
+      if (m0 >= d.n_pad) continue;
+      const int kc_total = d.n_pad / kKC;
+      for (int kc = 0; kc < kc_total; ++kc, ++it) {
+        const int s = it % S;
+        if (it >= S && !mbar_wait(&empty[s], ((it / S) + 1) & 1, t0)) {
+          atomicOr(&s_err, 1);
+          break;
+        }
+        if (*(volatile int*)&s_err) break;
+        unsigned char* st = smem + s * stage_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)(d.digits * kTileBytesA + bytesB));
+        for (int dg = 0; dg < d.digits; ++dg)
+          tma_load_2d(st + dg * kTileBytesA, &mapA, kc * kKC,
+                      (int)(dg * G.plane_rows + (long long)inst * G.NP + m0), &full[s]);
+        tma_load_2d(st + Dm * kTileBytesA, &mapB, kc * kKC, d.first_search + n0, &full[s]);
       }
-      if (*(volatile int*)&s_err) break;
-      unsigned char* st = smem + s * stage_bytes;
-      mbar_expect_tx(&full[s], (uint32_t)(D * kTileBytesA + bytesB));
-      for (int dg = 0; dg < D; ++dg)
-        tma_load_2d(st + dg * kTileBytesA, &mapA, kc * kKC,
-                    (int)(dg * G.plane_rows + (long long)inst * G.NP + m0), &full[s]);
-      tma_load_2d(st + G.digits_max * kTileBytesA, &mapB, kc * kKC, d.first_search + n0, &full[s]);
-      ++issued;
     }
-    // drain: on an error, the last (at most S) issued stages may still be in flight; their
-    // full barriers are in the last phase armed for each stage, so parity waits are exact
+    // drain: after an error the last (at most S) issued stages may still be in flight; each
+    // stage's full barrier is in the phase armed last, so the parity waits are exact
     if (*(volatile int*)&s_err) {
-      for (int kc = max(0, issued - S); kc < issued; ++kc)
-        mbar_wait(&full[kc % S], (kc / S) & 1, gtimer());
-    }
-  } else if (warp >= 2) {
-    // ---------------- warps 2-3: stage the epilogue's per-search inputs while the GEMM runs
-    const int w0 = m0 >> 6;
-    for (int t = threadIdx.x - 64; t < NT; t += 64) {
-      const int r = n0 + t;
-      const long long b = d.first_search + r;
-      const bool valid = r < G.R;
-      s_act[t] = valid ? P.active[b] : 0;
-      s_pw[t][0] = valid ? P.par_bits[b * G.Wmax + w0] : 0ull;
-      s_pw[t][1] = (valid && w0 + 1 < G.Wmax) ? P.par_bits[b * G.Wmax + w0 + 1] : 0ull;
+      for (int k = max(0, it - S); k < it; ++k) mbar_wait(&full[k % S], (k / S) & 1, gtimer());
     }
   } else if (threadIdx.x == 32) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: tile lt accumulates into TMEM buffer lt % nbuf
     const uint32_t idesc = idesc_f16(NT);
-    int kc = 0;
-    for (; kc < kc_total; ++kc) {
-      const int s = kc % S;
-      if (!mbar_wait(&full[s], (kc / S) & 1, t0)) {
+    int it = 0, lt = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128;
+      const InstDesc d = P.inst[inst];
+      if (m0 >= d.n_pad) continue;
+      const int buf = lt % nbuf, use = lt / nbuf;
+      if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1, t0)) {
         atomicOr(&s_err, 2);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      unsigned char* st = smem + s * stage_bytes;
-      const uint32_t b_addr = smem_u32(st + G.digits_max * kTileBytesA);
-      for (int dg = 0; dg < D; ++dg) {
-        const uint32_t a_addr = smem_u32(st + dg * kTileBytesA);
+      const uint32_t acc = tmem + (uint32_t)(buf * Dm * NT);
+      const int kc_total = d.n_pad / kKC;
+      bool ok = true;
+      for (int kc = 0; kc < kc_total; ++kc, ++it) {
+        const int s = it % S;
+        if (!mbar_wait(&full[s], (it / S) & 1, t0)) {
+          atomicOr(&s_err, 2);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        unsigned char* st = smem + s * stage_bytes;
+        const uint32_t b_addr = smem_u32(st + Dm * kTileBytesA);
+        for (int dg = 0; dg < d.digits; ++dg) {
+          const uint32_t a_addr = smem_u32(st + dg * kTileBytesA);
 #pragma unroll
-        for (int k4 = 0; k4 < kKC / 16; ++k4)
-          mma_f16(tmem + dg * NT, sdesc(a_addr + k4 * 32), sdesc(b_addr + k4 * 32), idesc, (kc | k4) != 0);
+          for (int k4 = 0; k4 < kKC / 16; ++k4)
+            mma_f16(acc + dg * NT, sdesc(a_addr + k4 * 32), sdesc(b_addr + k4 * 32), idesc, (kc | k4) != 0);
+        }
+        mma_commit(&empty[s]);   // stage free once these MMAs have read it
       }
-      mma_commit(&empty[s]);   // stage free once these MMAs have read it
+      if (!ok) break;
+      mma_commit(&tfull[buf]);   // the tile's accumulators are complete
+      ++lt;
     }
-    mma_commit(&done);         // all issued MMAs complete -> done
-  }
-  // ---------------- epilogue (all warps)
-  const bool ok_done = mbar_wait(&done, 0, t0);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  __syncthreads();
-  const bool ok = ok_done && (s_err == 0);
-  if (!ok && threadIdx.x == 0) atomicOr(P.status, kStatTimeout);
-  if (ok) {
-    const int i = m0 + warp * 32 + lane;
-    const long long hq = (i < d.n) ? P.hq[d.off_vec + i] : 0;
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-      long long acc[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) acc[u] = hq;
-      long long wdig = 1;
-      for (int dg = 0; dg < D; ++dg) {
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dg * NT + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int u = 0; u < 16; ++u) acc[u] += wdig * (long long)__float2int_rn(__uint_as_float(v[u]));
-        wdig *= 4096;
+    mma_commit(&done);           // every MMA issued so far completes -> done
+    mbar_wait(&done, 0, gtimer());
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps 2-5: TMEM lane quarter (warp % 4), exact int64 fields
+    const int quarter = warp & 3, etid = threadIdx.x - 64;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128, n0 = (tile % n_nt) * NT;
+      const InstDesc d = P.inst[inst];
+      if (m0 >= d.n_pad) continue;
+      const int buf = lt % nbuf, use = lt / nbuf;
+      // the tile's per-search inputs, staged while its accumulators are being computed
+      epi_bar();   // every epilogue warp is done with the previous tile's copy
+      const int w0 = m0 >> 6;
+      for (int t = etid; t < NT; t += 128) {
+        const int r = n0 + t;
+        const long long b = d.first_search + r;
+        const bool valid = r < G.R;
+        s_act[t] = valid ? P.active[b] : 0;
+        s_pw[t][0] = valid ? P.par_bits[b * G.Wmax + w0] : 0ull;
+        s_pw[t][1] = (valid && w0 + 1 < G.Wmax) ? P.par_bits[b * G.Wmax + w0 + 1] : 0ull;
       }
-      if (i < d.n_pad) {
-        const int row = i - m0;
+      const bool ok = mbar_wait(&tfull[buf], use & 1, t0);
+      if (epi_vote(!ok || *(volatile int*)&s_err != 0)) {   // also orders the staging above
+        if (!ok) atomicOr(&s_err, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row = quarter * 32 + lane;
+      const int i = m0 + row;
+      const long long hq = (i < d.n) ? P.hq[d.off_vec + i] : 0;
+      for (int c0 = 0; c0 < NT; c0 += 16) {
+        long long acc[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int t = c0 + u;
-          if (n0 + t >= G.R || !s_act[t]) continue;
-          const long long b = d.first_search + n0 + t;
-          long long aq = 0;
-          float2 as = make_float2(0.f, 0.f);
-          if (i < d.n) {
-            const int sg = (int)((s_pw[t][row >> 6] >> (row & 63)) & 1ull);   // sigma_i of the parent
-            aq = sg ? 2 * acc[u] : -2 * acc[u];
-            as = make_float2((float)((double)aq * d.inv_scale), sg ? -1.f : 1.f);   // 2^-q: exact
+        for (int u = 0; u < 16; ++u) acc[u] = hq;
+        long long wdig = 1;
+        for (int dg = 0; dg < d.digits; ++dg) {
+          uint32_t v[16];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * Dm * NT + dg * NT + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[u] += wdig * (long long)__float2int_rn(__uint_as_float(v[u]));
+          wdig *= 4096;
+        }
+        if (i < d.n_pad) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int t = c0 + u;
+            if (n0 + t >= G.R || !s_act[t]) continue;
+            const long long b = d.first_search + n0 + t;
+            long long aq = 0;
+            float2 as = make_float2(0.f, 0.f);
+            if (i < d.n) {
+              const int sg = (int)((s_pw[t][row >> 6] >> (row & 63)) & 1ull);   // sigma_i of the parent
+              aq = sg ? 2 * acc[u] : -2 * acc[u];
+              as = make_float2((float)((double)aq * d.inv_scale), sg ? -1.f : 1.f);   // 2^-q: exact
+            }
+            P.aq[b * P.NP + i] = aq;
+            P.as32[b * P.NP + i] = as;
           }
-          P.aq[b * P.NP + i] = aq;
-          P.as32[b * P.NP + i] = as;
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[buf])) : "memory");
+      ++lt;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  if (s_err && threadIdx.x == 0) atomicOr(P.status, kStatTimeout);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
@@ -274,18 +327,30 @@ cudaError_t make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t r
 }
 }  // namespace
 
+// Searches per tile: a multiple of 16 with two accumulator sets in TMEM (2 * digits * nt <= 512
+// columns) when possible, else one; among those the one that pads R the least, then the widest.
 int gemm_tile_n(int R, int digits) {
-  int nt = 16;
-  while (nt < R && nt < 256) nt += 16;
-  while (nt > 16 && digits * nt > 512) nt -= 16;   // all digit accumulators must fit in TMEM
-  return nt;
+  int cap = 512 / (2 * digits) / 16 * 16;
+  if (cap < 16) cap = 512 / digits / 16 * 16;
+  if (cap > 256) cap = 256;
+  int best = 16, best_pad = 1 << 30;
+  for (int nt = 16; nt <= cap; nt += 16) {
+    const int pad = (R + nt - 1) / nt * nt;
+    if (pad < best_pad || (pad == best_pad && nt > best)) {
+      best = nt;
+      best_pad = pad;
+    }
+  }
+  return best;
 }
 
-// Three stages when two CTAs still fit on an SM, else two (two CTAs per SM let one CTA's
-// epilogue overlap the other's loads).
+// As many stages as fit in ~200 KB of shared memory (one CTA per SM), at most kStages.
 int gemm_stages(int digits, int nt) {
   const size_t per = (size_t)digits * kTileBytesA + (size_t)nt * kKC * 2;
-  return (3 * per + 1024 <= 110 * 1024) ? 3 : 2;
+  int st = (int)((200 * 1024) / per);
+  if (st > kStages) st = kStages;
+  if (st < 2) st = 2;
+  return st;
 }
 
 size_t gemm_smem(int digits, int nt) {
@@ -310,6 +375,7 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
   G.plane_rows = plane_rows;
   G.NT = nt > 0 ? nt : gemm_tile_n(P.R, digits_max);
   G.stages = gemm_stages(digits_max, G.NT);
+  G.nbuf = (2 * digits_max * G.NT <= 512) ? 2 : 1;   // double-buffered accumulators if TMEM holds two
   e = make_map(&mB, S16, (uint64_t)P.NP, (uint64_t)max_inst * P.R, (uint32_t)G.NT);
   if (e != cudaSuccess) return e;
   const size_t sm = gemm_smem(digits_max, G.NT);
@@ -319,8 +385,17 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
     if (e != cudaSuccess) return e;
     attr = sm;
   }
-  dim3 grid(P.NP / 128, (P.R + G.NT - 1) / G.NT, P.n_inst);
-  k_fields_tc<<<grid, 128, sm, s>>>(mA, mB, P, G);
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int tiles = P.n_inst * (P.NP / 128) * ((P.R + G.NT - 1) / G.NT);
+  const int grid = tiles < n_sm ? tiles : n_sm;
+  if (grid <= 0) return cudaSuccess;
+  k_fields_tc<<<grid, 192, sm, s>>>(mA, mB, P, G);
   return cudaGetLastError();
 }
 

@@ -179,79 +179,6 @@ __device__ inline float fkey_inv(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// Warp-parallel search of a 256-bin histogram: the bin holding the rank-th element (0-based),
-// and the rank of that element within the bin. Called by one full warp.
-__device__ inline void find_bin(const int* hist, int rank, int& bin, int& within) {
-  const int lane = threadIdx.x & 31;
-  int loc[8], s = 0;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    loc[u] = hist[lane * 8 + u];
-    s += loc[u];
-  }
-  int incl = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const unsigned m = __ballot_sync(0xffffffffu, incl > rank);
-  const int L = m ? __ffs(m) - 1 : 31;
-  int r = rank - __shfl_sync(0xffffffffu, incl - s, L);
-  int bb = 255;
-  if (lane == L) {
-    int u = 0;
-    for (; u < 7; ++u) {
-      if (r < loc[u]) break;
-      r -= loc[u];
-    }
-    bb = L * 8 + u;
-  }
-  bin = __shfl_sync(0xffffffffu, bb, L);
-  within = __shfl_sync(0xffffffffu, r, L);
-}
-
-// Block-wide radix select: the rank-th smallest (0-based) of `cnt` keys in smem, 8 bits per
-// pass from the top. `hist` holds 256 counters. Every thread of the block must call it.
-template <typename K>
-__device__ K radix_select(const K* keys, int cnt, int rank, int* hist) {
-  __shared__ K s_prefix;
-  __shared__ int s_rank;
-  K prefix = 0, mask = 0;
-  constexpr int kBits = 8 * sizeof(K);
-  for (int shift = kBits - 8; shift >= 0; shift -= 8) {
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
-    // warp-aggregated: the lanes of a warp that fall into one bin add once (most keys share
-    // their leading bits, so plain atomics would serialise on one counter)
-    for (int t0 = 0; t0 < cnt; t0 += blockDim.x) {
-      const int t = t0 + threadIdx.x;
-      const bool in = t < cnt && (keys[t] & mask) == prefix;
-      const unsigned act = __ballot_sync(0xffffffffu, in);
-      if (in) {
-        const int bin = (int)((keys[t] >> shift) & 255);
-        const unsigned peers = __match_any_sync(act, bin);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      int dgt, r;
-      find_bin(hist, rank, dgt, r);
-      if (threadIdx.x == 0) {
-        s_prefix = prefix | ((K)dgt << shift);
-        s_rank = r;
-      }
-    }
-    __syncthreads();
-    prefix = s_prefix;
-    rank = s_rank;
-    mask |= (K)255 << shift;
-    __syncthreads();
-  }
-  return prefix;
-}
-
 // ---------------------------------------------------------------- per-search bound
 constexpr int kSubSites = 64;   // at most this many low-a sites in the subset (2080 candidates)
 constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
@@ -272,7 +199,7 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
   __shared__ int hist[256];
   __shared__ int sites[kSubSites];
-  __shared__ int s_nsites, s_bin;
+  __shared__ int s_nsites, s_bin, s_near;
   __shared__ float s_amin, s_amax;
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ float s_thr;
@@ -281,7 +208,6 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   const double T = (cnt == P.K1) ? P.lst_E[base + P.lst_ord[base + P.K1 - 1]] : INFINITY;
   const double Ep = P.par_E[b];
   const long long C = (long long)n * (n + 1) / 2;
-  const int k = P.K1 + cnt;
   const float2* as = P.as32 + (long long)b * P.NP;
   const double* a64 = P.a64 + (long long)b * P.NP;
   for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
@@ -290,6 +216,7 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     s_amin = INFINITY;
     s_amax = -INFINITY;
     s_nsites = 0;
+    s_near = 0;
   }
   __syncthreads();
   // range of a_i (a ~ fl32 of the exact value in FP64 mode too: only used to bin sites)
@@ -321,6 +248,17 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     }
     __syncthreads();
   }
+  // kept states one or two flips away from the parent: the only candidates that can be
+  // duplicates (each equals exactly one candidate), so among the K+1+near lowest candidates
+  // at least K+1 are new states
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    const uint64_t* x = P.lst_bits + (base + P.lst_ord[base + r]) * P.Wmax;
+    int dist = 0;
+    for (int w = 0; w < d.W && dist <= 2; ++w) dist += __popcll(x[w] ^ pb[w]);
+    if (dist == 1 || dist == 2) atomicAdd(&s_near, 1);
+  }
+  __syncthreads();
+  const int k = P.K1 + s_near;
   const float amin = s_amin, amax = s_amax;
   double U = INFINITY;
   if (C > k && k <= kSubMax) {
@@ -417,12 +355,6 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     }
   }
   __syncthreads();
-  if (!fp64) {
-    // per-row bound of the pair scan: c_i = fl32(thr - a_i), with the row spin
-    float2* cs = P.cs32 + (long long)b * P.NP;
-    for (int i = threadIdx.x; i < d.n_pad; i += blockDim.x)
-      cs[i] = (i < n) ? make_float2(s_thr - as[i].x, as[i].y) : make_float2(0.f, 1.f);
-  }
   // single flips: dE_i = a_i
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     bool ok;

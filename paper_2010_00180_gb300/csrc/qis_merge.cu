@@ -214,7 +214,34 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     }
   }
   __syncthreads();
-  const int nv = s_nv;
+  int nv = s_nv;
+  // ---- 1b. more than one block of candidates: only the K+1 lowest of them can enter the list
+  //          (each later one has K+1 new states below it), so keep the keys up to the (K+1)-th
+  //          smallest (ties included) before sorting; compaction in place, chunk by chunk
+  if (nv > (int)blockDim.x && nv > K1) {
+    __shared__ int hist[256];
+    const unsigned long long x = radix_select<unsigned long long>(sk, nv, K1 - 1, hist);
+    int kept = 0;
+    for (int t0 = 0; t0 < nv; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      unsigned long long kk = 0, ee = 0;
+      bool keep = false;
+      if (t < nv) {
+        kk = sk[t];
+        ee = se[t];
+        keep = kk <= x;
+      }
+      int total;
+      const int pos = kept + block_exclusive_sum(keep ? 1 : 0, wsum, &total);   // syncs: reads done
+      if (keep) {
+        sk[pos] = kk;   // pos <= t: never a slot still to be read
+        se[pos] = ee;
+      }
+      kept += total;
+      __syncthreads();
+    }
+    nv = kept;
+  }
   // ---- 2. order the kept candidates by (E, c)
   if (nv > 1) {
     const int n2 = max(32, next_pow2(nv));

@@ -3,26 +3,30 @@
 // Pair candidates (i, j), i < j, of one parent: dE_ij = a_i + a_j + 4 s_i s_j J_ij (Sec. III,
 // energy change from the couplings of the flipped sites). A pair survives the filter when
 //     y_ij = a_j + (s_i s_j) 4J~_ij  <=  c_i = thr - a_i
-// where k_bound derives thr with its error band and writes c_i per site.
+// where k_bound derives thr with its error band (c_i is formed here, in FP32).
 //
 // Work unit = one block task: 32 consecutive rows i (4 warps x 8 rows) and a chunk of 32*NC
-// columns j of one instance, for all R searches of that instance. Each lane keeps its 8 x NC
-// couplings 4J~_ij in registers and reuses them for every search; lane l owns columns
-// c0 + 32k + l, so every coupling load is a coalesced 128-byte row segment. Per search the
-// block stages {a_j, s_j} of the chunk's columns, {c_i, s_i} of its rows and {thr, active} with
-// cp.async, two searches ahead (triple buffer, one block barrier per search).
+// columns j of one instance, for a group of searches of that instance. Each lane keeps its
+// 8 x NC couplings 4J~_ij in registers and reuses them for every search; lane l owns columns
+// c0 + 32k + l, so every coupling load is a coalesced 128-byte row segment.
+//
+// Per search the block needs {a_j, s_j} of the chunk's columns and of its rows and a control
+// word; one thread stages them with three TMA bulk copies into a ring of kRing slots
+// (completion counted on the slot's mbarrier). The warps do not synchronise with each other:
+// each waits for the slot of its next search, reads it, and releases it; the fourth release
+// refills the slot with the search kRing ahead. A warp that meets many hits may fall behind
+// the others by up to kRing searches without stalling them.
 //
 // Per search and row (warp-uniform) each lane computes y_ij = fma(+-4J~_ij, s_j, a_j) -- the
 // row spin, taken from a ballot so the branch is provably uniform, picks the operand sign --
 // reduces min_j y_ij with three-input minima and compares it with c_i. Pairs that must not be
 // evaluated (j <= i, j >= n) hold NaN couplings: the FMA propagates NaN and min ignores it.
-// A warp with a hit recomputes, on that rare path, each lane's exact (row, column) hits with
-// the same FP32 expression and appends one survivor entry per passing pair.
+// Rows whose c_i lies below a lower bound of every y_ij of the search are skipped whole. When a
+// row's minimum passes, the lane marks which of its columns pass from the same values, and
+// appends one survivor entry per passing pair.
 #include "qis_common.cuh"
 
 namespace qis {
-
-constexpr int kBufs = 3;   // staging depth: search s is computed while s+1, s+2 land
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
   float r;
@@ -43,34 +47,80 @@ __device__ __forceinline__ float rowmin(const float (&y)[NC]) {
   else return min3f(min3f(y[0], y[1], y[2]), min3f(y[3], y[4], y[5]), fminf(y[6], y[7]));
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-  const int sz = valid ? 16 : 0;   // 0 bytes read -> 16 zero bytes written
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared (TMA); completion is counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
 
-struct ScanSmem {
-  float2 col[kBufs][256];   // {a_j, s_j}
-  float2 row[kBufs][32];    // {c_i, s_i}
-  float4 ctl[kBufs];        // {thr, active, RD(min_j a_j - j4max), -}
+constexpr int kRing = 8;                      // staging ring depth (power of two)
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
+
+// Staging ring of one block: search s lives in slot s % kRing. full[q] completes a phase when
+// the slot's three bulk copies have landed; rel[q] counts the warps' releases.
+struct __align__(128) ScanRing {
+  float2 col[kRing][256];   // {a_j, s_j} of the chunk's columns
+  float2 row[kRing][32];    // {a_i, s_i} of the block's rows
+  float4 ctl[kRing];        // {thr, active, RD(min_j a_j - j4max), -}
+  uint64_t full[kRing];
+  int rel[kRing];
+  int issued[kRing];
+  int err;
 };
 
 template <int NC>
 __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, int row0, int c0, int g, int RG,
-                                          ScanSmem& sm) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+                                          ScanRing& sm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = d.n, np = d.n_pad, NPs = P.NP, cap = P.cap;
-  const int b0 = d.first_search + g * RG;        // searches [g RG, g RG + R) of the instance
+  const int b0 = d.first_search + g * RG;   // searches [g RG, g RG + R) of the instance
   const int R = min(RG, P.R - g * RG);
   const float* J4 = P.J4 + d.off_mat;
-  const float2* as_base = P.as32;
-  const float2* cs_base = P.cs32;
-  const float4* ctl_base = P.sctl;
   const float qnan = __int_as_float(0x7fc00000);
   const int i0 = row0 + warp * 8;
+  // bytes of one slot: the chunk's columns (clipped to the row stride; columns past n hold NaN
+  // couplings, so whatever the slot holds there never matters), 32 rows, the control word.
+  // All sources are 16-byte aligned: NP is a multiple of 128, c0 and row0 of 32.
+  const int cols = min(32 * NC, NPs - c0);
+  const uint32_t slot_bytes = (uint32_t)(cols * 8 + 32 * 8 + 16);
+  auto stage = [&](int s, int q) {   // one thread
+    const long long b = b0 + s;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // order the warps' reads first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.full[q])),
+                 "r"(slot_bytes) : "memory");
+    bulk_g2s(&sm.col[q][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
+    bulk_g2s(&sm.row[q][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
+    bulk_g2s(&sm.ctl[q], P.sctl + b, 16, &sm.full[q]);
+    sm.issued[q] += 1;
+  };
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kRing; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[q])));
+      sm.rel[q] = 0;
+      sm.issued[q] = 0;
+    }
+    sm.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int s = 0; s < min(kRing, R); ++s) stage(s, s);
+  }
+  __syncthreads();
+  // this lane's couplings 4J~_ij, rows i0..i0+7, columns c0 + 32k + lane (NaN where j <= i or
+  // j >= n), reused for every search of the group
   float J[8][NC];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
@@ -81,43 +131,49 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       J[r][k] = (i < n && j < n && j > i) ? J4[(long long)i * np + j] : qnan;
     }
   }
-  // stage search s into buffer q: columns (16 bytes = 2 sites per thread), rows (16 threads),
-  // {thr, active} (one thread)
-  const int col = c0 + 2 * t;
-  auto stage = [&](int s, int q) {
-    const long long b = b0 + s;
-    if (t < 16 * NC) cp_async16(&sm.col[q][2 * t], as_base + b * NPs + min(col, NPs - 2), col < NPs);
-    if (t < 16) cp_async16(&sm.row[q][2 * t], cs_base + b * NPs + row0 + 2 * t, true);
-    if (t == 16) cp_async16(&sm.ctl[q], ctl_base + b, true);
-    cp_async_commit();
-  };
-  stage(0, 0);
-  if (R > 1) stage(1, 1);
-  int q = 0;
+  const uint64_t t0 = gtimer();
+  int nlive = 0;   // rows this warp evaluated (statistics)
   for (int s = 0; s < R; ++s) {
-    // own copies of search s complete (s+1 may still be in flight); the barrier makes every
-    // thread's copies visible and guarantees that all warps have left iteration s-1, whose
-    // buffer (s+2) % 3 is restaged right after
-    if (s + 1 < R) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncthreads();
-    if (s + 2 < R) stage(s + 2, q == 0 ? 2 : q - 1);
+    const int q = s & (kRing - 1);
+    const uint32_t par = (uint32_t)(s / kRing) & 1u;
+    // bounded wait for the slot; an error anywhere in the block ends every warp's loop
+    bool ready = mbar_try(&sm.full[q], par);
+    while (!ready) {
+      if (*(volatile int*)&sm.err || gtimer() - t0 > kWaitNs) break;
+      ready = mbar_try(&sm.full[q], par);
+    }
+    if (!__all_sync(0xffffffffu, ready)) {
+      if (lane == 0) {
+        atomicOr(&sm.err, 1);
+        atomicOr(P.status, kStatTimeout);
+      }
+      break;
+    }
     const float4 ctl = sm.ctl[q];
     // rows that can hit: y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding is
-    // monotone), so a row with c_i < ctl.z has no pair below its bound; skipped rows cost a vote
-    const float2 rv = sm.row[q][warp * 8 + (lane & 7)];
+    // monotone), so a row with c_i below it has no pair under its bound
+    float2 rv = sm.row[q][warp * 8 + (lane & 7)];
+    rv.x = __fsub_rn(ctl.x, rv.x);   // c_i = fl32(thr - a_i)
     const unsigned live = __ballot_sync(0xffffffffu, ctl.y != 0.f && rv.x >= ctl.z) & 0xffu;
-    if (live) {   // vote result: uniform branch
-      const float2* cb = sm.col[q];
-      const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
-      float aj[NC], sj[NC];
+    float aj[NC], sj[NC];
+    if (live) {
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        const float2 v = cb[32 * k + lane];
+        const float2 v = sm.col[q][32 * k + lane];
         aj[k] = v.x;
         sj[k] = v.y;
       }
-      unsigned hm = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {   // release the slot; the last of the four warps refills it
+      __threadfence_block();   // this warp's reads of the slot precede the release
+      const int old = atomicAdd(&sm.rel[q], 1);
+      if ((old & 3) == 3 && s + kRing < R) stage(s + kRing, q);
+    }
+    nlive += __popc(live);
+    if (live) {   // vote result: uniform branch
+      const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
+      unsigned long long cm = 0;   // exact hits of this lane: bit r NC + k = (row i0 + r, column k)
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         if (!((live >> r) & 1u)) continue;   // uniform
@@ -130,53 +186,43 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
 #pragma unroll
           for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
         }
-        if (rowmin<NC>(y) <= c) hm |= 1u << r;
+        if (rowmin<NC>(y) <= c) {   // this lane has a hit in row r: which columns
+#pragma unroll
+          for (int k = 0; k < NC; ++k)
+            if (y[k] <= c) cm |= 1ull << (r * NC + k);
+        }
       }
-      const unsigned hit = __ballot_sync(0xffffffffu, hm != 0);
-      if (hit) {
-        // rare path: the exact (row, column) hits of this lane, recomputed with the same FP32
-        // expression from the couplings still in registers, one survivor entry per pair
-        unsigned long long cm = 0;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float c = __shfl_sync(0xffffffffu, rv.x, r);
-          if ((hm >> r) & 1u) {
-            const bool neg = (smask >> r) & 1u;
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-              const float y = neg ? fmaf(-J[r][k], sj[k], aj[k]) : fmaf(J[r][k], sj[k], aj[k]);
-              if (y <= c) cm |= 1ull << (r * NC + k);
-            }
-          }
-        }
-        const int mine = __popcll(cm);
-        int incl = mine;   // inclusive warp prefix of the per-lane hit counts
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        int base = 0;
-        if (lane == 31) base = atomicAdd(P.surv_cnt + b0 + s, incl);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int slot = base + incl - mine;
-        while (cm) {
+      if (cm) {   // one survivor entry per passing pair
+        int slot = atomicAdd(P.surv_cnt + b0 + s, __popcll(cm));
+        do {
           const int bit = __ffsll((long long)cm) - 1;
           cm &= cm - 1;
           const int i = i0 + bit / NC, j = c0 + 32 * (bit % NC) + lane;
           if (slot < cap) P.surv[(long long)(b0 + s) * cap + slot] = surv_entry(pair_index(n, i, j), i, j);
           ++slot;
-        }
+        } while (cm);
       }
     }
-    q = (q == kBufs - 1) ? 0 : q + 1;
+  }
+  if (lane == 0 && nlive) atomicAdd(P.eval_cnt + (blockIdx.x & 63), (unsigned long long)nlive * (32 * NC));
+  // after an error, wait (bounded) for every copy the block issued before its shared memory
+  // is released; without one, every issued copy has been waited for in the loop
+  __syncthreads();
+  if (threadIdx.x == 0 && sm.err) {
+    for (int q = 0; q < kRing; ++q) {
+      if (sm.issued[q] == 0) continue;
+      const uint32_t par = (uint32_t)(sm.issued[q] - 1) & 1u;
+      const uint64_t t1 = gtimer();
+      while (!mbar_try(&sm.full[q], par) && gtimer() - t1 < kWaitNs) {
+      }
+    }
   }
 }
 
 // task.x = instance, task.y = first row of the 32-row block, task.z = first column,
 // task.w = NC | (search group << 8); a group is RG consecutive searches of the instance
-__global__ void __launch_bounds__(128, 4) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
-  __shared__ __align__(16) ScanSmem sm;
+__global__ void __launch_bounds__(128, 5) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
+  __shared__ ScanRing sm;
   const int4 w = tasks[blockIdx.x];
   const InstDesc d = P.inst[w.x];
   const int g = w.w >> 8;

@@ -22,7 +22,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "C
 SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_clear_instances",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
-           "qis_get_tuning", "qis_set_tuning", "qis_autotune",
+           "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
            "qis_select_candidates_noalloc",
@@ -81,6 +81,7 @@ def load():
         "qis_save": (I, [P, C.c_char_p]),
         "qis_instance_n": (I, [P, I, C.POINTER(I)]),
         "qis_get_tuning": (I, [P, C.POINTER(Tuning)]),
+        "qis_evaluated_pairs": (I, [P, C.POINTER(U64)]),
         "qis_set_tuning": (I, [P, C.POINTER(Tuning)]),
         "qis_autotune": (I, [P, I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
         "qis_load": (I, [P, C.c_char_p]),
@@ -232,6 +233,12 @@ class Context:
         self._check(self.lib.qis_set_search_list(self.h, iid, r, cnt, _ptr(bits), _ptr(E),
                                                  _ptr(u) if u is not None else None,
                                                  _ptr(st) if st is not None else None, int(t)))
+
+    def evaluated_pairs(self) -> int:
+        """Pair terms the scan evaluated one by one (the rest were decided by the row bound)."""
+        v = C.c_uint64()
+        self._check(self.lib.qis_evaluated_pairs(self.h, C.byref(v)))
+        return v.value
 
     def tuning(self) -> dict:
         t = Tuning()
