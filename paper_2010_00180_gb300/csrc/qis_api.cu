@@ -322,6 +322,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     P.zob = ctx->zob;
     ALLOC(P.lst_bits, B * K1 * W);
     ALLOC(P.lst_E, B * K1);
+    ALLOC(P.lst_q, B * K1);
     ALLOC(P.lst_stamp, B * K1);
     ALLOC(P.lst_hash, B * K1);
     ALLOC(P.lst_used, B * K1);
@@ -329,6 +330,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.lst_count, B);
     ALLOC(P.par_bits, B * W);
     ALLOC(P.par_E, B);
+    ALLOC(P.par_q, B);
     ALLOC(P.par_hash, B);
     ALLOC(P.active, B);
     ALLOC(P.iter_t, B);
@@ -672,18 +674,20 @@ namespace {
 
 // Write one search's kept list (entries in key order) into the device list of search b. The
 // caller has validated the arguments; hashes are computed on the device from the bits.
-int import_search(qis_ctx* ctx, int b, int W, int count, const uint64_t* bits, const double* E,
+int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* bits, const double* E,
                   const uint8_t* used, const uint64_t* stamp, int t) {
   const int K1 = ctx->K1, Wm = ctx->Wmax;
   const size_t base = (size_t)b * K1;
   std::vector<uint64_t> lb((size_t)K1 * Wm, 0ull), st(K1, 0ull);
   std::vector<double> e(K1, INFINITY);
+  std::vector<long long> eq(K1, 0);
   std::vector<uint8_t> u(K1, 0);
   std::vector<int> ord(K1, -1);
   int act = 0;
   for (int k = 0; k < count; ++k) {
     memcpy(&lb[(size_t)k * Wm], bits + (size_t)k * W, W * sizeof(uint64_t));
     e[k] = E[k];
+    eq[k] = (ctx->mode != QIS_FP64) ? llrint(ldexp(E[k], q)) : 0;   // exact on the grid
     u[k] = used ? (used[k] != 0) : 0;
     st[k] = stamp ? stamp[k] : (uint64_t)k;
     ord[k] = k;
@@ -694,6 +698,7 @@ int import_search(qis_ctx* ctx, int b, int W, int count, const uint64_t* bits, c
   const DevPtrs& P = ctx->P;
   CK(cudaMemcpyAsync(P.lst_bits + base * Wm, lb.data(), lb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_E + base, e.data(), K1 * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_q + base, eq.data(), K1 * sizeof(long long), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_stamp + base, st.data(), K1 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_used + base, u.data(), K1, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_ord + base, ord.data(), K1 * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -740,7 +745,7 @@ int qis_set_search_list(qis_ctx* ctx, int instance_id, int r, int count, const u
   CK(cudaSetDevice(ctx->cfg.device));
   rc = sync_and_check(ctx);
   if (rc) return rc;
-  rc = import_search(ctx, d.first_search + r, d.W, count, bits, E, used, stamp, t);
+  rc = import_search(ctx, d.first_search + r, d.W, d.q, count, bits, E, used, stamp, t);
   if (rc) return rc;
   ctx->merged_fresh = false;
   return 0;
@@ -937,7 +942,7 @@ int qis_load(qis_ctx* ctx, const char* path) {
       if (!ih[1]) continue;   // lists of an instance without initial states are not restored
       rc = check_list(ctx, n, cnt, bits.data(), E.data());
       if (rc) return rc;
-      rc = import_search(ctx, d.first_search + r, W, cnt, bits.data(), E.data(), used.data(), stamp.data(), sh[1]);
+      rc = import_search(ctx, d.first_search + r, W, d.q, cnt, bits.data(), E.data(), used.data(), stamp.data(), sh[1]);
       if (rc) return rc;
       const int act = sh[2];
       CK(cudaMemcpy(ctx->P.active + d.first_search + r, &act, sizeof(int), cudaMemcpyHostToDevice));

@@ -52,6 +52,7 @@ struct DevPtrs {
   // per-search state, search b
   uint64_t* lst_bits;     // [b][K1][Wmax]
   double* lst_E;          // [b][K1]
+  long long* lst_q;       // [b][K1] exact E * 2^q of each slot (split modes)
   uint64_t* lst_stamp;    // [b][K1]
   uint64_t* lst_hash;     // [b][K1]
   uint8_t* lst_used;      // [b][K1]
@@ -59,6 +60,7 @@ struct DevPtrs {
   int* lst_count;         // [b]
   uint64_t* par_bits;     // [b][Wmax]
   double* par_E;          // [b]
+  long long* par_q;       // [b] exact E_p * 2^q (split modes)
   uint64_t* par_hash;     // [b]
   int* active;            // [b]
   int* iter_t;            // [b] iterations done

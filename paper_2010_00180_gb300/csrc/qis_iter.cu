@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
     } else {
       P.lst_used[base + sel] = 1;
       P.par_E[b] = P.lst_E[base + sel];
+      if (P.mode != QIS_FP64) P.par_q[b] = P.lst_q[base + sel];
       P.par_hash[b] = P.lst_hash[base + sel];
       P.nprod[b] += 1;   // n(n-1)/2 pair and n single candidates, counted on query
     }
@@ -170,13 +171,66 @@ cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- helpers
-__device__ inline unsigned fkey(float x) {
-  x = x + 0.f;
-  const unsigned u = __float_as_uint(x);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+// Block-wide minimum and maximum of one value per thread (every thread gets both).
+__device__ void block_min_max(float& lo, float& hi) {
+  __shared__ float s_lo[32], s_hi[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[w] = lo;
+    s_hi[w] = hi;
+  }
+  __syncthreads();
+  lo = s_lo[0];
+  hi = s_hi[0];
+  for (int k = 1; k < nw; ++k) {
+    lo = fminf(lo, s_lo[k]);
+    hi = fmaxf(hi, s_hi[k]);
+  }
+  __syncthreads();
 }
-__device__ inline float fkey_inv(unsigned k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+
+// An upper bound of the rank-th smallest (0-based) of cnt finite values in shared memory,
+// tight to one of 256 equal-width bins of their range: the largest value whose bin is at most
+// the bin holding that element (binning is monotone, so at least rank + 1 values lie in those
+// bins). Two passes over the values instead of the four of a radix select. Every thread of
+// the block calls it.
+__device__ float value_select_upper(const float* v, int cnt, int rank, int* hist) {
+  __shared__ int s_b;
+  float lo = INFINITY, hi = -INFINITY;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    lo = fminf(lo, v[t]);
+    hi = fmaxf(hi, v[t]);
+  }
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+  block_min_max(lo, hi);
+  const float scale = 255.99f / fmaxf(hi - lo, 1e-30f);
+  for (int t0 = 0; t0 < cnt; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
+    const bool in = t < cnt;
+    const unsigned act = __ballot_sync(0xffffffffu, in);
+    if (in) {
+      const int bin = min(255, (int)((v[t] - lo) * scale));
+      const unsigned peers = __match_any_sync(act, bin);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int b, within;
+    find_bin(hist, rank, b, within);
+    if (threadIdx.x == 0) s_b = b;
+  }
+  __syncthreads();
+  const int bsel = s_b;
+  float mx = -INFINITY, dummy = INFINITY;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x)
+    if (min(255, (int)((v[t] - lo) * scale)) <= bsel) mx = fmaxf(mx, v[t]);
+  block_min_max(dummy, mx);
+  return mx;
 }
 
 // ---------------------------------------------------------------- per-search bound
@@ -208,8 +262,13 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   const double T = (cnt == P.K1) ? P.lst_E[base + P.lst_ord[base + P.K1 - 1]] : INFINITY;
   const double Ep = P.par_E[b];
   const long long C = (long long)n * (n + 1) / 2;
-  const float2* as = P.as32 + (long long)b * P.NP;
   const double* a64 = P.a64 + (long long)b * P.NP;
+  // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory
+  float2* as = reinterpret_cast<float2*>(subkey + kSubMax);   // [NP]
+  if (!fp64) {
+    const float2* g = P.as32 + (long long)b * P.NP;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) as[i] = g[i];
+  }
   for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   if (threadIdx.x == 0) {
     P.surv_cnt[b] = 0;
@@ -254,7 +313,7 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const uint64_t* x = P.lst_bits + (base + P.lst_ord[base + r]) * P.Wmax;
     int dist = 0;
-    for (int w = 0; w < d.W && dist <= 2; ++w) dist += __popcll(x[w] ^ pb[w]);
+    for (int w = 0; w < d.W; ++w) dist += __popcll(x[w] ^ pb[w]);   // independent loads
     if (dist == 1 || dist == 2) atomicAdd(&s_near, 1);
   }
   __syncthreads();
@@ -294,6 +353,7 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     const int M = mm + mm * (mm - 1) / 2;
     if (M >= k) {
       // subset candidate energies, in the scan's arithmetic
+#pragma unroll 2
       for (int t = threadIdx.x; t < M; t += blockDim.x) {
         int i, j = -1;
         if (t < mm) {
@@ -324,12 +384,12 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
             const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
             de = as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x);
           }
-          reinterpret_cast<unsigned*>(subkey)[t] = fkey(de);
+          reinterpret_cast<float*>(subkey)[t] = de;
         }
       }
       __syncthreads();
       if (fp64) U = dkey_inv(radix_select<unsigned long long>(subkey, M, k - 1, hist));
-      else U = (double)fkey_inv(radix_select<unsigned>(reinterpret_cast<unsigned*>(subkey), M, k - 1, hist));
+      else U = (double)value_select_upper(reinterpret_cast<const float*>(subkey), M, k - 1, hist);
     }
   }
   if (threadIdx.x == 0) {
@@ -372,11 +432,12 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
 }
 
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = (size_t)kSubMax * 8;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
+  const size_t sm = (size_t)kSubMax * 8 + (size_t)P.NP * sizeof(float2);
+  static size_t attr = 0;
+  if (attr < sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = sm;
   }
   k_bound<<<P.B, 128, sm, s>>>(P);
   return cudaGetLastError();

@@ -4,12 +4,13 @@
 // and of the pairs that passed the scan's filter). Output: the new kept list.
 //
 //  1. Every candidate gets its exact energy: in the split modes from exact fixed-point
-//     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), in the FP64 mode with the
-//     defining FP64 arithmetic. Candidates with E' >= T (the last kept energy, Alg. 2: strict
+//     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), compared as integers with the
+//     integer energies of the kept states (no floating point on this path); in the FP64 mode
+//     with the defining FP64 arithmetic. Candidates with E' >= T (the last kept energy, Alg. 2: strict
 //     <) are dropped, as are duplicates of a kept state (Zobrist hash table + full compare:
 //     the binary search of Alg. 2).
-//  2. The kept candidates are sorted by (E, c) (bitonic network: in registers and shuffles for
-//     up to 256 candidates, in shared memory beyond).
+//  2. The kept candidates are sorted by (E, c): warp-sorted runs of 32 merged by rank (binary
+//     search in the other runs) for up to 256 candidates, a shared-memory bitonic network beyond.
 //  3. New list = first K+1 of (old list, new candidates) by (E, stamp): old entries precede
 //     new ones of equal energy (they arrived earlier), new ones are ordered by candidate
 //     index c (the order of the Alg. 3 loop). Slots of evicted entries are reused.
@@ -18,6 +19,9 @@
 namespace qis {
 
 __device__ inline uint32_t hmix(uint64_t h) { return (uint32_t)(h ^ (h >> 29) ^ (h >> 47)); }
+
+// order-preserving key of an exact integer energy E 2^q (signed -> unsigned)
+__device__ inline unsigned long long qkey(long long x) { return (unsigned long long)x ^ (1ull << 63); }
 
 // exclusive prefix sum of one int per thread over the block (blockDim multiple of 32)
 __device__ int block_exclusive_sum(int v, int* wsum /* [33] */, int* total) {
@@ -72,31 +76,61 @@ __device__ void bitonic_sort_smem(unsigned long long* key, unsigned long long* e
   }
 }
 
-// Ascending bitonic sort of n2 <= blockDim.x pairs (32 <= n2, power of two), one per thread in
-// registers: partners closer than 32 are exchanged with shuffles, farther ones through shared
-// memory. Every thread of the block calls it (barriers); warps at or beyond n2 only pass them.
-__device__ void bitonic_sort_regs(unsigned long long& key, unsigned long long& ent, int n2,
-                                  unsigned long long* xk, unsigned long long* xe) {
-  const int t = threadIdx.x;
-  const bool on = t < n2;   // warp-uniform: n2 is a multiple of 32
-  for (int k = 2; k <= n2; k <<= 1) {
+// Ascending bitonic sort of the 32 (key, entry) pairs of one warp, one per lane, in shuffles.
+__device__ __forceinline__ void warp_sort32(unsigned long long& key, unsigned long long& ent) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      unsigned long long ko, eo;
-      if (j >= 32) {
-        __syncthreads();
-        if (on) { xk[t] = key; xe[t] = ent; }
-        __syncthreads();
-        if (on) { ko = xk[t ^ j]; eo = xe[t ^ j]; }
-      } else if (on) {
-        ko = __shfl_xor_sync(0xffffffffu, key, j);
-        eo = __shfl_xor_sync(0xffffffffu, ent, j);
-      }
-      if (on) {
-        const bool want_min = ((t & j) == 0) == ((t & k) == 0);
-        const bool take = want_min ? kc_less(ko, eo, key, ent) : kc_less(key, ent, ko, eo);
-        if (take) { key = ko; ent = eo; }
+      const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key, j);
+      const unsigned long long eo = __shfl_xor_sync(0xffffffffu, ent, j);
+      const bool want_min = ((lane & j) == 0) == ((lane & k) == 0);
+      const bool take = want_min ? kc_less(ko, eo, key, ent) : kc_less(key, ent, ko, eo);
+      if (take) {
+        key = ko;
+        ent = eo;
       }
     }
+  }
+}
+
+// Sort of nv <= blockDim.x pairs: every warp sorts a run of 32 (padding ~0 sorts last), then
+// each element's place = its index in its run + the number of smaller elements in every other
+// run (binary search, 32 entries). Input in (key, ent)[0..nv), output in (okey, oent)[0..nv).
+// Every thread of the block calls it.
+__device__ void sort_runs(const unsigned long long* key, const unsigned long long* ent, int nv,
+                          unsigned long long* okey, unsigned long long* oent) {
+  const int t = threadIdx.x, w = t >> 5;
+  const int nr = (nv + 31) >> 5;
+  unsigned long long k = ~0ull, e = ~0ull;
+  if (t < nv) {
+    k = key[t];
+    e = ent[t];
+  }
+  if (w < nr) warp_sort32(k, e);   // warp-uniform
+  okey[t] = k;                     // runs staged in the output arrays (blockDim.x entries)
+  oent[t] = e;
+  __syncthreads();
+  int pos = t & 31;
+  const bool real = w < nr && k != ~0ull;   // a finite energy's key is never all ones
+  if (real) {
+    for (int v = 0; v < nr; ++v) {
+      if (v == w) continue;
+      const unsigned long long* rk = okey + 32 * v;
+      const unsigned long long* re = oent + 32 * v;
+      int lo = 0, hi = 32;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (kc_less(rk[mid], re[mid], k, e)) lo = mid + 1; else hi = mid;
+      }
+      pos += lo;
+    }
+  }
+  __syncthreads();   // every search done before the runs are overwritten
+  if (real) {
+    okey[pos] = k;
+    oent[pos] = e;
   }
   __syncthreads();
 }
@@ -129,17 +163,27 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   uint64_t* oH = reinterpret_cast<uint64_t*>(okey + K1);                    // [K1]
   unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);  // [PC] keys of valid candidates
   unsigned long long* se = sk + PC;                                         // [PC] their survivor entries
-  int* oslot = reinterpret_cast<int*>(se + PC);                             // [K1]
+  unsigned long long* sk2 = se + PC;                                        // [kMergeThreads] sorted keys
+  unsigned long long* se2 = sk2 + kMergeThreads;                            // [kMergeThreads] sorted entries
+  int* oslot = reinterpret_cast<int*>(se2 + kMergeThreads);                 // [K1]
   int* occ = oslot + K1;                                                    // [K1]
   int* freel = occ + K1;                                                    // [K1]
   int* htab = freel + K1;                                                   // [HT]
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ int s_nv, wsum[33], s_total;
   const int cnt = P.lst_count[b];
-  const double T = (cnt == K1) ? P.lst_E[base + P.lst_ord[base + K1 - 1]] : INFINITY;
-  const double Ep = P.par_E[b];
-  const uint64_t ph = P.par_hash[b];
   const bool fp64 = P.mode == QIS_FP64;
+  // threshold and parent energy: FP64 values in the plain form, exact integers E 2^q otherwise
+  double T = INFINITY, Ep = 0.0;
+  long long Tq = LLONG_MAX, Epq = 0;
+  if (fp64) {
+    if (cnt == K1) T = P.lst_E[base + P.lst_ord[base + K1 - 1]];
+    Ep = P.par_E[b];
+  } else {
+    if (cnt == K1) Tq = P.lst_q[base + P.lst_ord[base + K1 - 1]];
+    Epq = P.par_q[b];
+  }
+  const uint64_t ph = P.par_hash[b];
   for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = -1;
   for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
@@ -148,7 +192,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const int slot = P.lst_ord[base + r];
     oslot[r] = slot;
-    okey[r] = dkey(P.lst_E[base + slot]);
+    okey[r] = fp64 ? dkey(P.lst_E[base + slot]) : qkey(P.lst_q[base + slot]);
     const uint64_t h = P.lst_hash[base + slot];
     oH[r] = h;
     uint32_t pos = hmix(h) & (HT - 1);
@@ -158,8 +202,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   // ---- 1. exact energy of every survivor of the filter; keep E' < T (strict, Alg. 2) that
   //         is not a kept state (Zobrist hash table + full compare: the binary search of
   //         Alg. 2); compact the kept ones (warp-aggregated)
-  const long long Epq = fp64 ? 0 : __double2ll_rn(ldexp(Ep, d.q));
-  const long long Tq = (fp64 || T == INFINITY) ? LLONG_MAX : __double2ll_rn(ldexp(T, d.q));
   const unsigned long long* sv = P.surv + (long long)b * P.cap;
   for (int t0 = 0; t0 < S; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
@@ -171,12 +213,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
       int i, j;
       surv_decode(ent, c, i, j);
       const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
-      double e;
       if (fp64) {
         const double* a = P.a64 + (long long)b * P.NP;
         const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
-        e = __dadd_rn(Ep, de);
+        const double e = __dadd_rn(Ep, de);
         keep = e < T;
+        kk = dkey(e);
       } else {
         const long long* aq = P.aq + (long long)b * P.NP;
         long long de = aq[i];
@@ -186,7 +228,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
         }
         const long long eq = Epq + de;
         keep = eq < Tq;
-        e = ldexp((double)eq, -d.q);
+        kk = qkey(eq);
       }
       if (keep) {
         const uint64_t hsh = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
@@ -199,7 +241,6 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
           if (same) keep = false;   // duplicate of a kept state
         }
       }
-      kk = dkey(e);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (bal) {
@@ -244,19 +285,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   }
   // ---- 2. order the kept candidates by (E, c)
   if (nv > 1) {
-    const int n2 = max(32, next_pow2(nv));
-    if (n2 <= (int)blockDim.x) {
-      unsigned long long key = ~0ull, ent = ~0ull;   // padding sorts last
-      if ((int)threadIdx.x < nv) {
-        key = sk[threadIdx.x];
-        ent = se[threadIdx.x];
-      }
-      __syncthreads();
-      bitonic_sort_regs(key, ent, n2, sk, se);
-      if ((int)threadIdx.x < nv) {
-        sk[threadIdx.x] = key;
-        se[threadIdx.x] = ent;
-      }
+    if (nv <= (int)blockDim.x) {
+      sort_runs(sk, se, nv, sk2, se2);
+      sk = sk2;
+      se = se2;
     } else {
       const int m2 = next_pow2(nv);
       for (int t = nv + threadIdx.x; t < m2; t += blockDim.x) {
@@ -306,7 +338,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     surv_decode(se[p], c, i, j);
     uint64_t* dst = P.lst_bits + (base + slot) * P.Wmax;
     for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
-    P.lst_E[base + slot] = dkey_inv(kp);
+    if (fp64) {
+      P.lst_E[base + slot] = dkey_inv(kp);
+    } else {
+      const long long eq = (long long)(kp ^ (1ull << 63));
+      P.lst_q[base + slot] = eq;
+      P.lst_E[base + slot] = (double)eq * d.inv_scale;   // 2^-q: exact
+    }
     P.lst_stamp[base + slot] = ((uint64_t)t_now << 32) | c;
     P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
     P.lst_used[base + slot] = 0;
@@ -321,7 +359,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
 
 size_t merge_smem(int K1, int cap) {
   const int PC = next_pow2(cap > kMergeThreads ? cap : kMergeThreads), HT = next_pow2(2 * K1);
-  return (size_t)K1 * 16 + (size_t)PC * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
+  return (size_t)K1 * 16 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
