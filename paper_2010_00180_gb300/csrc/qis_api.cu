@@ -348,8 +348,12 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.thrE, B);
     ALLOC(P.capE, B);
     ALLOC(P.surv_cnt, B);
+    ALLOC(P.dup_c, (size_t)B * K1);
+    ALLOC(P.dup_n, B);
     ALLOC(P.surv, B * (size_t)ctx->cap);
     ALLOC(P.init_bits, B * W);
+    ALLOC(P.init_E, B);
+    ALLOC(P.init_q, B);
     ALLOC(P.status, 4);
     ALLOC(P.nprod, B);
     ALLOC(P.eval_cnt, 64);
@@ -569,7 +573,7 @@ int qis_reset(qis_ctx* ctx) {
   for (size_t i = 0; i < ctx->inst.size(); ++i)
     if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
   CK(cudaMemsetAsync(ctx->P.status, 0, sizeof(int), ctx->stream));
-  LAUNCH(launch_init_search(ctx->P, 0, ctx->P.B, ctx->stream));
+  LAUNCH(launch_init_search(ctx->P, 0, ctx->P.B, ctx->stream, true));   // energies of the stored states
   ctx->merged_fresh = false;
   return 0;
 }

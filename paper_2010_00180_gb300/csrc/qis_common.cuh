@@ -72,9 +72,13 @@ struct DevPtrs {
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
   int* surv_cnt;          // [b]
+  uint32_t* dup_c;        // [b][K1] candidate index of every kept state one or two flips from the parent
+  int* dup_n;             // [b] their number
   unsigned long long* surv;  // [b][cap] survivor entries {c, i, j} (surv_entry)
   __half* S16;            // [b][NP] +-1 spins of the parent (0 past n), tensor-core operand
   uint64_t* init_bits;    // [b][Wmax]
+  double* init_E;         // [b] energy of the initial state (set with it)
+  long long* init_q;      // [b] the same, exact E 2^q (split modes)
   int* status;            // [0] error bits
   int* nprod;             // [b] productive iterations (a parent was expanded) of search b
   unsigned long long* eval_cnt;  // [64] pair terms the FP32 scan evaluated (live rows x chunk width)
@@ -239,7 +243,7 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
 int gemm_tile_n(int R, int digits);
 cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
                             float* J4, long long* hq, cudaStream_t s);
-cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s);
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached = false);
 cudaError_t launch_hash_list(const DevPtrs& P, int b, int count, cudaStream_t s);
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);

@@ -107,7 +107,9 @@ cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __hal
 // Alg. 3 initial list: [psi0, K placeholders], E(psi0) from Eq. (1), nothing used.
 // Split modes: E0 = (sum_{i<j} Jq_ij s_i s_j + sum_i hq_i s_i) 2^-q in exact int64.
 // FP64 mode: one thread adds the pair terms i-major, j ascending, then the field terms.
-__global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0) {
+// cached: the initial state's energy was computed by an earlier launch for the same initial
+// states (qis_reset) and is taken from init_E / init_q instead of being summed again.
+__global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cached) {
   const int b = b0 + blockIdx.x;
   const InstDesc d = P.inst[b / P.R];
   const int n = d.n, np = d.n_pad, W = d.W;
@@ -116,7 +118,10 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0) {
   for (int w = threadIdx.x; w < W; w += blockDim.x) bits[w] = P.init_bits[(long long)b * P.Wmax + w];
   __syncthreads();
   double E0 = 0.0;
-  if (P.mode != QIS_FP64) {
+  if (cached) {
+    E0 = P.init_E[b];
+    if (threadIdx.x == 0) red[0] = P.init_q[b];
+  } else if (P.mode != QIS_FP64) {
     long long acc = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const long long* row = P.Jq + d.off_mat + (long long)i * np;
@@ -147,6 +152,8 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0) {
     E0 = __dadd_rn(Pp, F);
   }
   if (threadIdx.x == 0) {
+    P.init_E[b] = E0;
+    P.init_q[b] = (P.mode != QIS_FP64) ? red[0] : 0;
     uint64_t hsh = 0;
     for (int i = 0; i < n; ++i)
       if (sigma_of(bits, i)) hsh ^= P.zob[i];
@@ -167,9 +174,9 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0) {
   }
 }
 
-cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s) {
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached) {
   if (nb <= 0) return cudaSuccess;
-  k_init_search<<<nb, 256, 0, s>>>(P, b0);
+  k_init_search<<<nb, 256, 0, s>>>(P, b0, cached ? 1 : 0);
   return cudaGetLastError();
 }
 

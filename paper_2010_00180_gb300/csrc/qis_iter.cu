@@ -308,15 +308,32 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     __syncthreads();
   }
   // kept states one or two flips away from the parent: the only candidates that can be
-  // duplicates (each equals exactly one candidate), so among the K+1+near lowest candidates
-  // at least K+1 are new states
+  // duplicates, each equal to exactly one candidate (the single flip of its differing site, or
+  // the pair of its two). Their candidate indices go to dup_c for the merge's duplicate test;
+  // among the K+1+near lowest candidates at least K+1 are new states.
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const uint64_t* x = P.lst_bits + (base + P.lst_ord[base + r]) * P.Wmax;
-    int dist = 0;
-    for (int w = 0; w < d.W; ++w) dist += __popcll(x[w] ^ pb[w]);   // independent loads
-    if (dist == 1 || dist == 2) atomicAdd(&s_near, 1);
+    // one pass: the distance and the first two differing sites (ascending)
+    int dist = 0, p0 = 0, p1 = 0;
+    for (int w = 0; w < d.W; ++w) {
+      uint64_t v = x[w] ^ pb[w];
+      if (v && dist < 2) {
+        const int lo = w * 64 + __ffsll((long long)v) - 1;
+        if (dist == 0) {
+          p0 = lo;
+          v &= v - 1;
+          if (v) p1 = w * 64 + __ffsll((long long)v) - 1;
+        } else {
+          p1 = lo;
+        }
+      }
+      dist += __popcll(x[w] ^ pb[w]);
+    }
+    if (dist == 1 || dist == 2)
+      P.dup_c[base + atomicAdd(&s_near, 1)] = (dist == 1) ? (uint32_t)p0 : pair_index(n, p0, p1);
   }
   __syncthreads();
+  if (threadIdx.x == 0) P.dup_n[b] = s_near;
   const int k = P.K1 + s_near;
   const float amin = s_amin, amax = s_amax;
   double U = INFINITY;

@@ -7,8 +7,9 @@
 //     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), compared as integers with the
 //     integer energies of the kept states (no floating point on this path); in the FP64 mode
 //     with the defining FP64 arithmetic. Candidates with E' >= T (the last kept energy, Alg. 2: strict
-//     <) are dropped, as are duplicates of a kept state (Zobrist hash table + full compare:
-//     the binary search of Alg. 2).
+//     <) are dropped, as are duplicates of a kept state (the binary search of Alg. 2): a kept
+//     state equals a candidate only if it is one or two flips from the parent, and then it
+//     is exactly the candidate of those flips, so duplicates are found by candidate index.
 //  2. The kept candidates are sorted by (E, c): warp-sorted runs of 32 merged by rank (binary
 //     search in the other runs) for up to 256 candidates, a shared-memory bitonic network beyond.
 //  3. New list = first K+1 of (old list, new candidates) by (E, stamp): old entries precede
@@ -18,7 +19,8 @@
 
 namespace qis {
 
-__device__ inline uint32_t hmix(uint64_t h) { return (uint32_t)(h ^ (h >> 29) ^ (h >> 47)); }
+constexpr uint32_t kNoCand = 0xffffffffu;   // empty slot of the duplicate table
+__device__ inline uint32_t chash(uint32_t c) { return (c * 2654435761u) >> 7; }
 
 // order-preserving key of an exact integer energy E 2^q (signed -> unsigned)
 __device__ inline unsigned long long qkey(long long x) { return (unsigned long long)x ^ (1ull << 63); }
@@ -160,15 +162,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   const int HT = next_pow2(2 * K1);
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* okey = reinterpret_cast<unsigned long long*>(smem);   // [K1]
-  uint64_t* oH = reinterpret_cast<uint64_t*>(okey + K1);                    // [K1]
-  unsigned long long* sk = reinterpret_cast<unsigned long long*>(oH + K1);  // [PC] keys of valid candidates
+  unsigned long long* sk = okey + K1;                                       // [PC] keys of valid candidates
   unsigned long long* se = sk + PC;                                         // [PC] their survivor entries
   unsigned long long* sk2 = se + PC;                                        // [kMergeThreads] sorted keys
   unsigned long long* se2 = sk2 + kMergeThreads;                            // [kMergeThreads] sorted entries
   int* oslot = reinterpret_cast<int*>(se2 + kMergeThreads);                 // [K1]
   int* occ = oslot + K1;                                                    // [K1]
   int* freel = occ + K1;                                                    // [K1]
-  int* htab = freel + K1;                                                   // [HT]
+  uint32_t* htab = reinterpret_cast<uint32_t*>(freel + K1);                // [HT] duplicate candidates
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ int s_nv, wsum[33], s_total;
   const int cnt = P.lst_count[b];
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   }
   const uint64_t ph = P.par_hash[b];
   for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
-  for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = -1;
+  for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = kNoCand;
   for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
   if (threadIdx.x == 0) s_nv = 0;
   __syncthreads();
@@ -193,15 +194,19 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     const int slot = P.lst_ord[base + r];
     oslot[r] = slot;
     okey[r] = fp64 ? dkey(P.lst_E[base + slot]) : qkey(P.lst_q[base + slot]);
-    const uint64_t h = P.lst_hash[base + slot];
-    oH[r] = h;
-    uint32_t pos = hmix(h) & (HT - 1);
-    while (atomicCAS(&htab[pos], -1, r) != -1) pos = (pos + 1) & (HT - 1);
+  }
+  // candidate indices of the kept states one or two flips from the parent (from k_bound): the
+  // only candidates that can equal a kept state
+  const int ndup = P.dup_n[b];
+  for (int r = threadIdx.x; r < ndup; r += blockDim.x) {
+    const uint32_t c = P.dup_c[base + r];
+    uint32_t pos = chash(c) & (HT - 1);
+    while (atomicCAS(&htab[pos], kNoCand, c) != kNoCand) pos = (pos + 1) & (HT - 1);
   }
   __syncthreads();
   // ---- 1. exact energy of every survivor of the filter; keep E' < T (strict, Alg. 2) that
-  //         is not a kept state (Zobrist hash table + full compare: the binary search of
-  //         Alg. 2); compact the kept ones (warp-aggregated)
+  //         is not a kept state (the binary search of Alg. 2: membership of its candidate
+  //         index among those of the near kept states); compact the kept ones (warp-aggregated)
   const unsigned long long* sv = P.surv + (long long)b * P.cap;
   for (int t0 = 0; t0 < S; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
@@ -231,15 +236,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
         kk = qkey(eq);
       }
       if (keep) {
-        const uint64_t hsh = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
-        uint32_t pos = hmix(hsh) & (HT - 1);
-        for (int r = htab[pos]; r >= 0 && keep; pos = (pos + 1) & (HT - 1), r = htab[pos]) {
-          if (oH[r] != hsh) continue;
-          const uint64_t* sbits = P.lst_bits + (base + oslot[r]) * P.Wmax;
-          bool same = true;
-          for (int x = 0; x < W && same; ++x) same = sbits[x] == (pb[x] ^ flip_mask(x, i, j));
-          if (same) keep = false;   // duplicate of a kept state
-        }
+        for (uint32_t pos = chash(c) & (HT - 1); htab[pos] != kNoCand; pos = (pos + 1) & (HT - 1))
+          if (htab[pos] == c) {
+            keep = false;   // duplicate of a kept state
+            break;
+          }
       }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
 
 size_t merge_smem(int K1, int cap) {
   const int PC = next_pow2(cap > kMergeThreads ? cap : kMergeThreads), HT = next_pow2(2 * K1);
-  return (size_t)K1 * 16 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
+  return (size_t)K1 * 8 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {

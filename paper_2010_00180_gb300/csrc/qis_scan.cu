@@ -69,14 +69,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 constexpr int kRing = 8;                      // staging ring depth (power of two)
+constexpr int kPer = 2;                       // searches per ring slot
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
 
-// Staging ring of one block: search s lives in slot s % kRing. full[q] completes a phase when
-// the slot's three bulk copies have landed; rel[q] counts the warps' releases.
+// Staging ring of one block: slot u % kRing holds searches kPer u .. kPer u + kPer - 1. full[q]
+// completes a phase when the slot's bulk copies have landed; rel[q] counts the warps' releases.
 struct __align__(128) ScanRing {
-  float2 col[kRing][256];   // {a_j, s_j} of the chunk's columns
-  float2 row[kRing][32];    // {a_i, s_i} of the block's rows
-  float4 ctl[kRing];        // {thr, active, RD(min_j a_j - j4max), -}
+  float2 col[kRing][kPer][256];   // {a_j, s_j} of the chunk's columns
+  float2 row[kRing][kPer][32];    // {a_i, s_i} of the block's rows
+  float4 ctl[kRing][kPer];        // {thr, active, RD(min_j a_j - j4max), -}
   uint64_t full[kRing];
   int rel[kRing];
   int issued[kRing];
@@ -97,15 +98,18 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
   // couplings, so whatever the slot holds there never matters), 32 rows, the control word.
   // All sources are 16-byte aligned: NP is a multiple of 128, c0 and row0 of 32.
   const int cols = min(32 * NC, NPs - c0);
-  const uint32_t slot_bytes = (uint32_t)(cols * 8 + 32 * 8 + 16);
-  auto stage = [&](int s, int q) {   // one thread
-    const long long b = b0 + s;
+  const int nslots = (R + kPer - 1) / kPer;
+  auto stage = [&](int u, int q) {   // one thread: the searches of slot iteration u
+    const int ns = min(kPer, R - u * kPer);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // order the warps' reads first
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.full[q])),
-                 "r"(slot_bytes) : "memory");
-    bulk_g2s(&sm.col[q][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
-    bulk_g2s(&sm.row[q][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
-    bulk_g2s(&sm.ctl[q], P.sctl + b, 16, &sm.full[q]);
+                 "r"((uint32_t)(ns * (cols * 8 + 32 * 8 + 16))) : "memory");
+    for (int p = 0; p < ns; ++p) {
+      const long long b = b0 + u * kPer + p;
+      bulk_g2s(&sm.col[q][p][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
+      bulk_g2s(&sm.row[q][p][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
+      bulk_g2s(&sm.ctl[q][p], P.sctl + b, 16, &sm.full[q]);
+    }
     sm.issued[q] += 1;
   };
   if (threadIdx.x == 0) {
@@ -116,7 +120,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
     }
     sm.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int s = 0; s < min(kRing, R); ++s) stage(s, s);
+    for (int u = 0; u < min(kRing, nslots); ++u) stage(u, u);
   }
   __syncthreads();
   // this lane's couplings 4J~_ij, rows i0..i0+7, columns c0 + 32k + lane (NaN where j <= i or
@@ -133,9 +137,9 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
   }
   const uint64_t t0 = gtimer();
   int nlive = 0;   // rows this warp evaluated (statistics)
-  for (int s = 0; s < R; ++s) {
-    const int q = s & (kRing - 1);
-    const uint32_t par = (uint32_t)(s / kRing) & 1u;
+  for (int u = 0; u < nslots; ++u) {
+    const int q = u & (kRing - 1);
+    const uint32_t par = (uint32_t)(u / kRing) & 1u;
     // bounded wait for the slot; an error anywhere in the block ends every warp's loop
     bool ready = mbar_try(&sm.full[q], par);
     while (!ready) {
@@ -149,59 +153,63 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       }
       break;
     }
-    const float4 ctl = sm.ctl[q];
-    // rows that can hit: y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding is
-    // monotone), so a row with c_i below it has no pair under its bound
-    float2 rv = sm.row[q][warp * 8 + (lane & 7)];
-    rv.x = __fsub_rn(ctl.x, rv.x);   // c_i = fl32(thr - a_i)
-    const unsigned live = __ballot_sync(0xffffffffu, ctl.y != 0.f && rv.x >= ctl.z) & 0xffu;
-    float aj[NC], sj[NC];
-    if (live) {
+    const int ns = min(kPer, R - u * kPer);
+    for (int p = 0; p < ns; ++p) {
+      const int s = u * kPer + p;
+      const float4 ctl = sm.ctl[q][p];
+      // rows that can hit: y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding is
+      // monotone), so a row with c_i below it has no pair under its bound
+      float2 rv = sm.row[q][p][warp * 8 + (lane & 7)];
+      rv.x = __fsub_rn(ctl.x, rv.x);   // c_i = fl32(thr - a_i)
+      const unsigned live = __ballot_sync(0xffffffffu, ctl.y != 0.f && rv.x >= ctl.z) & 0xffu;
+      float aj[NC], sj[NC];
+      nlive += __popc(live);
+      if (live) {
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const float2 v = sm.col[q][32 * k + lane];
-        aj[k] = v.x;
-        sj[k] = v.y;
+        for (int k = 0; k < NC; ++k) {
+          const float2 v = sm.col[q][p][32 * k + lane];
+          aj[k] = v.x;
+          sj[k] = v.y;
+        }
       }
-    }
+      if (live) {   // vote result: uniform branch
+        const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
+        unsigned long long cm = 0;   // exact hits of this lane: bit r NC + k = (row i0 + r, column k)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          if (!((live >> r) & 1u)) continue;   // uniform
+          const float c = __shfl_sync(0xffffffffu, rv.x, r);
+          float y[NC];
+          if ((smask >> r) & 1u) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], aj[k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
+          }
+          if (rowmin<NC>(y) <= c) {   // this lane has a hit in row r: which columns
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+              if (y[k] <= c) cm |= 1ull << (r * NC + k);
+          }
+        }
+        if (cm) {   // one survivor entry per passing pair
+          int slot = atomicAdd(P.surv_cnt + b0 + s, __popcll(cm));
+          do {
+            const int bit = __ffsll((long long)cm) - 1;
+            cm &= cm - 1;
+            const int i = i0 + bit / NC, j = c0 + 32 * (bit % NC) + lane;
+            if (slot < cap) P.surv[(long long)(b0 + s) * cap + slot] = surv_entry(pair_index(n, i, j), i, j);
+            ++slot;
+          } while (cm);
+        }
+      }
+    }   // searches of the slot
     __syncwarp();
     if (lane == 0) {   // release the slot; the last of the four warps refills it
       __threadfence_block();   // this warp's reads of the slot precede the release
       const int old = atomicAdd(&sm.rel[q], 1);
-      if ((old & 3) == 3 && s + kRing < R) stage(s + kRing, q);
-    }
-    nlive += __popc(live);
-    if (live) {   // vote result: uniform branch
-      const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
-      unsigned long long cm = 0;   // exact hits of this lane: bit r NC + k = (row i0 + r, column k)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        if (!((live >> r) & 1u)) continue;   // uniform
-        const float c = __shfl_sync(0xffffffffu, rv.x, r);
-        float y[NC];
-        if ((smask >> r) & 1u) {
-#pragma unroll
-          for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], aj[k]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
-        }
-        if (rowmin<NC>(y) <= c) {   // this lane has a hit in row r: which columns
-#pragma unroll
-          for (int k = 0; k < NC; ++k)
-            if (y[k] <= c) cm |= 1ull << (r * NC + k);
-        }
-      }
-      if (cm) {   // one survivor entry per passing pair
-        int slot = atomicAdd(P.surv_cnt + b0 + s, __popcll(cm));
-        do {
-          const int bit = __ffsll((long long)cm) - 1;
-          cm &= cm - 1;
-          const int i = i0 + bit / NC, j = c0 + 32 * (bit % NC) + lane;
-          if (slot < cap) P.surv[(long long)(b0 + s) * cap + slot] = surv_entry(pair_index(n, i, j), i, j);
-          ++slot;
-        } while (cm);
-      }
+      if ((old & 3) == 3 && u + kRing < nslots) stage(u + kRing, q);
     }
   }
   if (lane == 0 && nlive) atomicAdd(P.eval_cnt + (blockIdx.x & 63), (unsigned long long)nlive * (32 * NC));
