@@ -386,6 +386,20 @@ def run_warmstart(args, device=0):
     print(json.dumps(line))
 
 
+def scan_traffic():
+    """DRAM bytes per launch of the candidate scan from its last ncu capture, or None when the
+    kernel source has changed since that capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_scan_pairs_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["traffic_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def roofline(res, pk):
     """Candidate scan (dominant kernel) against the SM issue rate."""
     ms, nl = res["prof"]["scan"]
@@ -400,7 +414,7 @@ def roofline(res, pk):
     peak = 152 * 128 * clk * 1e6 / 1e12
     ev = 2.0 * res["evald"] / max(1, nl) / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan_pairs",
+            "frac": round(achieved / peak, 4), "traffic": scan_traffic(), "kernel": "k_scan_pairs",
             "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch,
             "per_unit": "2 operations per pair candidate decided (signed FMA + compare)",
             "evaluated_ops_per_launch": 2.0 * res["evald"] / max(1, nl), "achieved_evaluated": round(ev, 3),

@@ -189,7 +189,7 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   CK(prof_begin(ctx, 1));
   if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
   else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
-  else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, ctx->tune.gemm_tile_searches, s));
+  else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, P.gemm_nt, s));
   CK(prof_end(ctx, 1));
   CK(prof_begin(ctx, 2));
   LAUNCH(launch_bound(P, s));
@@ -210,6 +210,9 @@ void drop_graph(qis_ctx* ctx) {
 }
 
 int build_work(qis_ctx* ctx) {
+  // searches per tensor-core tile: also the tiling of the spin operand that k_pick writes
+  ctx->P.gemm_nt = ctx->tune.gemm_tile_searches > 0 ? ctx->tune.gemm_tile_searches
+                                                      : gemm_tile_n(ctx->R, ctx->digits_used);
   std::vector<int4> w;
   for (int id = 0; id < (int)ctx->inst.size(); ++id) {
     const int nb = (ctx->inst[id].n + kTile - 1) / kTile;
@@ -337,7 +340,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     if (ctx->mode != QIS_FP64) {
       ALLOC(P.aq, B * NP);
       ALLOC(P.as32, B * NP);
-      ALLOC(P.S16, B * NP);
+      P.s16_stride = (long long)(ctx->R + 255) * NP;   // room for ceil(R / NT) tiles of any NT <= 256
+      ALLOC(P.S16, (size_t)ctx->max_inst * P.s16_stride);
     } else {
       ALLOC(P.a64, B * NP);
     }

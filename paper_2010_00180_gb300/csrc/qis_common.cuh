@@ -75,7 +75,9 @@ struct DevPtrs {
   uint32_t* dup_c;        // [b][K1] candidate index of every kept state one or two flips from the parent
   int* dup_n;             // [b] their number
   unsigned long long* surv;  // [b][cap] survivor entries {c, i, j} (surv_entry)
-  __half* S16;            // [b][NP] +-1 spins of the parent (0 past n), tensor-core operand
+  __half* S16;            // +-1 spins of the parents (0 past n), tensor-core operand, tiled (s16_offset)
+  long long s16_stride;   // halves of one instance's region of S16
+  int gemm_nt;            // searches per tensor-core tile (the S16 tiling)
   uint64_t* init_bits;    // [b][Wmax]
   double* init_E;         // [b] energy of the initial state (set with it)
   long long* init_q;      // [b] the same, exact E 2^q (split modes)
@@ -89,6 +91,23 @@ struct DevPtrs {
 };
 
 __host__ __device__ inline int words_of(int n) { return (n + 63) >> 6; }
+
+// Tensor-core operands are stored pre-tiled in the exact shared-memory image of a K-major
+// operand with 128-byte swizzle: a tile is rows x 64 FP16 (128 bytes per row), 8-row groups
+// of 1024 bytes, and the 16-byte chunk c of row r sits at chunk c ^ (r & 7). One contiguous bulk
+// copy then moves a whole tile into place.
+__host__ __device__ inline long long swz_in_tile(int r, int k) {
+  return (long long)r * 64 + ((((k & 63) >> 3) ^ (r & 7)) << 3) + (k & 7);
+}
+// Element (i, j) of one instance's digit plane: 128 x 64 tiles, row-block major.
+__host__ __device__ inline long long d16_offset(int i, int j, int NP) {
+  return ((long long)(i >> 7) * (NP >> 6) + (j >> 6)) * 8192 + swz_in_tile(i & 127, j);
+}
+// Spin k of search r (0 <= r < R) of one instance's S16 region: NT x 64 tiles, tile block of
+// searches major.
+__host__ __device__ inline long long s16_offset(int r, int k, int NT, int NP) {
+  return ((long long)(r / NT) * (NP >> 6) + (k >> 6)) * ((long long)NT * 64) + swz_in_tile(r % NT, k);
+}
 __host__ __device__ inline int pad_of(int n) { return (n + kPad - 1) / kPad * kPad; }
 
 // candidate index <-> sites: c < n single i = c; c >= n pair (i, j), i < j, lexicographic

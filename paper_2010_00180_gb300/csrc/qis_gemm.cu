@@ -10,8 +10,10 @@
 // single-flip energy change a_i = -2 s_i f_i (Sec. III) follows exactly.
 //
 // Persistent kernel, one CTA per SM, walking 128-row x NT-search tiles of all instances:
-//   warp 0 lane 0 : TMA producer (digit tiles of 128 x 64 and the spin tile NT x 64 per stage),
-//                   one ring of stages running across tile boundaries
+//   warp 0 lane 0 : producer: one bulk copy (TMA engine) per digit tile of 128 x 64 and one for
+//                   the spin tile NT x 64 per stage -- both operands are stored pre-tiled in the
+//                   swizzled shared-memory image (d16_offset, s16_offset), so every copy is
+//                   contiguous; one ring of stages runs across tile boundaries
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::f16, M=128, N=NT, K=16); tile number lt
 //                   accumulates into TMEM buffer lt % 2, so one tile's epilogue overlaps the
 //                   next tile's loads and MMAs
@@ -20,8 +22,6 @@
 //                   combination of the digits, a_i = -2 s_i f_i; release the buffer.
 // Every wait is bounded (2 s of %globaltimer); on timeout the CTA raises kStatTimeout, drains
 // what it issued (again bounded), frees its TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include "qis_common.cuh"
@@ -34,7 +34,8 @@ constexpr int kTileBytesA = 128 * kKC * 2;
 
 struct GemmArgs {
   int n_inst, R, NP, Wmax, NT, digits_max, stages, nbuf;
-  long long plane_rows;              // rows of one digit plane in the A tensor map (max_inst * NP)
+  long long plane;        // halves of one digit plane (every instance's NP x NP tiles)
+  long long s16_stride;   // halves of one instance's spin region
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -65,11 +66,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
   return true;
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
+// 1-D bulk copy global -> shared (TMA engine); completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 // K-major operand tile, 128-byte rows, 128B swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -110,9 +110,8 @@ __device__ __forceinline__ bool epi_vote(bool flag) {
 // Persistent: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; tile t is
 // (instance t / tpi, 128-row block, NT-search block), tpi = (NP / 128) * ceil(R / NT); row blocks
 // at or past an instance's n_pad are skipped by every role alike.
-__global__ void __launch_bounds__(192, 1) k_fields_tc(const __grid_constant__ CUtensorMap mapA,
-                                                      const __grid_constant__ CUtensorMap mapB, DevPtrs P,
-                                                      GemmArgs G) {
+__global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__ D16, const __half* __restrict__ S16,
+                                                      DevPtrs P, GemmArgs G) {
   const int NT = G.NT, S = G.stages, Dm = G.digits_max, nbuf = G.nbuf;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bytesB = NT * kKC * 2;
@@ -171,10 +170,13 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __grid_constant__ CU
         if (*(volatile int*)&s_err) break;
         unsigned char* st = smem + s * stage_bytes;
         mbar_expect_tx(&full[s], (uint32_t)(d.digits * kTileBytesA + bytesB));
+        // pre-tiled operands (d16_offset / s16_offset): one contiguous bulk copy per tile
+        const long long ta = ((long long)(m0 >> 7) * (G.NP >> 6) + kc) * 8192;
         for (int dg = 0; dg < d.digits; ++dg)
-          tma_load_2d(st + dg * kTileBytesA, &mapA, kc * kKC,
-                      (int)(dg * G.plane_rows + (long long)inst * G.NP + m0), &full[s]);
-        tma_load_2d(st + Dm * kTileBytesA, &mapB, kc * kKC, d.first_search + n0, &full[s]);
+          bulk_g2s(st + dg * kTileBytesA, D16 + dg * G.plane + (long long)inst * G.NP * G.NP + ta,
+                   (uint32_t)kTileBytesA, &full[s]);
+        const long long tb = ((long long)(n0 / NT) * (G.NP >> 6) + kc) * ((long long)NT * 64);
+        bulk_g2s(st + Dm * kTileBytesA, S16 + (long long)inst * G.s16_stride + tb, (uint32_t)bytesB, &full[s]);
       }
     }
     // drain: after an error the last (at most S) issued stages may still be in flight; each
@@ -301,32 +303,6 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __grid_constant__ CU
 }
 
 // ---------------------------------------------------------------- host side
-namespace {
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-cudaError_t get_encode() {
-  if (g_encode) return cudaSuccess;
-  cudaDriverEntryPointQueryResult q;
-  void* fn = nullptr;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess) return e;
-  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return cudaSuccess;
-}
-
-cudaError_t make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
-  cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kKC, box_rows};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-}  // namespace
-
 // Searches per tile: a multiple of 16 with two accumulator sets in TMEM (2 * digits * nt <= 512
 // columns) when possible, else one; among those the one that pads R the least, then the widest.
 int gemm_tile_n(int R, int digits) {
@@ -360,24 +336,18 @@ size_t gemm_smem(int digits, int nt) {
 // nt: searches per tile (multiple of 16, digits_max * nt <= 512), or 0 for gemm_tile_n's choice.
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,
                              int nt, cudaStream_t s) {
-  cudaError_t e = get_encode();
-  if (e != cudaSuccess) return e;
-  CUtensorMap mA, mB;
-  const long long plane_rows = (long long)max_inst * P.NP;
-  e = make_map(&mA, D16, (uint64_t)P.NP, (uint64_t)(plane_rows * digits_max), 128);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   GemmArgs G;
   G.n_inst = P.n_inst;
   G.R = P.R;
   G.NP = P.NP;
   G.Wmax = P.Wmax;
   G.digits_max = digits_max;
-  G.plane_rows = plane_rows;
+  G.plane = (long long)max_inst * P.NP * P.NP;
+  G.s16_stride = P.s16_stride;
   G.NT = nt > 0 ? nt : gemm_tile_n(P.R, digits_max);
   G.stages = gemm_stages(digits_max, G.NT);
   G.nbuf = (2 * digits_max * G.NT <= 512) ? 2 : 1;   // double-buffered accumulators if TMEM holds two
-  e = make_map(&mB, S16, (uint64_t)P.NP, (uint64_t)max_inst * P.R, (uint32_t)G.NT);
-  if (e != cudaSuccess) return e;
   const size_t sm = gemm_smem(digits_max, G.NT);
   static size_t attr = 0;
   if (attr < sm) {
@@ -395,7 +365,7 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
   const int tiles = P.n_inst * (P.NP / 128) * ((P.R + G.NT - 1) / G.NT);
   const int grid = tiles < n_sm ? tiles : n_sm;
   if (grid <= 0) return cudaSuccess;
-  k_fields_tc<<<grid, 192, sm, s>>>(mA, mB, P, G);
+  k_fields_tc<<<grid, 192, sm, s>>>(static_cast<const __half*>(D16), static_cast<const __half*>(S16), P, G);
   return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat
 }
 
 // ---------------------------------------------------------------- fixed point + digits
-// D16 rows use the context-wide stride NP (one 2D tensor map covers every instance and digit).
+// D16 holds, per digit and instance, an NP x NP plane in the tiled layout of d16_offset.
 __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pad, int NP, int q, int digits,
                            long long plane, __half* D16, long long* Jq, float* J4, long long* hq) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,7 +87,7 @@ __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pa
     for (int d = 0; d < digits; ++d) {
       long long r = x & 4095;                 // x mod 4096 in [0, 4095]
       if (r >= 2048) r -= 4096;               // balanced digit in [-2048, 2047]
-      D16[d * plane + (long long)i * NP + j] = __float2half_rn((float)r);
+      D16[d * plane + d16_offset(i, j, NP)] = __float2half_rn((float)r);
       x = (x - r) >> 12;                      // exact
     }
   }

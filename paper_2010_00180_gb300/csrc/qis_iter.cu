@@ -60,9 +60,11 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
     for (int w = lane; w < d.W; w += 32) P.par_bits[(long long)b * P.Wmax + w] = P.lst_bits[(base + sel) * P.Wmax + w];
     if (P.mode != QIS_FP64) {
       const uint64_t* src = P.lst_bits + (base + sel) * P.Wmax;
+      __half* dst = P.S16 + (long long)(b / P.R) * P.s16_stride;
+      const int r = b % P.R;
       for (int k = lane; k < d.n_pad; k += 32) {
         float v = (k < d.n) ? (sigma_of(src, k) ? -1.f : 1.f) : 0.f;
-        P.S16[(long long)b * P.NP + k] = __float2half_rn(v);
+        dst[s16_offset(r, k, P.gemm_nt, P.NP)] = __float2half_rn(v);
       }
     }
   }

@@ -166,12 +166,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   unsigned long long* se = sk + PC;                                         // [PC] their survivor entries
   unsigned long long* sk2 = se + PC;                                        // [kMergeThreads] sorted keys
   unsigned long long* se2 = sk2 + kMergeThreads;                            // [kMergeThreads] sorted entries
-  int* oslot = reinterpret_cast<int*>(se2 + kMergeThreads);                 // [K1]
-  int* occ = oslot + K1;                                                    // [K1]
-  int* freel = occ + K1;                                                    // [K1]
-  uint32_t* htab = reinterpret_cast<uint32_t*>(freel + K1);                // [HT] duplicate candidates
+  int* oslot = reinterpret_cast<int*>(se2 + kMergeThreads);                 // [K1] slot of old rank r
+  uint32_t* htab = reinterpret_cast<uint32_t*>(oslot + K1);                // [HT] duplicate candidates
   __shared__ uint64_t pb[kMaxN / 64];
-  __shared__ int s_nv, wsum[33], s_total;
+  __shared__ int s_nv, s_ocut, wsum[33];
   const int cnt = P.lst_count[b];
   const bool fp64 = P.mode == QIS_FP64;
   // threshold and parent energy: FP64 values in the plain form, exact integers E 2^q otherwise
@@ -187,8 +185,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   const uint64_t ph = P.par_hash[b];
   for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = kNoCand;
-  for (int k = threadIdx.x; k < K1; k += blockDim.x) occ[k] = 0;
-  if (threadIdx.x == 0) s_nv = 0;
+  if (threadIdx.x == 0) {
+    s_nv = 0;
+    s_ocut = cnt;
+  }
   __syncthreads();
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const int slot = P.lst_ord[base + r];
@@ -302,7 +302,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   }
   __syncthreads();
   // ---- 3. merge with the old list: old entry o -> rank o + #(new with E < E_o) (old entries
-  //         precede new ones of equal energy); new entry p -> p + #(old with E <= E_p)
+  //         precede new ones of equal energy); new entry p -> p + #(old with E <= E_p). Both
+  //         ranks grow along their lists, so the evicted old entries (rank >= K+1) are a
+  //         suffix o >= s_ocut and the kept new entries a prefix p < K+1 - s_ocut.
   for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
     const unsigned long long ko = okey[o];
     int lo = 0, hi = nv;
@@ -311,18 +313,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
       if (sk[mid] < ko) lo = mid + 1; else hi = mid;
     }
     const int rank = o + lo;
-    if (rank < K1) occ[oslot[o]] = 1 + rank;
+    if (rank < K1) P.lst_ord[base + rank] = oslot[o];
+    else atomicMin(&s_ocut, o);
   }
   __syncthreads();
-  // free slots in slot order (contiguous chunk per thread)
-  const int per = (K1 + blockDim.x - 1) / blockDim.x;
-  const int lo_k = threadIdx.x * per, hi_k = min(K1, lo_k + per);
-  int nfree = 0;
-  for (int k = lo_k; k < hi_k; ++k) nfree += occ[k] == 0;
-  int pos = block_exclusive_sum(nfree, wsum, &s_total);
-  for (int k = lo_k; k < hi_k; ++k)
-    if (occ[k] == 0) freel[pos++] = k;
-  __syncthreads();
+  // slots for the kept new entries, in order: those of the evicted old entries, then the ones
+  // a list that is not yet full has never used (its used slots are 0 .. cnt-1)
+  const int ocut = s_ocut, n_ev = cnt - ocut;
   const int t_now = P.iter_t[b];
   for (int p = threadIdx.x; p < nv; p += blockDim.x) {
     const unsigned long long kp = sk[p];
@@ -333,7 +330,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     }
     const int rank = p + lo;
     if (rank >= K1) continue;
-    const int slot = freel[p];   // the new entries kept are the first ones in sorted order
+    const int slot = (p < n_ev) ? oslot[ocut + p] : cnt + (p - n_ev);
     uint32_t c;
     int i, j;
     surv_decode(se[p], c, i, j);
@@ -351,16 +348,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     P.lst_used[base + slot] = 0;
     P.lst_ord[base + rank] = slot;
   }
-  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
-    const int slot = oslot[o];
-    if (occ[slot]) P.lst_ord[base + occ[slot] - 1] = slot;
-  }
   if (threadIdx.x == 0) P.lst_count[b] = min(K1, cnt + nv);
 }
 
 size_t merge_smem(int K1, int cap) {
   const int PC = next_pow2(cap > kMergeThreads ? cap : kMergeThreads), HT = next_pow2(2 * K1);
-  return (size_t)K1 * 8 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 12 + (size_t)HT * 4;
+  return (size_t)K1 * 8 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 4 + (size_t)HT * 4;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {

@@ -11,11 +11,11 @@
 // c0 + 32k + l, so every coupling load is a coalesced 128-byte row segment.
 //
 // Per search the block needs {a_j, s_j} of the chunk's columns and of its rows and a control
-// word; one thread stages them with three TMA bulk copies into a ring of kRing slots
-// (completion counted on the slot's mbarrier). The warps do not synchronise with each other:
-// each waits for the slot of its next search, reads it, and releases it; the fourth release
-// refills the slot with the search kRing ahead. A warp that meets many hits may fall behind
-// the others by up to kRing searches without stalling them.
+// word; one thread stages them with TMA bulk copies into a ring of kRing slots of kPer
+// searches each (completion counted on the slot's mbarrier). The warps do not synchronise with
+// each other: each waits for its next slot, works through its searches and releases it; the
+// fourth release refills the slot kRing slots ahead. A warp that meets many hits may fall
+// behind the others by up to kRing slots without stalling them.
 //
 // Per search and row (warp-uniform) each lane computes y_ij = fma(+-4J~_ij, s_j, a_j) -- the
 // row spin, taken from a ballot so the branch is provably uniform, picks the operand sign --
@@ -68,8 +68,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kRing = 8;                      // staging ring depth (power of two)
-constexpr int kPer = 2;                       // searches per ring slot
+constexpr int kRing = 4;                      // staging ring depth (power of two)
+constexpr int kPer = 4;                       // searches per ring slot
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
 
 // Staging ring of one block: slot u % kRing holds searches kPer u .. kPer u + kPer - 1. full[q]
