@@ -326,6 +326,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.lst_bits, B * K1 * W);
     ALLOC(P.lst_E, B * K1);
     ALLOC(P.lst_q, B * K1);
+    ALLOC(P.lst_key, B * K1);
     ALLOC(P.lst_stamp, B * K1);
     ALLOC(P.lst_hash, B * K1);
     ALLOC(P.lst_used, B * K1);
@@ -689,6 +690,7 @@ int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* 
   std::vector<uint64_t> lb((size_t)K1 * Wm, 0ull), st(K1, 0ull);
   std::vector<double> e(K1, INFINITY);
   std::vector<long long> eq(K1, 0);
+  std::vector<unsigned long long> key(K1, ~0ull);
   std::vector<uint8_t> u(K1, 0);
   std::vector<int> ord(K1, -1);
   int act = 0;
@@ -696,6 +698,14 @@ int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* 
     memcpy(&lb[(size_t)k * Wm], bits + (size_t)k * W, W * sizeof(uint64_t));
     e[k] = E[k];
     eq[k] = (ctx->mode != QIS_FP64) ? llrint(ldexp(E[k], q)) : 0;   // exact on the grid
+    if (ctx->mode != QIS_FP64) {
+      key[k] = qkey(eq[k]);
+    } else {   // order key of a double (as dkey on the device)
+      uint64_t u;
+      const double x = E[k] + 0.0;
+      memcpy(&u, &x, 8);
+      key[k] = (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+    }
     u[k] = used ? (used[k] != 0) : 0;
     st[k] = stamp ? stamp[k] : (uint64_t)k;
     ord[k] = k;
@@ -707,6 +717,7 @@ int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* 
   CK(cudaMemcpyAsync(P.lst_bits + base * Wm, lb.data(), lb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_E + base, e.data(), K1 * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_q + base, eq.data(), K1 * sizeof(long long), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.lst_key + base, key.data(), K1 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_stamp + base, st.data(), K1 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_used + base, u.data(), K1, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.lst_ord + base, ord.data(), K1 * sizeof(int), cudaMemcpyHostToDevice, s));

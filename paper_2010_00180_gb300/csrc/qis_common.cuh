@@ -53,6 +53,7 @@ struct DevPtrs {
   uint64_t* lst_bits;     // [b][K1][Wmax]
   double* lst_E;          // [b][K1]
   long long* lst_q;       // [b][K1] exact E * 2^q of each slot (split modes)
+  unsigned long long* lst_key;  // [b][K1] order key of the entry of rank r (qkey of E 2^q, or dkey of E)
   uint64_t* lst_stamp;    // [b][K1]
   uint64_t* lst_hash;     // [b][K1]
   uint8_t* lst_used;      // [b][K1]
@@ -157,6 +158,9 @@ __device__ inline unsigned long long dkey(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
   return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
 }
+
+// order-preserving key of an exact integer energy E 2^q (signed -> unsigned)
+__host__ __device__ inline unsigned long long qkey(long long x) { return (unsigned long long)x ^ (1ull << 63); }
 
 __host__ __device__ inline int next_pow2(int x) {
   int p = 1;

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
     for (int w = 0; w < W; ++w) P.lst_bits[base * P.Wmax + w] = bits[w];
     P.lst_E[base] = E0;
     if (P.mode != QIS_FP64) P.lst_q[base] = red[0];
+    P.lst_key[base] = (P.mode != QIS_FP64) ? qkey(red[0]) : dkey(E0);
     P.lst_stamp[base] = 0;
     P.lst_hash[base] = hsh;
     for (int k = 0; k < P.K1; ++k) {

@@ -200,13 +200,10 @@ __device__ void block_min_max(float& lo, float& hi) {
 // the bin holding that element (binning is monotone, so at least rank + 1 values lie in those
 // bins). Two passes over the values instead of the four of a radix select. Every thread of
 // the block calls it.
-__device__ float value_select_upper(const float* v, int cnt, int rank, int* hist) {
+// lo, hi: this thread's minimum and maximum of the values (the caller tracks them while writing
+// the values; the block-wide range is reduced here).
+__device__ float value_select_upper(const float* v, int cnt, int rank, int* hist, float lo, float hi) {
   __shared__ int s_b;
-  float lo = INFINITY, hi = -INFINITY;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    lo = fminf(lo, v[t]);
-    hi = fmaxf(hi, v[t]);
-  }
   for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
   block_min_max(lo, hi);
   const float scale = 255.99f / fmaxf(hi - lo, 1e-30f);
@@ -239,7 +236,7 @@ __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist
 constexpr int kSubSites = 64;   // at most this many low-a sites in the subset (2080 candidates)
 constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
 
-__global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
+__global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) {
     if (threadIdx.x == 0) {
@@ -261,7 +258,12 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   __shared__ float s_thr;
   __shared__ double s_T, s_cap;
   const int cnt = P.lst_count[b];
-  const double T = (cnt == P.K1) ? P.lst_E[base + P.lst_ord[base + P.K1 - 1]] : INFINITY;
+  // T: the last kept energy, from the rank-ordered keys (exact integers in the split modes)
+  double T = INFINITY;
+  if (cnt == P.K1) {
+    const unsigned long long kT = P.lst_key[base + P.K1 - 1];
+    T = fp64 ? dkey_inv(kT) : (double)(long long)(kT ^ (1ull << 63)) * d.inv_scale;
+  }
   const double Ep = P.par_E[b];
   const long long C = (long long)n * (n + 1) / 2;
   const double* a64 = P.a64 + (long long)b * P.NP;
@@ -315,21 +317,28 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
   // among the K+1+near lowest candidates at least K+1 are new states.
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
     const uint64_t* x = P.lst_bits + (base + P.lst_ord[base + r]) * P.Wmax;
-    // one pass: the distance and the first two differing sites (ascending)
+    // one pass: the distance and the first two differing sites (ascending); the words come in
+    // blocks of 8 loaded together, then examined
     int dist = 0, p0 = 0, p1 = 0;
-    for (int w = 0; w < d.W; ++w) {
-      uint64_t v = x[w] ^ pb[w];
-      if (v && dist < 2) {
-        const int lo = w * 64 + __ffsll((long long)v) - 1;
-        if (dist == 0) {
-          p0 = lo;
-          v &= v - 1;
-          if (v) p1 = w * 64 + __ffsll((long long)v) - 1;
-        } else {
-          p1 = lo;
+    for (int w0 = 0; w0 < d.W; w0 += 8) {
+      uint64_t xw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xw[u] = (w0 + u < d.W) ? (x[w0 + u] ^ pb[w0 + u]) : 0ull;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        uint64_t v = xw[u];
+        if (v && dist < 2) {
+          const int lo = (w0 + u) * 64 + __ffsll((long long)v) - 1;
+          if (dist == 0) {
+            p0 = lo;
+            v &= v - 1;
+            if (v) p1 = (w0 + u) * 64 + __ffsll((long long)v) - 1;
+          } else {
+            p1 = lo;
+          }
         }
+        dist += __popcll(xw[u]);
       }
-      dist += __popcll(x[w] ^ pb[w]);
     }
     if (dist == 1 || dist == 2)
       P.dup_c[base + atomicAdd(&s_near, 1)] = (dist == 1) ? (uint32_t)p0 : pair_index(n, p0, p1);
@@ -371,7 +380,8 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
     const int mm = min(s_nsites, kSubSites);
     const int M = mm + mm * (mm - 1) / 2;
     if (M >= k) {
-      // subset candidate energies, in the scan's arithmetic
+      // subset candidate energies, in the scan's arithmetic (with their range per thread)
+      float vlo = INFINITY, vhi = -INFINITY;
 #pragma unroll 2
       for (int t = threadIdx.x; t < M; t += blockDim.x) {
         int i, j = -1;
@@ -404,11 +414,13 @@ __global__ void __launch_bounds__(128) k_bound(DevPtrs P) {
             de = as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x);
           }
           reinterpret_cast<float*>(subkey)[t] = de;
+          vlo = fminf(vlo, de);
+          vhi = fmaxf(vhi, de);
         }
       }
       __syncthreads();
       if (fp64) U = dkey_inv(radix_select<unsigned long long>(subkey, M, k - 1, hist));
-      else U = (double)value_select_upper(reinterpret_cast<const float*>(subkey), M, k - 1, hist);
+      else U = (double)value_select_upper(reinterpret_cast<const float*>(subkey), M, k - 1, hist, vlo, vhi);
     }
   }
   if (threadIdx.x == 0) {

@@ -22,8 +22,7 @@ namespace qis {
 constexpr uint32_t kNoCand = 0xffffffffu;   // empty slot of the duplicate table
 __device__ inline uint32_t chash(uint32_t c) { return (c * 2654435761u) >> 7; }
 
-// order-preserving key of an exact integer energy E 2^q (signed -> unsigned)
-__device__ inline unsigned long long qkey(long long x) { return (unsigned long long)x ^ (1ull << 63); }
+
 
 // exclusive prefix sum of one int per thread over the block (blockDim multiple of 32)
 __device__ int block_exclusive_sum(int v, int* wsum /* [33] */, int* total) {
@@ -190,10 +189,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     s_ocut = cnt;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-    const int slot = P.lst_ord[base + r];
-    oslot[r] = slot;
-    okey[r] = fp64 ? dkey(P.lst_E[base + slot]) : qkey(P.lst_q[base + slot]);
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {   // two independent coalesced loads
+    oslot[r] = P.lst_ord[base + r];
+    okey[r] = P.lst_key[base + r];
   }
   // candidate indices of the kept states one or two flips from the parent (from k_bound): the
   // only candidates that can equal a kept state
@@ -313,8 +311,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
       if (sk[mid] < ko) lo = mid + 1; else hi = mid;
     }
     const int rank = o + lo;
-    if (rank < K1) P.lst_ord[base + rank] = oslot[o];
-    else atomicMin(&s_ocut, o);
+    if (rank < K1) {
+      P.lst_ord[base + rank] = oslot[o];
+      P.lst_key[base + rank] = ko;
+    } else {
+      atomicMin(&s_ocut, o);
+    }
   }
   __syncthreads();
   // slots for the kept new entries, in order: those of the evicted old entries, then the ones
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
     P.lst_used[base + slot] = 0;
     P.lst_ord[base + rank] = slot;
+    P.lst_key[base + rank] = kp;
   }
   if (threadIdx.x == 0) P.lst_count[b] = min(K1, cnt + nv);
 }

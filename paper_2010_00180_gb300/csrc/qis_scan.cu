@@ -68,8 +68,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-constexpr int kRing = 4;                      // staging ring depth (power of two)
-constexpr int kPer = 4;                       // searches per ring slot
+constexpr int kRing = 2;                      // staging ring depth (power of two)
+constexpr int kPer = 8;                       // searches per ring slot
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
 
 // Staging ring of one block: slot u % kRing holds searches kPer u .. kPer u + kPer - 1. full[q]
