@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int row = quarter * 32 + lane;
       const int i = m0 + row;
+      const float scale_q = (float)d.inv_scale;   // 2^-q, exact in FP32 (q <= 64)
       const long long hq = (i < d.n) ? P.hq[d.off_vec + i] : 0;
       for (int c0 = 0; c0 < NT; c0 += 16) {
         long long acc[16];
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
             if (i < d.n) {
               const int sg = (int)((s_pw[t][row >> 6] >> (row & 63)) & 1ull);   // sigma_i of the parent
               aq = sg ? 2 * acc[u] : -2 * acc[u];
-              as = make_float2((float)((double)aq * d.inv_scale), sg ? -1.f : 1.f);   // 2^-q: exact
+              // fl32(aq 2^-q) = fl32(aq) 2^-q: scaling by a power of two commutes with rounding
+              as = make_float2(__ll2float_rn(aq) * scale_q, sg ? -1.f : 1.f);
             }
             P.aq[b * P.NP + i] = aq;
             P.as32[b * P.NP + i] = as;
