@@ -345,6 +345,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
       ALLOC(P.S16, (size_t)ctx->max_inst * P.s16_stride);
     } else {
       ALLOC(P.a64, B * NP);
+      ALLOC(P.amin64, B);
     }
     ALLOC(P.thr32, B);
     if (ctx->mode != QIS_FP64) {
@@ -443,6 +444,7 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
   d.inv_scale = 1.0;
   d.rounded = 0;
   d.j4max = 0.f;
+  d.j4max64 = 4.0 * maxJ;   // exact (power-of-two scaling)
   if (ctx->mode != QIS_FP64) {
     double S = 0.0;
     for (int i = 0; i < n; ++i) S += st[4 + i];

@@ -32,6 +32,7 @@ struct InstDesc {
   long long off_vec;  // element offset of this instance's n_pad vectors
   double inv_scale;   // 2^-q
   float j4max;        // max |fl32(4 J_ij)|
+  double j4max64;    // 4 max |J_ij| (exact in FP64)
   int rounded;        // input was rounded onto the grid
 };
 
@@ -72,6 +73,7 @@ struct DevPtrs {
   float4* sctl;           // [b] {thr, active, 0, 0}: staged by the scan with the row data
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
+  double* amin64;         // [b] FP64 mode: min_i a_i of the parent (the scan's row bound)
   int* surv_cnt;          // [b]
   uint32_t* dup_c;        // [b][K1] candidate index of every kept state one or two flips from the parent
   int* dup_n;             // [b] their number

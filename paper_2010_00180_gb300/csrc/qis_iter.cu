@@ -282,6 +282,20 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     s_near = 0;
   }
   __syncthreads();
+  if (fp64) {
+    // FP64 mode: min_i a_i exactly, for the scan's row bound
+    __shared__ double wmn64[4];
+    double mn = INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) mn = fmin(mn, a64[i]);
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) wmn64[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = wmn64[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmin(m, wmn64[w]);
+      P.amin64[b] = m;
+    }
+  }
   // range of a_i (a ~ fl32 of the exact value in FP64 mode too: only used to bin sites)
   {
     float mn = INFINITY, mx = -INFINITY;
@@ -349,8 +363,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   const float amin = s_amin, amax = s_amax;
   double U = INFINITY;
   if (C > k && k <= kSubMax) {
-    // m lowest sites with m + m(m-1)/2 >= min(4k, kSubMax): found with a 256-bin histogram of a
-    const int want = min(4 * k, kSubMax);
+    // m lowest sites with m + m(m-1)/2 >= min(3k, kSubMax): found with a 256-bin histogram of a
+    const int want = min(3 * k, kSubMax);
     int m = 1;
     while (m < n && m + m * (m - 1) / 2 < want) ++m;
     const float span = fmaxf(amax - amin, 1e-30f);
@@ -499,13 +513,18 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
     if (threadIdx.x < kTile) ar_s[threadIdx.x] = a[i0 + threadIdx.x];
     else if (threadIdx.x < 2 * kTile) ac_s[threadIdx.x - kTile] = a[j0 + threadIdx.x - kTile];
     __syncthreads();
-    const double T = P.thrE[b], cap = P.capE[b], Ep = P.par_E[b];
+    const double T = P.thrE[b], cap = P.capE[b], Ep = P.par_E[b], amin = P.amin64[b];
     const uint64_t wi = P.par_bits[(long long)b * P.Wmax + w.y];
     const uint64_t wj = P.par_bits[(long long)b * P.Wmax + w.z];
     const unsigned rs = (unsigned)(wi >> (ty * 4)) & 15u, cs = (unsigned)(wj >> (tx * 4)) & 15u;
     for (int r = 0; r < 4; ++r) {
       const int i = i0 + ty * 4 + r;
       const double ai = ar_s[ty * 4 + r];
+      // every E' of row i is at least the same expression with a_j -> min a and 4 s_i s_j J_ij
+      // -> -4 max |J| (each FP64 addition is monotone in both arguments): skip the row when
+      // that lower bound already fails the test
+      const double lb = __dadd_rn(Ep, __dadd_rn(__dadd_rn(ai, amin), -d.j4max64));
+      if (!(lb < T) || lb > cap) continue;
       for (int c = 0; c < 4; ++c) {
         const int j = j0 + tx * 4 + c;
         if (j <= i || j >= n) continue;
