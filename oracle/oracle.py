@@ -49,13 +49,20 @@ def _load():
             lib.orc_fields.argtypes = [C.c_int, P, P, P, P]
             lib.orc_candidates.restype = None
             lib.orc_candidates.argtypes = [C.c_int, P, P, P, P]
+            lib.orc_candidates_flips.restype = None
+            lib.orc_candidates_flips.argtypes = [C.c_int, P, P, P, C.c_int, P]
             lib.orc_pair_rank.restype = C.c_int64
             lib.orc_pair_rank.argtypes = [C.c_int, C.c_int, C.c_int]
             lib.orc_qi_search.restype = C.c_int
             lib.orc_qi_search.argtypes = [C.c_int, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P]
+            lib.orc_qi_search_flips.restype = C.c_int
+            lib.orc_qi_search_flips.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, P, P, P, P, P, P, P]
             lib.orc_qi_multi_search.restype = C.c_int
             lib.orc_qi_multi_search.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, P,
                                                 P, P, P, P, P, P, P, P, P, P]
+            lib.orc_qi_multi_search_flips.restype = C.c_int
+            lib.orc_qi_multi_search_flips.argtypes = [C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_int, P,
+                                                      P, P, P, P, P, P, P, P, P, P]
             lib.orc_brute_force.restype = C.c_int
             lib.orc_brute_force.argtypes = [C.c_int, P, P, C.c_int, P, P]
             _lib = lib
@@ -99,12 +106,16 @@ def fields(J, h, bits) -> np.ndarray:
     return f
 
 
-def candidates(J, h, bits) -> np.ndarray:
-    """E' of every single and pair flip of one state, in candidate order (n(n+1)/2 values)."""
+FLIPS = {"singles+pairs": 0, "singles": 1, "exchange": 2}
+
+
+def candidates(J, h, bits, flips: int = 0) -> np.ndarray:
+    """E' of every single and pair flip of one state, in candidate order (n(n+1)/2 values);
+    candidates outside the flip set (1: singles only, 2: exchanges only) are +inf."""
     J, h, n = _prep(J, h)
     b = np.ascontiguousarray(bits, dtype=np.uint64).reshape(-1)
     out = np.empty(n * (n + 1) // 2)
-    _load().orc_candidates(n, _p(J), _p(h), _p(b), _p(out))
+    _load().orc_candidates_flips(n, _p(J), _p(h), _p(b), int(flips), _p(out))
     return out
 
 
@@ -122,8 +133,9 @@ def _check(rc):
                            -3: "placeholder would become a parent"}.get(rc, str(rc)))
 
 
-def qi_search(J, h, K: int, I: int, psi0) -> dict:
-    """Algorithm 3 from one initial state; returns the K+1-slot list in energy order."""
+def qi_search(J, h, K: int, I: int, psi0, flips: int = 0) -> dict:
+    """Algorithm 3 from one initial state; returns the K+1-slot list in energy order.
+    flips: 0 single and pair flips (Eq. (H1)), 1 single flips only, 2 spin exchanges only."""
     J, h, n = _prep(J, h)
     W, K1 = words(n), K + 1
     psi0 = np.ascontiguousarray(psi0, dtype=np.uint64).reshape(-1)
@@ -134,12 +146,12 @@ def qi_search(J, h, K: int, I: int, psi0) -> dict:
     stamp = np.zeros(K1, np.uint64)
     cnt = C.c_int(0)
     prod = C.c_int(0)
-    _check(_load().orc_qi_search(n, _p(J), _p(h), K, I, _p(psi0), _p(bits), _p(E), _p(used),
-                                 _p(stamp), C.byref(cnt), C.byref(prod)))
+    _check(_load().orc_qi_search_flips(n, _p(J), _p(h), K, I, int(flips), _p(psi0), _p(bits), _p(E),
+                                       _p(used), _p(stamp), C.byref(cnt), C.byref(prod)))
     return dict(bits=bits, E=E, used=used, stamp=stamp, count=cnt.value, productive=prod.value)
 
 
-def qi_multi_search(J, h, K: int, I: int, phi, per_search: bool = False) -> dict:
+def qi_multi_search(J, h, K: int, I: int, phi, per_search: bool = False, flips: int = 0) -> dict:
     """Algorithm 4 with the L initial states ``phi`` (L, W); returns the merged list."""
     J, h, n = _prep(J, h)
     W, K1 = words(n), K + 1
@@ -159,8 +171,9 @@ def qi_multi_search(J, h, K: int, I: int, phi, per_search: bool = False) -> dict
         ac = np.zeros(L, np.int32)
     else:
         ab = aE = au = ast = ac = None
-    _check(_load().orc_qi_multi_search(n, _p(J), _p(h), K, I, L, _p(phi), _p(bits), _p(E), _p(used),
-                                       _p(src), C.byref(cnt), _p(ab), _p(aE), _p(au), _p(ast), _p(ac)))
+    _check(_load().orc_qi_multi_search_flips(n, _p(J), _p(h), K, I, int(flips), L, _p(phi), _p(bits), _p(E),
+                                             _p(used), _p(src), C.byref(cnt), _p(ab), _p(aE), _p(au), _p(ast),
+                                             _p(ac)))
     out = dict(bits=bits, E=E, used=used, src=src, count=cnt.value)
     if per_search:
         out["searches"] = [dict(bits=ab[r], E=aE[r], used=au[r], stamp=ast[r], count=int(ac[r]))

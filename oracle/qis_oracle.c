@@ -32,6 +32,15 @@
  * Sec. III): candidate index c = i for the single flip of site i (c < N), then
  * c = N + rank(i, j) for the pair i < j in lexicographic order.
  *
+ * Flip sets (`flips`): 0 = the single and pair flips of H1 (Eq. (H1), the paper's study);
+ * 1 = single flips only (J = 1, the uniform transverse field of the Sec. V outlook);
+ * 2 = spin exchanges only (the XX + YY interaction of the Sec. V outlook: the pair (i, j) is
+ * a candidate only when s_i != s_j, flipping both, so the total sigma^z is conserved). The
+ * candidate index space and loop order stay those of flips = 0; excluded candidates are
+ * skipped. With flips = 2 the reachable states are the initial state's magnetisation
+ * sector; if that sector is smaller than K+1, the first unused entry can be a placeholder,
+ * which (as for any search whose reachable states are all used) ends the search.
+ *
  * Every list entry also records a "stamp": 0 for the initial state, (t << 32) | c for a
  * state inserted as candidate c of iteration t (1-based). Stamps are bookkeeping for the
  * tests; they never influence the algorithm.
@@ -97,16 +106,32 @@ static double cand_dE(int n, const double* J, const double* f, const uint64_t* b
 
 /* E' of every candidate of one parent, in candidate order (singles, then pairs i<j):
  * E' = E(parent) + dE with the incremental formulas above. out has n(n+1)/2 entries. */
-void orc_candidates(int n, const double* J, const double* h, const uint64_t* bits, double* out) {
+/* Whether candidate (i, j) (j < 0: single flip) belongs to the flip set (see top). */
+static int in_flip_set(int flips, const uint64_t* bits, int i, int j) {
+  if (j < 0) return flips != 2;
+  if (flips == 1) return 0;
+  if (flips == 2) return get_sigma(bits, i) != get_sigma(bits, j);
+  return 1;
+}
+
+/* As orc_candidates for a flip set; excluded candidates get +infinity. */
+void orc_candidates_flips(int n, const double* J, const double* h, const uint64_t* bits, int flips,
+                          double* out) {
   double* f = malloc((size_t)n * sizeof(double));
   if (!f) return;
   orc_fields(n, J, h, bits, f);
   const double Ep = orc_energy(n, J, h, bits);
   int64_t c = 0;
-  for (int i = 0; i < n; ++i) out[c++] = Ep + cand_dE(n, J, f, bits, i, -1);
+  for (int i = 0; i < n; ++i, ++c)
+    out[c] = in_flip_set(flips, bits, i, -1) ? Ep + cand_dE(n, J, f, bits, i, -1) : 1.0 / 0.0;
   for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j) out[c++] = Ep + cand_dE(n, J, f, bits, i, j);
+    for (int j = i + 1; j < n; ++j, ++c)
+      out[c] = in_flip_set(flips, bits, i, j) ? Ep + cand_dE(n, J, f, bits, i, j) : 1.0 / 0.0;
   free(f);
+}
+
+void orc_candidates(int n, const double* J, const double* h, const uint64_t* bits, double* out) {
+  orc_candidates_flips(n, J, h, bits, 0, out);
 }
 
 /* ------------------------------------------------------------ state lists */
@@ -228,7 +253,7 @@ static void update_list_sub(qlist* L, const uint64_t* x, double e, uint8_t l, in
  * update_list computes E' first and performs the duplicate binary search only when
  * E' < E_{K+1}: both tests are side-effect free and the insertion needs both, so the
  * outcome equals the paper's search-first order. */
-static int qi_search(const double* J, const double* h, int n, int K, int I, const uint64_t* psi0,
+static int qi_search(const double* J, const double* h, int n, int K, int I, int flips, const uint64_t* psi0,
                      qlist* L, int* n_productive) {
   const int W = nwords(n);
   int rc = list_init(L, n, K);
@@ -251,7 +276,10 @@ static int qi_search(const double* J, const double* h, int n, int K, int I, cons
     for (k = 0; k < L->K1; ++k)
       if (!L->l[k]) break;
     if (k == L->K1) continue;              /* every entry used: the iteration does nothing */
-    if (L->empty[k]) { rc = ORC_EPLACEHOLDER; break; }
+    if (L->empty[k]) {
+      if (flips == 0) { rc = ORC_EPLACEHOLDER; break; }   /* unreachable for K < 2^N */
+      continue;                            /* the sector's reachable states are all used */
+    }
     L->l[k] = 1;
     ++prod;
     memcpy(parent, L->psi + (size_t)k * W, (size_t)W * 8);
@@ -262,6 +290,7 @@ static int qi_search(const double* J, const double* h, int n, int K, int I, cons
     for (int order = 1; order <= 2; ++order) {
       for (int i = 0; i < n; ++i) {
         for (int j = (order == 1 ? -1 : i + 1); j < (order == 1 ? 0 : n); ++j, ++c) {
+          if (!in_flip_set(flips, parent, i, j)) continue;
           const double e = Ep + cand_dE(n, J, f, parent, i, j);   /* E' */
           if (!(e < L->E[L->K1 - 1])) continue;
           memcpy(x, parent, (size_t)W * 8);                        /* Alg. 1: XOR with 2^i (+2^j) */
@@ -304,17 +333,25 @@ static void export_list(const qlist* L, uint64_t* bits, double* E, uint8_t* used
 
 /* Alg. 3. Outputs hold K+1 slots in energy order; slots past *count are placeholders
  * (bits 0, E = DBL_MAX, stamp = UINT64_MAX). Any output pointer may be NULL. */
-int orc_qi_search(int n, const double* J, const double* h, int K, int I, const uint64_t* psi0,
-                  uint64_t* bits_out, double* E_out, uint8_t* used_out, uint64_t* stamp_out,
-                  int* count_out, int* productive_out) {
+int orc_qi_search_flips(int n, const double* J, const double* h, int K, int I, int flips,
+                        const uint64_t* psi0, uint64_t* bits_out, double* E_out, uint8_t* used_out,
+                        uint64_t* stamp_out, int* count_out, int* productive_out) {
   int rc = check_args(n, K);
   if (rc) return rc;
+  if (flips < 0 || flips > 2) return ORC_EINVAL;
   qlist L;
-  rc = qi_search(J, h, n, K, I, psi0, &L, productive_out);
+  rc = qi_search(J, h, n, K, I, flips, psi0, &L, productive_out);
   if (rc) return rc;
   export_list(&L, bits_out, E_out, used_out, stamp_out, NULL, count_out);
   list_free(&L);
   return ORC_OK;
+}
+
+int orc_qi_search(int n, const double* J, const double* h, int K, int I, const uint64_t* psi0,
+                  uint64_t* bits_out, double* E_out, uint8_t* used_out, uint64_t* stamp_out,
+                  int* count_out, int* productive_out) {
+  return orc_qi_search_flips(n, J, h, K, I, 0, psi0, bits_out, E_out, used_out, stamp_out, count_out,
+                             productive_out);
 }
 
 /* ---------------------------------------------------------------- Alg. 4 */
@@ -325,17 +362,17 @@ int orc_qi_search(int n, const double* J, const double* h, int K, int I, const u
  * energy-ordered E_{0,j}; the entries are read here as (psi_{0,j}, E_{0,j}, l_{0,j}).)
  * src of a merged entry = (search index r << 32) | position in search r's final list.
  * Optional per-search outputs (L x (K+1) slots each) may be NULL. */
-int orc_qi_multi_search(int n, const double* J, const double* h, int K, int I, int Lc,
-                        const uint64_t* phi, uint64_t* bits_out, double* E_out, uint8_t* used_out,
-                        uint64_t* src_out, int* count_out,
-                        uint64_t* all_bits, double* all_E, uint8_t* all_used, uint64_t* all_stamp,
-                        int* all_count) {
+int orc_qi_multi_search_flips(int n, const double* J, const double* h, int K, int I, int flips, int Lc,
+                              const uint64_t* phi, uint64_t* bits_out, double* E_out, uint8_t* used_out,
+                              uint64_t* src_out, int* count_out,
+                              uint64_t* all_bits, double* all_E, uint8_t* all_used, uint64_t* all_stamp,
+                              int* all_count) {
   int rc = check_args(n, K);
   if (rc) return rc;
-  if (Lc < 1) return ORC_EINVAL;
+  if (Lc < 1 || flips < 0 || flips > 2) return ORC_EINVAL;
   const int W = nwords(n), K1 = K + 1;
   qlist M;
-  rc = qi_search(J, h, n, K, I, phi, &M, NULL);
+  rc = qi_search(J, h, n, K, I, flips, phi, &M, NULL);
   if (rc) return rc;
   for (int k = 0; k < K1; ++k)
     if (!M.empty[k]) M.src[k] = (uint64_t)k;
@@ -343,7 +380,7 @@ int orc_qi_multi_search(int n, const double* J, const double* h, int K, int I, i
     export_list(&M, all_bits, all_E, all_used, all_stamp, NULL, all_count);
   for (int r = 1; r < Lc && !rc; ++r) {
     qlist S;
-    rc = qi_search(J, h, n, K, I, phi + (size_t)r * W, &S, NULL);
+    rc = qi_search(J, h, n, K, I, flips, phi + (size_t)r * W, &S, NULL);
     if (rc) break;
     if (all_bits || all_E || all_used || all_stamp || all_count)
       export_list(&S, all_bits ? all_bits + (size_t)r * K1 * W : NULL, all_E ? all_E + (size_t)r * K1 : NULL,
@@ -361,6 +398,15 @@ int orc_qi_multi_search(int n, const double* J, const double* h, int K, int I, i
   if (!rc) export_list(&M, bits_out, E_out, used_out, NULL, src_out, count_out);
   list_free(&M);
   return rc;
+}
+
+int orc_qi_multi_search(int n, const double* J, const double* h, int K, int I, int Lc,
+                        const uint64_t* phi, uint64_t* bits_out, double* E_out, uint8_t* used_out,
+                        uint64_t* src_out, int* count_out,
+                        uint64_t* all_bits, double* all_E, uint8_t* all_used, uint64_t* all_stamp,
+                        int* all_count) {
+  return orc_qi_multi_search_flips(n, J, h, K, I, 0, Lc, phi, bits_out, E_out, used_out, src_out, count_out,
+                                   all_bits, all_E, all_used, all_stamp, all_count);
 }
 
 /* ------------------------------------------------------------ brute force */

@@ -46,7 +46,7 @@ struct qis_ctx {
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
   double* stats = nullptr;
-  int4* work = nullptr;    // FP64 scan: 64 x 64 tiles
+  int4* work = nullptr;    // FP64 scan: 64 x 64 tiles x groups of searches
   int n_work = 0;
   int4* tasks = nullptr;   // FP32 scan: warp tasks (instance, strip, first column, chunk width)
   int n_tasks = 0;
@@ -217,10 +217,12 @@ int build_work(qis_ctx* ctx) {
   for (int id = 0; id < (int)ctx->inst.size(); ++id) {
     const int nb = (ctx->inst[id].n + kTile - 1) / kTile;
     for (int bi = 0; bi < nb; ++bi)
-      for (int bj = bi; bj < nb; ++bj) w.push_back(make_int4(id, bi, bj, 0));
+      for (int bj = bi; bj < nb; ++bj)
+        for (int g = 0; g * kScan64Group < ctx->R; ++g) w.push_back(make_int4(id, bi, bj, g));
   }
   ctx->n_work = (int)w.size();
-  const size_t cap_items = (size_t)ctx->max_inst * ((ctx->NP / kTile) * (ctx->NP / kTile + 1) / 2);
+  const size_t cap_items = (size_t)ctx->max_inst * ((ctx->NP / kTile) * (ctx->NP / kTile + 1) / 2) *
+                           ((ctx->R + kScan64Group - 1) / kScan64Group);
   if (w.size() > cap_items) return fail(ctx, QIS_ERR_STATE, "work list overflow");
   if (!w.empty()) CK(cudaMemcpyAsync(ctx->work, w.data(), w.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
   // warp tasks of the FP32 pair scan, widest chunks first (better tail balance)
@@ -302,7 +304,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     }
     ALLOC(ctx->zob, kMaxN);
     ALLOC(ctx->stats, kMaxN + 8);
-    ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2));
+    ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2) *
+                         ((ctx->R + kScan64Group - 1) / kScan64Group));
     ctx->tasks_cap = (size_t)ctx->max_inst * (NP / 8) * (NP / 32 + 2);
     ALLOC(ctx->tasks, ctx->tasks_cap);
     DevPtrs& P = ctx->P;

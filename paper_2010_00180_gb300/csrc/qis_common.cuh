@@ -14,6 +14,7 @@ constexpr int kTile = 64;        // scan tile edge (sites)
 constexpr int kPad = 128;        // n is padded to a multiple of this (tensor-core M tile)
 constexpr int kMaxDigits = 5;    // 12-bit signed digits (base 4096) of the fixed-point couplings
 constexpr int kMaxN = 4096;
+constexpr int kScan64Group = 4;  // searches per block of the FP64 pair scan
 
 // Device error flags (bit mask in ctx status word).
 constexpr int kStatCapacity = 1;

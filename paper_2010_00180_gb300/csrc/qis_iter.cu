@@ -490,7 +490,7 @@ cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {
 
 // ---------------------------------------------------------------- FP64 pair scan
 // Plain form: E' = E_p + dE exactly as defined; survivors have E' < T and E' <= cap.
-// One block per 64 x 64 tile (bi <= bj) of one instance, all R searches.
+// One block per 64 x 64 tile (bi <= bj) of one instance and group of kScan64Group searches.
 __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
   const int4 w = work[blockIdx.x];
   const InstDesc d = P.inst[w.x];
@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
   }
   __syncthreads();
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  for (int s = 0; s < P.R; ++s) {
+  const int s_end = min(P.R, (w.w + 1) * kScan64Group);
+  for (int s = w.w * kScan64Group; s < s_end; ++s) {
     const int b = d.first_search + s;
     __syncthreads();
     if (!P.active[b]) continue;
