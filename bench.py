@@ -37,13 +37,27 @@ sys.path.insert(0, ROOT)
 METRIC = "pair-flip candidates evaluated/s and time-to-ground-state at N=600 on 1 GB300"
 UNIT = "pair candidates/s"
 
+
+def unit_of(flips):
+    return "single-flip candidates/s" if flips == "single" else UNIT
+
 WORKLOADS = {
-    # name: (ensemble, n, instances, K, R, iterations, precision)
+    # name: (ensemble, n, instances, K, R, iterations, precision[, flip set])
     "gaussian_n600_120x64": ("gaussian", 600, 120, 120, 64, 120, "split_bf16"),
     "gaussian_n100_120x32_fp64": ("gaussian", 100, 120, 120, 32, 120, "fp64"),
     "pm1_n1024_64x128": ("pm1", 1024, 64, 120, 128, 120, "pm1_fp8"),
     "gaussian_n16_1x4": ("gaussian", 16, 1, 8, 4, 8, "split_bf16"),
+    # flip-set variants (Sec. V outlook): spin exchanges; single flips only at a larger n
+    "gaussian_n600_120x64_exchange": ("gaussian", 600, 120, 120, 64, 120, "split_bf16", "exchange"),
+    "gaussian_n2048_32x64_single": ("gaussian", 2048, 32, 120, 64, 120, "split_bf16", "single"),
 }
+FLIP_CODES = {"single_pair": 0, "single": 1, "exchange": 2}
+
+
+def workload_spec(name):
+    """(ensemble, n, instances, K, R, iterations, precision, flip set name)."""
+    w = WORKLOADS[name]
+    return w if len(w) == 8 else w + ("single_pair",)
 DEFAULT = "gaussian_n600_120x64"
 
 
@@ -57,32 +71,34 @@ def peaks():
 
 # ------------------------------------------------------------------ CPU oracle leg
 def _oracle_job(args):
-    ens, n, K, I_, seed, inst, r = args
+    ens, n, K, I_, seed, inst, r, fl = args
     from oracle import oracle as O
     from paper_2010_00180_gb300 import inputs as I
     J, h = I.instance(ens, n, seed=seed, inst=inst)
     phi = I.random_states(n, 1 + r, seed=seed + 1000, inst=inst)[r]
     t = time.perf_counter()
-    res = O.qi_search(J, h, K, I_, phi)
-    return time.perf_counter() - t, res["productive"]
+    res = O.qi_search(J, h, K, I_, phi, flips=fl)
+    m = int(I.unpack_bits(phi, n).sum())
+    per = {0: n * (n - 1) // 2, 1: n, 2: m * (n - m)}[fl]   # candidates of the metric per parent
+    return time.perf_counter() - t, res["productive"] * per
 
 
 def oracle_sample(workload, n_searches, cores, seed):
     """The oracle as it stands on `n_searches` searches of instance 0 (full I iterations each),
     one process per core (spawned before any GPU use)."""
-    ens, n, _, K, _, I_, _ = WORKLOADS[workload]
+    ens, n, _, K, _, I_, _, flips = workload_spec(workload)
     from oracle import oracle as O
     O.build()
-    jobs = [(ens, n, K, I_, seed, 0, r) for r in range(n_searches)]
+    jobs = [(ens, n, K, I_, seed, 0, r, FLIP_CODES[flips]) for r in range(n_searches)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
         out = pool.map(_oracle_job, jobs)
     wall = time.perf_counter() - t0
-    pairs = sum(p for _, p in out) * n * (n - 1) // 2
-    return dict(value=pairs / wall, unit=UNIT, cores=cores, kind="oracle",
+    pairs = sum(p for _, p in out)
+    return dict(value=pairs / wall, unit=unit_of(flips), cores=cores, kind="oracle",
                 sample=f"{n_searches} searches x {I_} iterations of instance 0 of {workload} "
-                       f"({pairs:.3e} pair candidates, {wall:.1f} s wall)", wall_s=wall)
+                       f"({pairs:.3e} candidates, {wall:.1f} s wall)", wall_s=wall)
 
 
 # ------------------------------------------------------------------ clocks
@@ -135,7 +151,7 @@ class Clocks:
 # ------------------------------------------------------------------ GPU arm
 def make_inputs(workload, seed):
     from paper_2010_00180_gb300 import inputs as I
-    ens, n, n_inst, K, R, I_, prec = WORKLOADS[workload]
+    ens, n, n_inst, K, R, I_, prec, _ = workload_spec(workload)
     data = []
     for k in range(n_inst):
         J, h = I.instance(ens, n, seed=seed, inst=k)
@@ -150,10 +166,10 @@ def run_ours(args, rank, world, device):
     from paper_2010_00180_gb300 import build as B, qis as Q
 
     B.build()
-    ens, n, n_inst, K, R, I_, prec = WORKLOADS[args.workload]
+    ens, n, n_inst, K, R, I_, prec, flips = workload_spec(args.workload)
     seed = args.seed + 7919 * rank                     # each rank: its own instances
     data = make_inputs(args.workload, seed)
-    ctx = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device)
+    ctx = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device, flips=flips)
     for J, h, phi in data:
         iid = ctx.create_instance(J, h)
         ctx.init_states(iid, phi)
@@ -168,7 +184,7 @@ def run_ours(args, rank, world, device):
         step()
     ctx.synchronize()
     launches0 = ctx.kernel_launches()
-    pairs0, _ = ctx.candidate_count()
+    pairs0, singles0 = ctx.candidate_count()
     evald0 = ctx.evaluated_pairs()
     for k in range(5):
         ctx.profile_query(k)                            # drop warm-up timings
@@ -190,8 +206,11 @@ def run_ours(args, rank, world, device):
     ctx.profile(False)
     prof = {name: ctx.profile_query(k) for k, name in enumerate(Q.KERNEL_CLASSES)}
     launches = ctx.kernel_launches() - launches0
-    pairs, _ = ctx.candidate_count()
+    pairs, singles = ctx.candidate_count()
     pairs -= pairs0
+    singles -= singles0
+    if flips == "single":   # the metric counts single flips when there are no pairs
+        pairs = singles
     evald = ctx.evaluated_pairs() - evald0
     t = torch.tensor([ms, float(pairs), float(evald)], dtype=torch.float64, device=f"cuda:{device}")
     if world > 1:
@@ -207,14 +226,14 @@ def run_ours(args, rank, world, device):
     # longer run from other initial states (not certified)
     tts = None
     if not args.no_tts:
-        tts = tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device)
+        tts = tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device, flips)
 
     # the plain FP64 GPU form on the same searches: same kept sets (energies on the 2^-32
     # grid are exact in both forms), so the hit rate is identical and the TTS ratio is the
     # time ratio
     forms = None
     if not args.no_forms and prec != "fp64":
-        forms = compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_max / args.steps, device)
+        forms = compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_max / args.steps, device, flips)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -233,12 +252,14 @@ def run_ours(args, rank, world, device):
             for k in range(n_inst):
                 ctx.topk_states(k, K + 1)
         e2e_s = time.perf_counter() - t0
-        e2e = dict(value=pairs / args.steps * args.e2e_steps / e2e_s * world, unit=UNIT,
+        e2e = dict(value=pairs / args.steps * args.e2e_steps / e2e_s * world, unit=unit_of(flips),
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
     clocks = clk.summary(device)
+    digits = ctx.instance_info(0)[1] if n_inst else 0
     ctx.close()
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
-                e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec)
+                e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
+                digits=digits)
 
 
 def _timed_run(ctx, stream, iters):
@@ -257,7 +278,7 @@ def _best(ctx, n_inst):
     return np.array([ctx.topk_states(k, 1)["E"][0] for k in range(n_inst)])
 
 
-def tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device):
+def tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device, flips="single_pair"):
     from paper_2010_00180_gb300 import inputs as I
     from paper_2010_00180_gb300 import qis as Q
     sweep = [I_, 2 * I_, 4 * I_, 8 * I_]
@@ -265,7 +286,7 @@ def tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device):
     for it in sweep:
         t = _timed_run(ctx, stream, it)
         runs.append((it, t, _best(ctx, n_inst)))
-    ref = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device)
+    ref = Q.Context(K=K, R=R, precision=prec, max_n=n, max_instances=n_inst, device=device, flips=flips)
     for k, (J, h, _) in enumerate(data):
         ref.create_instance(J, h)
         ref.init_states(k, I.random_states(n, R, seed=seed + 2000, inst=k))
@@ -292,10 +313,10 @@ def tts_sweep(ctx, stream, data, K, R, n, n_inst, prec, I_, seed, device):
             "batch": f"{n_inst} instances x R={R} searches run together; per-instance = batch / {n_inst}"}
 
 
-def compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_split, device):
+def compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_split, device, flips="single_pair"):
     import torch
     from paper_2010_00180_gb300 import qis as Q
-    f = Q.Context(K=K, R=R, precision="fp64", max_n=n, max_instances=n_inst, device=device)
+    f = Q.Context(K=K, R=R, precision="fp64", max_n=n, max_instances=n_inst, device=device, flips=flips)
     for k, (J, h, phi) in enumerate(data):
         f.create_instance(J, h)
         f.init_states(k, phi)
@@ -400,6 +421,24 @@ def scan_traffic():
         return None
 
 
+def roofline_fields(res, pk, src):
+    """Local-field GEMM against the measured HBM bandwidth (the dominant kernel when there is
+    no pair scan): the FP16 digit planes of every instance are read once per launch."""
+    ms, nl = res["prof"]["fields"]
+    if nl == 0 or ms <= 0:
+        return None
+    n_pad = (res["n"] + 127) // 128 * 128
+    bytes_per_launch = 2.0 * res["digits"] * n_pad * n_pad * res["n_inst"]
+    dur = ms / nl / 1e3
+    achieved = bytes_per_launch / dur / 1e9
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_fields_tc",
+            "launch_us": round(dur * 1e6, 2), "bytes_per_launch": bytes_per_launch,
+            "per_unit": "2 bytes per coupling and digit (FP16 digit planes, shared by the R searches)",
+            "peak_source": src}
+
+
 def roofline(res, pk):
     """Candidate scan (dominant kernel) against the SM issue rate."""
     ms, nl = res["prof"]["scan"]
@@ -407,6 +446,19 @@ def roofline(res, pk):
         return None
     n, n_inst, R = res["n"], res["n_inst"], res["R"]
     pairs_per_launch = res["pairs"] / max(1, nl)   # active searches only
+    if res["prec"] == "fp64":
+        # the plain FP64 form: per pair three additions, one multiplication and two compares on
+        # the FP64 pipe; GB300's nominal FP64 rate is 1.25 TFLOP/s counting an FMA as two
+        dur = ms / nl / 1e3
+        ops = 6.0 * pairs_per_launch
+        achieved = ops / dur / 1e12
+        peak = 1.25 / 2
+        return {"bound": "fp64", "achieved": round(achieved, 4), "peak": peak, "unit": "T FP64 ops/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan64",
+                "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops,
+                "per_unit": "6 FP64-pipe operations per pair candidate decided (3 adds, 1 multiply, 2 compares)",
+                "peak_source": "nominal FP64 rate (no measured FP64 peak on this pool)",
+                "note": "rows whose FP64 lower bound fails are decided without per-pair work"}
     ops_per_launch = 2.0 * pairs_per_launch       # signed add + compare per pair candidate
     dur = ms / nl / 1e3
     achieved = ops_per_launch / dur / 1e12
@@ -448,9 +500,11 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cores = os.cpu_count() or 1
-    ens, n, n_inst, K, R, I_, prec = WORKLOADS[args.workload]
+    ens, n, n_inst, K, R, I_, prec, flips = workload_spec(args.workload)
+    metric = METRIC if args.workload == DEFAULT else f"{unit_of(flips)[:-2]} decided/s ({args.workload})"
+    unit = unit_of(flips)
     config = {"workload": args.workload, "ensemble": ens, "n": n, "instances_per_gpu": n_inst, "K": K,
-              "kept": K + 1, "R": R, "iterations": I_, "precision": prec,
+              "kept": K + 1, "R": R, "iterations": I_, "precision": prec, "flips": flips,
               "l2": "inputs larger than L2 (J planes of all instances streamed every iteration)"}
 
     if args.impl == "reference":
@@ -462,13 +516,13 @@ def main():
             vals.append(oracle_sample(args.workload, ns, cores, args.seed))
         timed = vals[args.warmup:]
         v = float(np.mean([x["value"] for x in timed]))
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": float(np.mean([x["wall_s"] for x in timed])) * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": UNIT},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "cpu_baseline": {k: timed[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": unit},
+                "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
 
@@ -490,9 +544,9 @@ def main():
     if rank != 0:
         return
     pk, src = peaks()
-    rl = roofline(res, pk)
+    rl = roofline(res, pk) if flips != "single" else roofline_fields(res, pk, src)
     value = res["pairs"] / (res["ms"] / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 filter / int64 exact keys" if prec != "fp64" else "f64", "data": "synthetic",
@@ -501,8 +555,9 @@ def main():
             "tts": res["tts"], "forms": res["forms"],
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["prof"].items()},
             "evaluated_pairs_per_s": res["evald"] / (res["ms"] / 1e3),
-            "metric_note": "value = pair candidates decided exactly per second (all n(n-1)/2 pairs of every "
-                           "parent); evaluated_pairs_per_s = those tested one by one in the scan"}
+            "metric_note": "value = candidates decided exactly per second (every pair of the flip set of every "
+                           "parent: n(n-1)/2 by default); evaluated_pairs_per_s = those tested one by one in "
+                           "the scan"}
     print(json.dumps(line))
 
 

@@ -64,7 +64,23 @@ typedef struct {
   int survivor_cap;  /* per-search candidate buffer (0 = default 2048) */
   int device;        /* CUDA device ordinal */
   uint64_t seed;     /* key of the library's SplitMix64 stream for random initial states */
+  int flips;         /* flip set of every search: QIS_FLIPS_SINGLE_PAIR (0, default), QIS_FLIPS_SINGLE
+                        or QIS_FLIPS_EXCHANGE */
 } qis_config;
+
+/* Flip sets (the candidates generated from a parent):
+ *   QIS_FLIPS_SINGLE_PAIR  single flips X_i and pair flips X_i X_j (Eq. (H1), the paper's study);
+ *   QIS_FLIPS_SINGLE       single flips only (J = 1: the uniform transverse field of the
+ *                          Sec. V outlook);
+ *   QIS_FLIPS_EXCHANGE     spin exchanges only (the XX + YY interaction of the Sec. V outlook):
+ *                          pairs (i, j) with s_i != s_j, so every kept state has the initial
+ *                          state's magnetisation; a search whose sector holds fewer than K+1
+ *                          states stops once all of them are used.
+ * Candidate indices keep the default numbering (c = i, c = n + rank(i, j)); excluded candidates
+ * are skipped. */
+#define QIS_FLIPS_SINGLE_PAIR 0
+#define QIS_FLIPS_SINGLE 1
+#define QIS_FLIPS_EXCHANGE 2
 
 /* Create a context and allocate every device buffer it will use (sized by max_n,
  * max_instances, K, R). Nothing else allocates device memory afterwards. */
@@ -171,9 +187,9 @@ int qis_synchronize(qis_ctx* ctx);
 /* Launch statistics: number of kernels this context has launched so far. */
 int qis_kernel_launches(qis_ctx* ctx, uint64_t* count);
 
-/* Candidates evaluated since the context was created: pair flips X_i X_j and single flips
- * X_i of every parent (n(n-1)/2 and n per active search per iteration, Sec. III flip sets).
- * Synchronises the stream. */
+/* Candidates decided since the context was created, per expanded parent: pairs n(n-1)/2 and
+ * singles n (QIS_FLIPS_SINGLE_PAIR, the Sec. III flip sets), singles n only (QIS_FLIPS_SINGLE),
+ * pairs n_up n_down only (QIS_FLIPS_EXCHANGE). Synchronises the stream. */
 int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles);
 
 /* Launch shapes of the iteration. None of them changes any result (the candidate sets, the

@@ -148,12 +148,17 @@ int count_candidates(qis_ctx* ctx, uint64_t c[2]) {
   if (ctx->P.B == 0) return 0;
   std::vector<int> np(ctx->P.B);
   CK(cudaMemcpy(np.data(), ctx->P.nprod, sizeof(int) * np.size(), cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> pp(ctx->P.B);
+  CK(cudaMemcpy(pp.data(), ctx->P.npair, sizeof(unsigned long long) * pp.size(), cudaMemcpyDeviceToHost));
   for (size_t id = 0; id < ctx->inst.size(); ++id) {
     const uint64_t n = (uint64_t)ctx->inst[id].n;
     uint64_t it = 0;
-    for (int r = 0; r < ctx->R; ++r) it += (uint64_t)np[(size_t)ctx->inst[id].first_search + r];
-    c[0] += it * (n * (n - 1) / 2);
-    c[1] += it * n;
+    for (int r = 0; r < ctx->R; ++r) {
+      const size_t b = (size_t)ctx->inst[id].first_search + r;
+      it += (uint64_t)np[b];
+      c[0] += pp[b];
+    }
+    if (ctx->cfg.flips != QIS_FLIPS_EXCHANGE) c[1] += it * n;
   }
   return 0;
 }
@@ -195,8 +200,13 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   LAUNCH(launch_bound(P, s));
   CK(prof_end(ctx, 2));
   CK(prof_begin(ctx, 3));
-  if (ctx->mode == QIS_FP64) LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
-  else LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R, s));
+  if (ctx->cfg.flips == QIS_FLIPS_SINGLE) {
+    // no pair candidates: nothing to scan
+  } else if (ctx->mode == QIS_FP64) {
+    LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
+  } else {
+    LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R, s));
+  }
   CK(prof_end(ctx, 3));
   CK(prof_begin(ctx, 4));
   LAUNCH(launch_merge(P, s));
@@ -256,6 +266,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   if (cfg->max_instances < 1) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_instances must be >= 1");
   if (cfg->precision != QIS_FP64 && cfg->precision != QIS_SPLIT_BF16 && cfg->precision != QIS_PM1_FP8)
     return fail(nullptr, QIS_ERR_INVALID_ARG, "unknown precision mode");
+  if (cfg->flips < QIS_FLIPS_SINGLE_PAIR || cfg->flips > QIS_FLIPS_EXCHANGE)
+    return fail(nullptr, QIS_ERR_INVALID_ARG, "unknown flip set");
   int cap = cfg->survivor_cap ? cfg->survivor_cap : 2048;
   if (cap < 4 * (cfg->K + 1) + 64 || cap > 16384)
     return fail(nullptr, QIS_ERR_INVALID_ARG, "survivor_cap must be in [4(K+1)+64, 16384]");
@@ -318,6 +330,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     P.mode = ctx->mode;
     P.B = 0;
     P.NP = ctx->NP;
+    P.flips = ctx->cfg.flips;
     P.J64 = ctx->J64;
     P.Jq = ctx->Jq;
     P.J4 = ctx->J4;
@@ -365,6 +378,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.init_q, B);
     ALLOC(P.status, 4);
     ALLOC(P.nprod, B);
+    ALLOC(P.npair, B);
     ALLOC(P.eval_cnt, 64);
     ALLOC(P.mrg_ref, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_src, (size_t)ctx->max_inst * K1);
@@ -500,6 +514,7 @@ int qis_clear_instances(qis_ctx* ctx) {
     ctx->cand_acc[0] += c[0];
     ctx->cand_acc[1] += c[1];
     if (ctx->P.B > 0) CK(cudaMemset(ctx->P.nprod, 0, sizeof(int) * (size_t)ctx->P.B));
+    if (ctx->P.B > 0) CK(cudaMemset(ctx->P.npair, 0, sizeof(unsigned long long) * (size_t)ctx->P.B));
   }
   ctx->inst.clear();
   ctx->inst_ready.clear();
@@ -619,7 +634,7 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
     }
     for (int it = 0; it < n_iters; ++it) {
       CK(cudaGraphLaunch(ctx->graph_exec, s));
-      ctx->launches += 5;
+      ctx->launches += (ctx->cfg.flips == QIS_FLIPS_SINGLE) ? 4 : 5;   // kernels in the graph
     }
   } else {
     for (int it = 0; it < n_iters; ++it) {
@@ -776,7 +791,7 @@ int qis_set_search_list(qis_ctx* ctx, int instance_id, int r, int count, const u
 }
 
 // ---------------------------------------------------------------- checkpoint / resume
-// File layout (little endian): "QISCKPT1", int32 {version, K, R, precision, n_instances, 0},
+// File layout (little endian): "QISCKPT1", int32 {version, K, R, precision, n_instances, flips},
 // uint64 seed; per instance: int32 {n, ready}, J (n*n FP64 row major), h (n FP64), the R
 // initial states (R*W uint64); per search of the instance: int32 {count, t, active, 0}, then
 // count entries {W uint64 bits, FP64 E, uint64 stamp, uint64 used}; last, the FNV-1a 64-bit
@@ -831,7 +846,7 @@ int qis_save(qis_ctx* ctx, const char* path) {
   if (!f) return fail(ctx, QIS_ERR_INVALID_ARG, std::string("cannot open ") + path + " for writing");
   Writer w{f};
   const int K1 = ctx->K1, Wm = ctx->Wmax, R = ctx->R;
-  const int hdr[6] = {kCkptVersion, ctx->cfg.K, R, ctx->mode, (int)ctx->inst.size(), 0};
+  const int hdr[6] = {kCkptVersion, ctx->cfg.K, R, ctx->mode, (int)ctx->inst.size(), ctx->cfg.flips};
   w.put(kCkptMagic, 8);
   w.put(hdr, sizeof(hdr));
   w.put(&ctx->cfg.seed, 8);
@@ -926,8 +941,8 @@ int qis_load(qis_ctx* ctx, const char* path) {
   rd.get(&seed, 8);
   if (memcmp(magic, kCkptMagic, 8) != 0) return corrupt("not a checkpoint");
   if (hdr[0] != kCkptVersion) return corrupt("unsupported version");
-  if (hdr[1] != ctx->cfg.K || hdr[2] != ctx->R || hdr[3] != ctx->mode)
-    return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint K, R or precision differ from the context's");
+  if (hdr[1] != ctx->cfg.K || hdr[2] != ctx->R || hdr[3] != ctx->mode || hdr[5] != ctx->cfg.flips)
+    return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint K, R, precision or flip set differ from the context's");
   const int n_inst = hdr[4], R = ctx->R;
   if (n_inst < 0 || n_inst > ctx->max_inst) return fail(ctx, QIS_ERR_INVALID_ARG, "checkpoint has too many instances");
   const size_t end = rd.data.size() - 8;

@@ -42,6 +42,7 @@ struct DevPtrs {
   const InstDesc* inst;
   int n_inst, R, K1, Wmax, cap, mode, B;
   int NP;                 // row stride of per-search site arrays (max n_pad)
+  int flips;              // QIS_FLIPS_*: the candidate set
   // instance pools
   const double* J64;      // [off_mat + i*n_pad + j]
   const long long* Jq;    // fixed-point couplings
@@ -87,6 +88,7 @@ struct DevPtrs {
   long long* init_q;      // [b] the same, exact E 2^q (split modes)
   int* status;            // [0] error bits
   int* nprod;             // [b] productive iterations (a parent was expanded) of search b
+  unsigned long long* npair;  // [b] pair candidates of the expanded parents of search b
   unsigned long long* eval_cnt;  // [64] pair terms the FP32 scan evaluated (live rows x chunk width)
   // final merge (Alg. 4) per instance
   int* mrg_ref;           // [inst][K1] search*K1 + slot

@@ -57,7 +57,19 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
     }
   }
   if (sel >= 0) {
-    for (int w = lane; w < d.W; w += 32) P.par_bits[(long long)b * P.Wmax + w] = P.lst_bits[(base + sel) * P.Wmax + w];
+    int down = 0;   // spins -1 of the parent (sigma = 1)
+    for (int w = lane; w < d.W; w += 32) {
+      const uint64_t x = P.lst_bits[(base + sel) * P.Wmax + w];
+      P.par_bits[(long long)b * P.Wmax + w] = x;
+      down += __popcll(x);
+    }
+    for (int o = 16; o > 0; o >>= 1) down += __shfl_xor_sync(0xffffffffu, down, o);
+    if (lane == 0) {   // pair candidates of this parent for the flip set
+      const unsigned long long nn = (unsigned long long)d.n;
+      P.npair[b] += (P.flips == QIS_FLIPS_SINGLE)     ? 0ull
+                    : (P.flips == QIS_FLIPS_EXCHANGE) ? (unsigned long long)down * (nn - (unsigned long long)down)
+                                                      : nn * (nn - 1) / 2;
+    }
     if (P.mode != QIS_FP64) {
       const uint64_t* src = P.lst_bits + (base + sel) * P.Wmax;
       __half* dst = P.S16 + (long long)(b / P.R) * P.s16_stride;
@@ -195,13 +207,14 @@ __device__ void block_min_max(float& lo, float& hi) {
   __syncthreads();
 }
 
-// An upper bound of the rank-th smallest (0-based) of cnt finite values in shared memory,
-// tight to one of 256 equal-width bins of their range: the largest value whose bin is at most
-// the bin holding that element (binning is monotone, so at least rank + 1 values lie in those
-// bins). Two passes over the values instead of the four of a radix select. Every thread of
-// the block calls it.
-// lo, hi: this thread's minimum and maximum of the values (the caller tracks them while writing
-// the values; the block-wide range is reduced here).
+// An upper bound of the rank-th smallest (0-based) of cnt values in shared memory, tight to one
+// of 256 equal-width bins of the range of the finite ones: the largest value whose bin is at
+// most the bin holding that element (binning is monotone, so at least rank + 1 values lie in
+// those bins). +inf values (excluded candidates) go to the last bin, so the bound is +inf when
+// fewer than rank + 1 values are finite. Two passes over the values instead of the four of a
+// radix select. Every thread of the block calls it.
+// lo, hi: this thread's minimum and maximum of the finite values (the caller tracks them while
+// writing the values; the block-wide range is reduced here).
 __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist, float lo, float hi) {
   __shared__ int s_b;
   for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
@@ -212,7 +225,8 @@ __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist
     const bool in = t < cnt;
     const unsigned act = __ballot_sync(0xffffffffu, in);
     if (in) {
-      const int bin = min(255, (int)((v[t] - lo) * scale));
+      const float x = v[t];
+      const int bin = (x <= hi) ? min(255, (int)((x - lo) * scale)) : 255;   // +inf (excluded): last bin
       const unsigned peers = __match_any_sync(act, bin);
       if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
     }
@@ -226,8 +240,10 @@ __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist
   __syncthreads();
   const int bsel = s_b;
   float mx = -INFINITY, dummy = INFINITY;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x)
-    if (min(255, (int)((v[t] - lo) * scale)) <= bsel) mx = fmaxf(mx, v[t]);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const float x = v[t];
+    if (((x <= hi) ? min(255, (int)((x - lo) * scale)) : 255) <= bsel) mx = fmaxf(mx, x);
+  }
   block_min_max(dummy, mx);
   return mx;
 }
@@ -250,9 +266,9 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   const int n = d.n;
   const bool fp64 = P.mode == QIS_FP64;
   extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
-  __shared__ int hist[256];
+  __shared__ int hist[256], hist2[256];
   __shared__ int sites[kSubSites];
-  __shared__ int s_nsites, s_bin, s_near;
+  __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near;
   __shared__ float s_amin, s_amax;
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ float s_thr;
@@ -265,7 +281,6 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     T = fp64 ? dkey_inv(kT) : (double)(long long)(kT ^ (1ull << 63)) * d.inv_scale;
   }
   const double Ep = P.par_E[b];
-  const long long C = (long long)n * (n + 1) / 2;
   const double* a64 = P.a64 + (long long)b * P.NP;
   // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory
   float2* as = reinterpret_cast<float2*>(subkey + kSubMax);   // [NP]
@@ -279,6 +294,7 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     s_amin = INFINITY;
     s_amax = -INFINITY;
     s_nsites = 0;
+    s_n2 = 0;
     s_near = 0;
   }
   __syncthreads();
@@ -362,44 +378,103 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   const int k = P.K1 + s_near;
   const float amin = s_amin, amax = s_amax;
   double U = INFINITY;
+  // candidates of the flip set: n singles; nu nd exchanges (nu up, nd = n - nu down spins);
+  // or n singles and n(n-1)/2 pairs
+  const int fl = P.flips;
+  const bool ex = fl == QIS_FLIPS_EXCHANGE;
+  int nu = 0;
+  for (int w = 0; w < d.W; ++w) nu += __popcll(pb[w]);   // bits above n are zero
+  const long long C = fl == QIS_FLIPS_SINGLE ? (long long)n
+                      : ex ? (long long)nu * (n - nu) : (long long)n * (n + 1) / 2;
   if (C > k && k <= kSubMax) {
-    // m lowest sites with m + m(m-1)/2 >= min(3k, kSubMax): found with a 256-bin histogram of a
+    // a subset of the candidates with at least min(3k, kSubMax) members, built from low-a
+    // sites found with a 256-bin histogram of a (one histogram per spin for exchanges):
+    //   singles and pairs: the m lowest sites, m + m(m-1)/2 >= want, m <= kSubSites;
+    //   singles only: the sites up to the bin of the k-th lowest (their a_i, <= kSubMax);
+    //   exchanges: the mu lowest up and md lowest down sites, mu md >= want, every up-down
+    //   pair (all of them in the flip set), mu + md <= kSubSites.
+    // Any subset gives an upper bound of the k-th lowest candidate energy.
     const int want = min(3 * k, kSubMax);
-    int m = 1;
-    while (m < n && m + m * (m - 1) / 2 < want) ++m;
+    int t0 = 0, t1 = 0;
+    if (fl == QIS_FLIPS_SINGLE) {
+      t0 = k;
+    } else if (ex) {
+      const int nd = n - nu;   // nu, nd >= 1: C > k >= 1
+      int m0 = 1;
+      while (m0 * m0 < want) ++m0;
+      int mu = min(nu, m0);
+      int md = min(nd, (want + mu - 1) / mu);
+      mu = min(nu, (want + md - 1) / md);
+      if (mu + md > kSubSites) {
+        if (mu <= kSubSites / 2) md = kSubSites - mu;
+        else if (md <= kSubSites / 2) mu = kSubSites - md;
+        else mu = md = kSubSites / 2;
+      }
+      t0 = mu;
+      t1 = md;
+    } else {
+      int m = 1;
+      while (m < n && m + m * (m - 1) / 2 < want) ++m;
+      t0 = min(m, kSubSites);
+    }
+    const int lim0 = ex ? kSubSites - t1 : kSubSites;   // site slots of the first class
     const float span = fmaxf(amax - amin, 1e-30f);
     const float scale = 255.99f / span;
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    auto bin_of = [&](int i) {
       const float a = fp64 ? (float)a64[i] : as[i].x;
-      atomicAdd(&hist[min(255, (int)((a - amin) * scale))], 1);
+      return min(255, (int)((a - amin) * scale));
+    };
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+      hist[t] = 0;
+      hist2[t] = 0;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      atomicAdd(&((ex && sigma_of(pb, i)) ? hist2 : hist)[bin_of(i)], 1);
     __syncthreads();
     if (threadIdx.x < 32) {
       int bin, within;
-      find_bin(hist, min(m, n) - 1, bin, within);   // bin of the m-th lowest a_i
+      find_bin(hist, t0 - 1, bin, within);   // bin of the t0-th lowest a_i (of its class)
       if (threadIdx.x == 0) s_bin = bin;
-    }
-    __syncthreads();
-    const int bin = s_bin;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float a = fp64 ? (float)a64[i] : as[i].x;
-      if (min(255, (int)((a - amin) * scale)) <= bin) {
-        const int slot = atomicAdd(&s_nsites, 1);
-        if (slot < kSubSites) sites[slot] = i;
+      if (ex) {
+        find_bin(hist2, t1 - 1, bin, within);
+        if (threadIdx.x == 0) s_bin2 = bin;
       }
     }
     __syncthreads();
-    const int mm = min(s_nsites, kSubSites);
-    const int M = mm + mm * (mm - 1) / 2;
+    // collect the sites (singles only: their candidate energies, in the scan's arithmetic,
+    // with their range per thread)
+    float vlo = INFINITY, vhi = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int c = ex ? sigma_of(pb, i) : 0;
+      if (bin_of(i) > (c ? s_bin2 : s_bin)) continue;
+      const int slot = atomicAdd(c ? &s_n2 : &s_nsites, 1);
+      if (fl == QIS_FLIPS_SINGLE) {
+        if (slot < kSubMax) {
+          if (fp64) {
+            subkey[slot] = dkey(__dadd_rn(Ep, a64[i]));
+          } else {
+            const float de = as[i].x;
+            vlo = fminf(vlo, de);
+            vhi = fmaxf(vhi, de);
+            reinterpret_cast<float*>(subkey)[slot] = de;
+          }
+        }
+      } else if (slot < (c ? t1 : lim0)) {
+        sites[c ? lim0 + slot : slot] = i;
+      }
+    }
+    __syncthreads();
+    const int mm = min(s_nsites, lim0), m2 = min(s_n2, t1);
+    const int M = fl == QIS_FLIPS_SINGLE ? min(s_nsites, kSubMax) : ex ? mm * m2 : mm + mm * (mm - 1) / 2;
     if (M >= k) {
-      // subset candidate energies, in the scan's arithmetic (with their range per thread)
-      float vlo = INFINITY, vhi = -INFINITY;
 #pragma unroll 2
-      for (int t = threadIdx.x; t < M; t += blockDim.x) {
+      for (int t = threadIdx.x; t < M && fl != QIS_FLIPS_SINGLE; t += blockDim.x) {
         int i, j = -1;
-        if (t < mm) {
+        if (ex) {
+          i = sites[t / m2];
+          j = sites[lim0 + t % m2];
+        } else if (t < mm) {
           i = sites[t];
         } else {
           // pair rank r -> (x, y), x < y < mm: row x starts at x mm - x(x+1)/2 (closed form,
@@ -413,8 +488,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
           const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
           i = sites[x];
           j = sites[y];
-          if (i > j) { const int tmp = i; i = j; j = tmp; }
         }
+        if (j >= 0 && i > j) { const int tmp = i; i = j; j = tmp; }
         if (fp64) {
           double de = a64[i];
           if (j >= 0) de = dE64(a64[i], a64[j], P.J64[d.off_mat + (long long)i * d.n_pad + j],
@@ -427,9 +502,9 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
             const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
             de = as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x);
           }
-          reinterpret_cast<float*>(subkey)[t] = de;
           vlo = fminf(vlo, de);
           vhi = fmaxf(vhi, de);
+          reinterpret_cast<float*>(subkey)[t] = de;
         }
       }
       __syncthreads();
@@ -460,8 +535,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     }
   }
   __syncthreads();
-  // single flips: dE_i = a_i
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  // single flips: dE_i = a_i (not candidates under exchanges)
+  for (int i = threadIdx.x; i < n && P.flips != QIS_FLIPS_EXCHANGE; i += blockDim.x) {
     bool ok;
     if (fp64) {
       const double e = __dadd_rn(Ep, a64[i]);
@@ -530,6 +605,7 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
         const int j = j0 + tx * 4 + c;
         if (j <= i || j >= n) continue;
         const int flip = ((rs >> r) ^ (cs >> c)) & 1;
+        if (!flip && P.flips == QIS_FLIPS_EXCHANGE) continue;   // exchanges need s_i != s_j
         const double e = __dadd_rn(Ep, dE64(ai, ac_s[tx * 4 + c], Jt[ty * 4 + r][tx * 4 + c], flip));
         if (e < T && e <= cap) {
           const int slot = atomicAdd(P.surv_cnt + b, 1);

@@ -69,7 +69,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 constexpr int kRing = 2;                      // staging ring depth (power of two)
-constexpr int kPer = 8;                       // searches per ring slot
+constexpr int kPer = 8;                       // searches per ring slot (two liveness ballots)
 constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
 
 // Staging ring of one block: slot u % kRing holds searches kPer u .. kPer u + kPer - 1. full[q]
@@ -84,7 +84,10 @@ struct __align__(128) ScanRing {
   int err;
 };
 
-template <int NC>
+// EX: spin exchanges only (the pair (i, j) is a candidate only when s_i != s_j): the column
+// values are kept twice, as a_j where s_j = -1 (partners of rows with s_i = +1) and as a_j where
+// s_j = +1 (rows with s_i = -1), NaN elsewhere, so same-spin pairs never pass.
+template <int NC, bool EX>
 __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, int row0, int c0, int g, int RG,
                                           ScanRing& sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -99,27 +102,34 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
   // All sources are 16-byte aligned: NP is a multiple of 128, c0 and row0 of 32.
   const int cols = min(32 * NC, NPs - c0);
   const int nslots = (R + kPer - 1) / kPer;
-  auto stage = [&](int u, int q) {   // one thread: the searches of slot iteration u
+  // one warp stages slot iteration u into slot q: lane 0 posts the byte count on the slot's
+  // barrier, then lane p issues the three copies of search p
+  auto stage = [&](int u, int q) {
     const int ns = min(kPer, R - u * kPer);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // order the warps' reads first
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.full[q])),
-                 "r"((uint32_t)(ns * (cols * 8 + 32 * 8 + 16))) : "memory");
-    for (int p = 0; p < ns; ++p) {
-      const long long b = b0 + u * kPer + p;
-      bulk_g2s(&sm.col[q][p][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
-      bulk_g2s(&sm.row[q][p][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
-      bulk_g2s(&sm.ctl[q][p], P.sctl + b, 16, &sm.full[q]);
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&sm.full[q])),
+                   "r"((uint32_t)(ns * (cols * 8 + 32 * 8 + 16))) : "memory");
+    __syncwarp();
+    if (lane < ns) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the warps' reads first
+      const long long b = b0 + u * kPer + lane;
+      bulk_g2s(&sm.col[q][lane][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
+      bulk_g2s(&sm.row[q][lane][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
+      bulk_g2s(&sm.ctl[q][lane], P.sctl + b, 16, &sm.full[q]);
     }
-    sm.issued[q] += 1;
+    if (lane == 0) sm.issued[q] += 1;
   };
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < kRing; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[q])));
-      sm.rel[q] = 0;
-      sm.issued[q] = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int q = 0; q < kRing; ++q) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[q])));
+        sm.rel[q] = 0;
+        sm.issued[q] = 0;
+      }
+      sm.err = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    sm.err = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
     for (int u = 0; u < min(kRing, nslots); ++u) stage(u, u);
   }
   __syncthreads();
@@ -153,36 +163,53 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       }
       break;
     }
+    // the slot's rows that can hit, four searches per ballot: lane l takes search 4h + (l >> 3)
+    // and row i0 + (l & 7). y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding
+    // is monotone), so a row with c_i = fl32(thr - a_i) below it has no pair under its bound
     const int ns = min(kPer, R - u * kPer);
-    for (int p = 0; p < ns; ++p) {
+    unsigned long long live64 = 0, neg64 = 0;   // bit 8p + r: row r of search p live / s_i = -1
+    float cv[kPer / 4];
+#pragma unroll
+    for (int h = 0; h < kPer / 4; ++h) {
+      const int p = 4 * h + (lane >> 3);
+      const float4 ctl = sm.ctl[q][p];   // slots past ns hold stale values: masked below
+      const float2 rv = sm.row[q][p][warp * 8 + (lane & 7)];
+      cv[h] = __fsub_rn(ctl.x, rv.x);
+      live64 |= (unsigned long long)__ballot_sync(0xffffffffu, p < ns && ctl.y != 0.f && cv[h] >= ctl.z)
+                << (32 * h);
+      neg64 |= (unsigned long long)__ballot_sync(0xffffffffu, rv.y < 0.f) << (32 * h);
+    }
+    nlive += __popcll(live64);
+    while (live64) {   // searches with a live row (uniform)
+      const int p = (__ffsll((long long)live64) - 1) >> 3;
+      const unsigned live = (unsigned)(live64 >> (8 * p)) & 0xffu;
+      const unsigned smask = (unsigned)(neg64 >> (8 * p)) & 0xffu;
+      live64 &= ~(0xffull << (8 * p));
       const int s = u * kPer + p;
-      const float4 ctl = sm.ctl[q][p];
-      // rows that can hit: y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding is
-      // monotone), so a row with c_i below it has no pair under its bound
-      float2 rv = sm.row[q][p][warp * 8 + (lane & 7)];
-      rv.x = __fsub_rn(ctl.x, rv.x);   // c_i = fl32(thr - a_i)
-      const unsigned live = __ballot_sync(0xffffffffu, ctl.y != 0.f && rv.x >= ctl.z) & 0xffu;
-      float aj[NC], sj[NC];
-      nlive += __popc(live);
-      if (live) {
+      const float cp = (p >> 2) ? cv[1] : cv[0];
+      float aj[NC], sj[NC], am[EX ? NC : 1];
+      {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           const float2 v = sm.col[q][p][32 * k + lane];
           aj[k] = v.x;
           sj[k] = v.y;
+          if constexpr (EX) {
+            aj[k] = (v.y < 0.f) ? v.x : qnan;   // partners of rows with s_i = +1
+            am[k] = (v.y > 0.f) ? v.x : qnan;   // partners of rows with s_i = -1
+          }
         }
       }
-      if (live) {   // vote result: uniform branch
-        const unsigned smask = __ballot_sync(0xffffffffu, rv.y < 0.f) & 0xffu;   // bit r: s_i = -1
+      {
         unsigned long long cm = 0;   // exact hits of this lane: bit r NC + k = (row i0 + r, column k)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           if (!((live >> r) & 1u)) continue;   // uniform
-          const float c = __shfl_sync(0xffffffffu, rv.x, r);
+          const float c = __shfl_sync(0xffffffffu, cp, (p & 3) * 8 + r);
           float y[NC];
           if ((smask >> r) & 1u) {
 #pragma unroll
-            for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], aj[k]);
+            for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], EX ? am[EX ? k : 0] : aj[k]);
           } else {
 #pragma unroll
             for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
@@ -206,11 +233,13 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       }
     }   // searches of the slot
     __syncwarp();
-    if (lane == 0) {   // release the slot; the last of the four warps refills it
+    int last = 0;   // release the slot; the last of the four warps refills it
+    if (lane == 0) {
       __threadfence_block();   // this warp's reads of the slot precede the release
-      const int old = atomicAdd(&sm.rel[q], 1);
-      if ((old & 3) == 3 && u + kRing < nslots) stage(u + kRing, q);
+      last = (atomicAdd(&sm.rel[q], 1) & 3) == 3;
+      if (last) __threadfence_block();   // and every other warp's precede the refill
     }
+    if (__shfl_sync(0xffffffffu, last, 0) && u + kRing < nslots) stage(u + kRing, q);
   }
   if (lane == 0 && nlive) atomicAdd(P.eval_cnt + (blockIdx.x & 63), (unsigned long long)nlive * (32 * NC));
   // after an error, wait (bounded) for every copy the block issued before its shared memory
@@ -229,26 +258,28 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
 
 // task.x = instance, task.y = first row of the 32-row block, task.z = first column,
 // task.w = NC | (search group << 8); a group is RG consecutive searches of the instance
-__global__ void __launch_bounds__(128, 5) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
+template <bool EX>
+__global__ void __launch_bounds__(128, EX ? 4 : 5) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
   __shared__ ScanRing sm;
   const int4 w = tasks[blockIdx.x];
   const InstDesc d = P.inst[w.x];
   const int g = w.w >> 8;
   switch (w.w & 0xff) {
-    case 8: scan_task<8>(P, d, w.y, w.z, g, RG, sm); break;
-    case 7: scan_task<7>(P, d, w.y, w.z, g, RG, sm); break;
-    case 6: scan_task<6>(P, d, w.y, w.z, g, RG, sm); break;
-    case 5: scan_task<5>(P, d, w.y, w.z, g, RG, sm); break;
-    case 4: scan_task<4>(P, d, w.y, w.z, g, RG, sm); break;
-    case 3: scan_task<3>(P, d, w.y, w.z, g, RG, sm); break;
-    case 2: scan_task<2>(P, d, w.y, w.z, g, RG, sm); break;
-    default: scan_task<1>(P, d, w.y, w.z, g, RG, sm); break;
+    case 8: scan_task<8, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 7: scan_task<7, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 6: scan_task<6, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 5: scan_task<5, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 4: scan_task<4, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 3: scan_task<3, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    case 2: scan_task<2, EX>(P, d, w.y, w.z, g, RG, sm); break;
+    default: scan_task<1, EX>(P, d, w.y, w.z, g, RG, sm); break;
   }
 }
 
 cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, int RG, cudaStream_t s) {
   if (n_tasks <= 0) return cudaSuccess;
-  k_scan_pairs<<<n_tasks, 128, 0, s>>>(P, tasks, n_tasks, RG);
+  if (P.flips == QIS_FLIPS_EXCHANGE) k_scan_pairs<true><<<n_tasks, 128, 0, s>>>(P, tasks, n_tasks, RG);
+  else k_scan_pairs<false><<<n_tasks, 128, 0, s>>>(P, tasks, n_tasks, RG);
   return cudaGetLastError();
 }
 

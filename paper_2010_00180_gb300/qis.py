@@ -51,7 +51,10 @@ class Tuning(C.Structure):
 class Config(C.Structure):
     _fields_ = [("K", C.c_int), ("R", C.c_int), ("precision", C.c_int), ("max_n", C.c_int),
                 ("max_instances", C.c_int), ("survivor_cap", C.c_int), ("device", C.c_int),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("flips", C.c_int)]
+
+
+FLIPS = {"single_pair": 0, "single": 1, "exchange": 2}
 
 
 _lib = None
@@ -140,10 +143,13 @@ class Context:
     """One qis_ctx: instances, R searches per instance, kept lists of K+1 states."""
 
     def __init__(self, K: int, R: int, precision="split_bf16", max_n: int = 1024, max_instances: int = 1,
-                 survivor_cap: int = 0, device: int = 0, seed: int = 0):
+                 survivor_cap: int = 0, device: int = 0, seed: int = 0, flips="single_pair"):
+        """flips: the candidate set -- "single_pair" (single and pair flips, the default),
+        "single" (single flips only) or "exchange" (spin exchanges, magnetisation conserving)."""
         self.lib = load()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        self.cfg = Config(K, R, prec, max_n, max_instances, survivor_cap, device, seed & 0xFFFFFFFFFFFFFFFF)
+        fl = FLIPS[flips] if isinstance(flips, str) else int(flips)
+        self.cfg = Config(K, R, prec, max_n, max_instances, survivor_cap, device, seed & 0xFFFFFFFFFFFFFFFF, fl)
         self.K, self.R = K, R
         self.h = C.c_void_p()
         rc = self.lib.qis_create(C.byref(self.cfg), C.byref(self.h))

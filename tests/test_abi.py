@@ -37,8 +37,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_config_struct_layout(lib):
-    assert C.sizeof(qis.Config) == 40
+    assert C.sizeof(qis.Config) == 48
     assert qis.Config.seed.offset == 32
+    assert qis.Config.flips.offset == 40
 
 
 def test_create_rejects_bad_config(lib):
@@ -48,6 +49,9 @@ def test_create_rejects_bad_config(lib):
     assert b"K" in lib.qis_last_error(None)
     cfg = qis.Config(8, 4, 7, 16, 1, 0, 0, 0)            # unknown precision
     assert lib.qis_create(C.byref(cfg), C.byref(h)) == -1
+    cfg = qis.Config(8, 4, 1, 16, 1, 0, 0, 0, 3)         # unknown flip set
+    assert lib.qis_create(C.byref(cfg), C.byref(h)) == -1
+    assert b"flip" in lib.qis_last_error(None)
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
