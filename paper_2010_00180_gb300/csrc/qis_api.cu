@@ -365,7 +365,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     }
     ALLOC(P.thr32, B);
     if (ctx->mode != QIS_FP64) {
-      ALLOC(P.sctl, B);
+      ALLOC(P.sctl, B * (size_t)(NP / 32));
     }
     ALLOC(P.thrE, B);
     ALLOC(P.capE, B);

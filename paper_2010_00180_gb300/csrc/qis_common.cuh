@@ -72,14 +72,14 @@ struct DevPtrs {
   float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
-  float4* sctl;           // [b] {thr, active, 0, 0}: staged by the scan with the row data
+  float4* sctl;           // [b][NP/32] scan control word per 32-column group (k_bound)
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
   double* amin64;         // [b] FP64 mode: min_i a_i of the parent (the scan's row bound)
   int* surv_cnt;          // [b]
   uint32_t* dup_c;        // [b][K1] candidate index of every kept state one or two flips from the parent
   int* dup_n;             // [b] their number
-  unsigned long long* surv;  // [b][cap] survivor entries {c, i, j} (surv_entry)
+  unsigned long long* surv;  // [b][cap] survivor entries {i, j} (surv_entry; c filled by the merge)
   __half* S16;            // +-1 spins of the parents (0 past n), tensor-core operand, tiled (s16_offset)
   long long s16_stride;   // halves of one instance's region of S16
   int gemm_nt;            // searches per tensor-core tile (the S16 tiling)
@@ -120,17 +120,21 @@ __host__ __device__ inline int pad_of(int n) { return (n + kPad - 1) / kPad * kP
 __host__ __device__ inline uint32_t pair_index(int n, int i, int j) {
   return (uint32_t)n + (uint32_t)((long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1));
 }
-// Survivor entry written by the candidate filters (singles by k_bound, pairs by the scans):
-// bits 0-31 candidate index c, bits 32-43 site i, bits 44-55 site j, bit 56 set for a single
-// flip (no j). n <= 4096 keeps i and j in 12 bits.
-__host__ __device__ inline unsigned long long surv_entry(uint32_t c, int i, int j) {
-  return (unsigned long long)c | ((unsigned long long)(unsigned)i << 32) |
+// Survivor entry: bits 32-43 site i, bits 44-55 site j, bit 56 set for a single flip (no j);
+// n <= 4096 keeps i and j in 12 bits. The candidate filters (singles by k_bound, pairs by the
+// scans) write the sites only; the merge fills bits 0-31 with the candidate index c (the
+// tie-break of equal energies) when it reads the entry.
+__host__ __device__ inline unsigned long long surv_entry(int i, int j) {
+  return ((unsigned long long)(unsigned)i << 32) |
          (j < 0 ? (1ull << 56) : ((unsigned long long)(unsigned)j << 44));
+}
+__host__ __device__ inline void surv_sites(unsigned long long e, int& i, int& j) {
+  i = (int)((e >> 32) & 0xfffu);
+  j = ((e >> 56) & 1u) ? -1 : (int)((e >> 44) & 0xfffu);
 }
 __host__ __device__ inline void surv_decode(unsigned long long e, uint32_t& c, int& i, int& j) {
   c = (uint32_t)e;
-  i = (int)((e >> 32) & 0xfffu);
-  j = ((e >> 56) & 1u) ? -1 : (int)((e >> 44) & 0xfffu);
+  surv_sites(e, i, j);
 }
 
 __device__ inline void decode_candidate(int n, uint32_t c, int& i, int& j) {

@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   if (!P.active[b]) {
     if (threadIdx.x == 0) {
       P.surv_cnt[b] = 0;
-      if (P.mode != QIS_FP64) P.sctl[b] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
     }
+    if (P.mode != QIS_FP64)
+      for (int g = threadIdx.x; g < P.NP / 32; g += blockDim.x)
+        P.sctl[(long long)b * (P.NP / 32) + g] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
     return;
   }
   const InstDesc d = P.inst[b / P.R];
@@ -268,6 +270,7 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
   __shared__ int hist[256], hist2[256];
   __shared__ int sites[kSubSites];
+  __shared__ float gmin[kMaxN / 32];   // min a_j of each 32-column group
   __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near;
   __shared__ float s_amin, s_amax;
   __shared__ uint64_t pb[kMaxN / 64];
@@ -529,12 +532,30 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
       const double t2 = U + 2.0 * delta;
       s_thr = fl32_up(fmin(t1, t2));
       P.thr32[b] = s_thr;
-      // lower bound of every pair term y_ij = fl(a_j +- 4J~_ij) of the scan (|4J~| <= j4max,
-      // rounding monotone): rows with c_i below it are skipped
-      P.sctl[b] = make_float4(s_thr, 1.f, __fsub_rd(amin, d.j4max), 0.f);
     }
   }
   __syncthreads();
+  if (!fp64) {
+    // the scan's control word of every 32-column group g: {thr, active, RD(min_j a_j - j4max),
+    // min of a_j over the groups g .. g+7 (columns < n)}. A scan chunk of at most 8 groups
+    // starting at g bounds every pair term y_ij = fl(a_j +- 4J~_ij) of row i from below by
+    // RD(w - max_j |4J~_ij|) (rounding is monotone), and skips rows with c_i below it.
+    const int G = P.NP / 32, lane = threadIdx.x & 31;
+    for (int g = threadIdx.x >> 5; g < G; g += blockDim.x >> 5) {
+      const int j = 32 * g + lane;
+      float v = (j < n) ? as[j].x : INFINITY;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) gmin[g] = v;
+    }
+    __syncthreads();
+    const float L = __fsub_rd(amin, d.j4max);
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+      float w = gmin[g];
+      for (int x = g + 1; x < min(g + 8, G); ++x) w = fminf(w, gmin[x]);
+      P.sctl[(long long)b * G + g] = make_float4(s_thr, 1.f, L, w);
+    }
+  }
   // single flips: dE_i = a_i (not candidates under exchanges)
   for (int i = threadIdx.x; i < n && P.flips != QIS_FLIPS_EXCHANGE; i += blockDim.x) {
     bool ok;
@@ -546,7 +567,7 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     }
     if (ok) {
       const int slot = atomicAdd(P.surv_cnt + b, 1);
-      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry((uint32_t)i, i, -1);
+      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, -1);
     }
   }
 }
@@ -609,7 +630,7 @@ __global__ void __launch_bounds__(256) k_scan64(DevPtrs P, const int4* work) {
         const double e = __dadd_rn(Ep, dE64(ai, ac_s[tx * 4 + c], Jt[ty * 4 + r][tx * 4 + c], flip));
         if (e < T && e <= cap) {
           const int slot = atomicAdd(P.surv_cnt + b, 1);
-          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(pair_index(n, i, j), i, j);
+          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, j);
         }
       }
     }

@@ -212,9 +212,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     unsigned long long kk = 0, ent = 0;
     if (t < S) {
       ent = sv[t];
-      uint32_t c;
       int i, j;
-      surv_decode(ent, c, i, j);
+      surv_sites(ent, i, j);
+      const uint32_t c = (j < 0) ? (uint32_t)i : pair_index(d.n, i, j);   // Sec. III flip order
+      ent |= c;
       const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
       if (fp64) {
         const double* a = P.a64 + (long long)b * P.NP;

@@ -77,7 +77,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
 struct __align__(128) ScanRing {
   float2 col[kRing][kPer][256];   // {a_j, s_j} of the chunk's columns
   float2 row[kRing][kPer][32];    // {a_i, s_i} of the block's rows
-  float4 ctl[kRing][kPer];        // {thr, active, RD(min_j a_j - j4max), -}
+  float4 ctl[kRing][kPer];        // {thr, active, -, w = min a_j over the chunk's 8-group window}
   uint64_t full[kRing];
   int rel[kRing];
   int issued[kRing];
@@ -115,7 +115,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       const long long b = b0 + u * kPer + lane;
       bulk_g2s(&sm.col[q][lane][0], P.as32 + b * NPs + c0, (uint32_t)(cols * 8), &sm.full[q]);
       bulk_g2s(&sm.row[q][lane][0], P.as32 + b * NPs + row0, 32 * 8, &sm.full[q]);
-      bulk_g2s(&sm.ctl[q][lane], P.sctl + b, 16, &sm.full[q]);
+      bulk_g2s(&sm.ctl[q][lane], P.sctl + b * (NPs / 32) + (c0 >> 5), 16, &sm.full[q]);
     }
     if (lane == 0) sm.issued[q] += 1;
   };
@@ -145,6 +145,18 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       J[r][k] = (i < n && j < n && j > i) ? J4[(long long)i * np + j] : qnan;
     }
   }
+  // max |4J~_ij| over the task's columns of the row this lane votes for (row i0 + lane % 8);
+  // -inf for a row without pairs here (NaN couplings are ignored by fmaxf)
+  float rmax = -INFINITY;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) m = fmaxf(m, fabsf(J[r][k]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((lane & 7) == r) rmax = m;
+  }
   const uint64_t t0 = gtimer();
   int nlive = 0;   // rows this warp evaluated (statistics)
   for (int u = 0; u < nslots; ++u) {
@@ -164,8 +176,9 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       break;
     }
     // the slot's rows that can hit, four searches per ballot: lane l takes search 4h + (l >> 3)
-    // and row i0 + (l & 7). y_ij >= RD(min_j a_j - j4max) = ctl.z for every column (rounding
-    // is monotone), so a row with c_i = fl32(thr - a_i) below it has no pair under its bound
+    // and row i0 + (l & 7). y_ij >= RD(w - max_j |4J~_ij|) for every column of the chunk
+    // (rounding is monotone; w <= a_j), so a row with c_i = fl32(thr - a_i) below it has no
+    // pair under its bound
     const int ns = min(kPer, R - u * kPer);
     unsigned long long live64 = 0, neg64 = 0;   // bit 8p + r: row r of search p live / s_i = -1
     float cv[kPer / 4];
@@ -175,7 +188,8 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       const float4 ctl = sm.ctl[q][p];   // slots past ns hold stale values: masked below
       const float2 rv = sm.row[q][p][warp * 8 + (lane & 7)];
       cv[h] = __fsub_rn(ctl.x, rv.x);
-      live64 |= (unsigned long long)__ballot_sync(0xffffffffu, p < ns && ctl.y != 0.f && cv[h] >= ctl.z)
+      live64 |= (unsigned long long)__ballot_sync(0xffffffffu,
+                                                  p < ns && ctl.y != 0.f && cv[h] >= __fsub_rd(ctl.w, rmax))
                 << (32 * h);
       neg64 |= (unsigned long long)__ballot_sync(0xffffffffu, rv.y < 0.f) << (32 * h);
     }
@@ -201,7 +215,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
         }
       }
       {
-        unsigned long long cm = 0;   // exact hits of this lane: bit r NC + k = (row i0 + r, column k)
+        unsigned long long cm = 0;   // exact hits of this lane: bit 8r + k = (row i0 + r, column k)
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           if (!((live >> r) & 1u)) continue;   // uniform
@@ -217,16 +231,17 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
           if (rowmin<NC>(y) <= c) {   // this lane has a hit in row r: which columns
 #pragma unroll
             for (int k = 0; k < NC; ++k)
-              if (y[k] <= c) cm |= 1ull << (r * NC + k);
+              if (y[k] <= c) cm |= 1ull << (r * 8 + k);
           }
         }
-        if (cm) {   // one survivor entry per passing pair
+        if (cm) {   // one survivor entry per passing pair: sites i0 + r, c0 + 32k + lane
           int slot = atomicAdd(P.surv_cnt + b0 + s, __popcll(cm));
+          unsigned long long* dst = P.surv + (long long)(b0 + s) * cap;
+          const unsigned long long e0 = surv_entry(i0, c0 + lane);
           do {
             const int bit = __ffsll((long long)cm) - 1;
             cm &= cm - 1;
-            const int i = i0 + bit / NC, j = c0 + 32 * (bit % NC) + lane;
-            if (slot < cap) P.surv[(long long)(b0 + s) * cap + slot] = surv_entry(pair_index(n, i, j), i, j);
+            if (slot < cap) dst[slot] = e0 + ((unsigned long long)(bit >> 3) << 32) + ((unsigned long long)(bit & 7) << 49);
             ++slot;
           } while (cm);
         }
