@@ -272,7 +272,6 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   __shared__ int sites[kSubSites];
   __shared__ float gmin[kMaxN / 32];   // min a_j of each 32-column group
   __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near;
-  __shared__ float s_amin, s_amax;
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ float s_thr;
   __shared__ double s_T, s_cap;
@@ -285,17 +284,40 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   }
   const double Ep = P.par_E[b];
   const double* a64 = P.a64 + (long long)b * P.NP;
-  // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory
+  // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory;
+  // the range of a_i is taken on the way (a ~ fl32 of the exact value in FP64 mode too: only
+  // used to bin sites)
   float2* as = reinterpret_cast<float2*>(subkey + kSubMax);   // [NP]
-  if (!fp64) {
-    const float2* g = P.as32 + (long long)b * P.NP;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) as[i] = g[i];
+  __shared__ float wmn[4], wmx[4];
+  {
+    float mn = INFINITY, mx = -INFINITY;
+    if (!fp64) {
+      const float2* g = P.as32 + (long long)b * P.NP;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float2 v = g[i];
+        as[i] = v;
+        mn = fminf(mn, v.x);
+        mx = fmaxf(mx, v.x);
+      }
+    } else {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float v = (float)a64[i];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wmn[threadIdx.x >> 5] = mn;
+      wmx[threadIdx.x >> 5] = mx;
+    }
   }
   for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   if (threadIdx.x == 0) {
     P.surv_cnt[b] = 0;
-    s_amin = INFINITY;
-    s_amax = -INFINITY;
     s_nsites = 0;
     s_n2 = 0;
     s_near = 0;
@@ -315,41 +337,15 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
       P.amin64[b] = m;
     }
   }
-  // range of a_i (a ~ fl32 of the exact value in FP64 mode too: only used to bin sites)
-  {
-    float mn = INFINITY, mx = -INFINITY;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float a = fp64 ? (float)a64[i] : as[i].x;
-      mn = fminf(mn, a);
-      mx = fmaxf(mx, a);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    __shared__ float wmn[4], wmx[4];
-    if ((threadIdx.x & 31) == 0) {
-      wmn[threadIdx.x >> 5] = mn;
-      wmx[threadIdx.x >> 5] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float a = wmn[0], c = wmx[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        a = fminf(a, wmn[w]);
-        c = fmaxf(c, wmx[w]);
-      }
-      s_amin = a;
-      s_amax = c;
-    }
-    __syncthreads();
-  }
+  const float amin = fminf(fminf(wmn[0], wmn[1]), fminf(wmn[2], wmn[3]));
+  const float amax = fmaxf(fmaxf(wmx[0], wmx[1]), fmaxf(wmx[2], wmx[3]));
   // kept states one or two flips away from the parent: the only candidates that can be
   // duplicates, each equal to exactly one candidate (the single flip of its differing site, or
   // the pair of its two). Their candidate indices go to dup_c for the merge's duplicate test;
-  // among the K+1+near lowest candidates at least K+1 are new states.
+  // among the K+1+near lowest candidates at least K+1 are new states. The kept states are the
+  // list slots 0 .. cnt-1, one per thread.
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-    const uint64_t* x = P.lst_bits + (base + P.lst_ord[base + r]) * P.Wmax;
+    const uint64_t* x = P.lst_bits + (base + r) * P.Wmax;
     // one pass: the distance and the first two differing sites (ascending); the words come in
     // blocks of 8 loaded together, then examined
     int dist = 0, p0 = 0, p1 = 0;
@@ -379,7 +375,6 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   __syncthreads();
   if (threadIdx.x == 0) P.dup_n[b] = s_near;
   const int k = P.K1 + s_near;
-  const float amin = s_amin, amax = s_amax;
   double U = INFINITY;
   // candidates of the flip set: n singles; nu nd exchanges (nu up, nd = n - nu down spins);
   // or n singles and n(n-1)/2 pairs

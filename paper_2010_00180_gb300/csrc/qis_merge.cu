@@ -136,6 +136,51 @@ __device__ void sort_runs(const unsigned long long* key, const unsigned long lon
   __syncthreads();
 }
 
+// Ascending bitonic sort of 32 single keys of one warp, one per lane, in shuffles.
+__device__ __forceinline__ void warp_sort32_key(unsigned long long& key) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key, j);
+      const bool want_min = ((lane & j) == 0) == ((lane & k) == 0);
+      key = want_min ? min(key, ko) : max(key, ko);
+    }
+  }
+}
+
+// sort_runs for packed keys ((key - kmin) << cb | c: one 64-bit value carries the (key, c)
+// order when the keys span less than 2^(64 - cb)); the packing is done on load. Output in
+// okey[0..nv). Every thread of the block calls it; nv <= blockDim.x.
+__device__ void sort_runs_packed(const unsigned long long* key, const unsigned long long* ent, int nv,
+                                 unsigned long long kmin, int cb, unsigned long long* okey) {
+  const int t = threadIdx.x, w = t >> 5;
+  const int nr = (nv + 31) >> 5;
+  unsigned long long k = ~0ull;
+  if (t < nv) k = ((key[t] - kmin) << cb) | (uint32_t)ent[t];
+  if (w < nr) warp_sort32_key(k);   // warp-uniform
+  okey[t] = k;
+  __syncthreads();
+  int pos = t & 31;
+  const bool real = w < nr && k != ~0ull;   // a packed key is never all ones (c < 2^cb - 1)
+  if (real) {
+    for (int v = 0; v < nr; ++v) {
+      if (v == w) continue;
+      const unsigned long long* rk = okey + 32 * v;
+      int lo = 0, hi = 32;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rk[mid] < k) lo = mid + 1; else hi = mid;
+      }
+      pos += lo;
+    }
+  }
+  __syncthreads();
+  if (real) okey[pos] = k;
+  __syncthreads();
+}
+
 __device__ inline uint64_t flip_mask(int x, int i, int j) {
   uint64_t m = 0;
   if ((i >> 6) == x) m ^= 1ull << (i & 63);
@@ -169,6 +214,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   uint32_t* htab = reinterpret_cast<uint32_t*>(oslot + K1);                // [HT] duplicate candidates
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ int s_nv, s_ocut, wsum[33];
+  __shared__ unsigned long long s_kmin, s_kmax;
   const int cnt = P.lst_count[b];
   const bool fp64 = P.mode == QIS_FP64;
   // threshold and parent energy: FP64 values in the plain form, exact integers E 2^q otherwise
@@ -187,6 +233,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   if (threadIdx.x == 0) {
     s_nv = 0;
     s_ocut = cnt;
+    s_kmin = ~0ull;
+    s_kmax = 0;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {   // two independent coalesced loads
@@ -206,6 +254,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   //         is not a kept state (the binary search of Alg. 2: membership of its candidate
   //         index among those of the near kept states); compact the kept ones (warp-aggregated)
   const unsigned long long* sv = P.surv + (long long)b * P.cap;
+  unsigned long long kmn = ~0ull, kmx = 0;   // range of this thread's kept keys
   for (int t0 = 0; t0 < S; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
     bool keep = false;
@@ -251,8 +300,19 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
         const int slot = wb + __popc(bal & ((1u << lane) - 1));
         sk[slot] = kk;          // slot < S <= cap <= PC
         se[slot] = ent;
+        kmn = min(kmn, kk);
+        kmx = max(kmx, kk);
       }
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kmn = min(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
+    kmx = max(kmx, __shfl_xor_sync(0xffffffffu, kmx, o));
+  }
+  if (lane == 0 && kmn <= kmx) {
+    atomicMin(&s_kmin, kmn);
+    atomicMax(&s_kmax, kmx);
   }
   __syncthreads();
   int nv = s_nv;
@@ -283,8 +343,17 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     }
     nv = kept;
   }
-  // ---- 2. order the kept candidates by (E, c)
-  if (nv > 1) {
+  // ---- 2. order the kept candidates by (E, c). When the kept keys span less than 2^(64-cb)
+  //         (cb = bits of the largest candidate index) one 64-bit value (key - kmin) << cb | c
+  //         carries that order: a single-key sort (the usual case)
+  const unsigned long long kmin = s_kmin;
+  const uint32_t n_cand = (uint32_t)d.n + (uint32_t)((long long)d.n * (d.n - 1) / 2);
+  const int cb = 32 - __clz((int)n_cand);   // c <= n_cand - 1 < 2^cb - 1
+  const bool packed = nv > 1 && nv <= (int)blockDim.x && ((s_kmax - kmin) >> (64 - cb)) == 0;
+  if (packed) {
+    sort_runs_packed(sk, se, nv, kmin, cb, sk2);
+    sk = sk2;
+  } else if (nv > 1) {
     if (nv <= (int)blockDim.x) {
       sort_runs(sk, se, nv, sk2, se2);
       sk = sk2;
@@ -304,12 +373,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   //         precede new ones of equal energy); new entry p -> p + #(old with E <= E_p). Both
   //         ranks grow along their lists, so the evicted old entries (rank >= K+1) are a
   //         suffix o >= s_ocut and the kept new entries a prefix p < K+1 - s_ocut.
+  const unsigned long long cmask = (1ull << cb) - 1;
+  auto new_key = [&](int p) { return packed ? (sk[p] >> cb) + kmin : sk[p]; };
   for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
     const unsigned long long ko = okey[o];
     int lo = 0, hi = nv;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (sk[mid] < ko) lo = mid + 1; else hi = mid;
+      if (new_key(mid) < ko) lo = mid + 1; else hi = mid;
     }
     const int rank = o + lo;
     if (rank < K1) {
@@ -325,7 +396,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   const int ocut = s_ocut, n_ev = cnt - ocut;
   const int t_now = P.iter_t[b];
   for (int p = threadIdx.x; p < nv; p += blockDim.x) {
-    const unsigned long long kp = sk[p];
+    const unsigned long long kp = new_key(p);
     int lo = 0, hi = cnt;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
@@ -336,7 +407,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     const int slot = (p < n_ev) ? oslot[ocut + p] : cnt + (p - n_ev);
     uint32_t c;
     int i, j;
-    surv_decode(se[p], c, i, j);
+    if (packed) {
+      c = (uint32_t)(sk[p] & cmask);
+      decode_candidate(d.n, c, i, j);
+    } else {
+      surv_decode(se[p], c, i, j);
+    }
     uint64_t* dst = P.lst_bits + (base + slot) * P.Wmax;
     for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
     if (fp64) {
