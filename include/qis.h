@@ -220,6 +220,17 @@ int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t);
  * (as qis_reset). best / best_ms (may be NULL) receive the choice and its time. */
 int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms);
 
+/* Local fields by update (Sec. III energy algebra; the incremental form of the fields): a kept
+ * state is a one- or two-site flip of the parent it was generated from, so its exact integer
+ * fields are that parent's minus the flipped sites' coupling columns, O(n) instead of the
+ * O(n^2) field GEMM. The context keeps the fields of the last ring_n parents of every search
+ * (as many iterations as fit in 4 GiB, 2 to 128); a parent whose generator is older, the
+ * initial state and the entries of an imported list get full fields from the tensor-core GEMM
+ * (its tiles holding no such parent are skipped). Results are bit-identical either way.
+ * on = 1 (the default in the split modes) or 0; QIS_ERR_INVALID_ARG for on = 1 in the FP64
+ * mode (its fields follow the defining FP64 summation order) or with the SIMT field kernel. */
+int qis_set_incremental_fields(qis_ctx* ctx, int on);
+
 /* Pair terms the candidate scan evaluated one by one since the context was created: in the
  * split modes the scan skips every row whose bound c_i = thr - a_i lies below a lower bound
  * of all its pair terms, and counts (rows evaluated) x (chunk width, masked entries

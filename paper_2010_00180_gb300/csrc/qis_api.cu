@@ -192,6 +192,7 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   LAUNCH(launch_pick(P, s));
   CK(prof_end(ctx, 0));
   CK(prof_begin(ctx, 1));
+  if (P.inc_on) LAUNCH(launch_fields_inc(P, s));   // the rest: tiles the GEMM computes in full
   if (ctx->mode == QIS_FP64) LAUNCH(launch_fields_fp64(P, s));
   else if (ctx->fields_simt) LAUNCH(launch_fields_exact(P, s));
   else LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, P.gemm_nt, s));
@@ -354,8 +355,21 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.par_hash, B);
     ALLOC(P.active, B);
     ALLOC(P.iter_t, B);
+    ALLOC(P.par_stamp, B);
+    ALLOC(P.ring_t0, B);
+    ALLOC(P.full_tile, (size_t)ctx->max_inst * ((ctx->R + 15) / 16));
+    P.ring_n = 1;
+    P.ring_slot = (long long)B * NP;
     if (ctx->mode != QIS_FP64) {
-      ALLOC(P.aq, B * NP);
+      // the exact fields of the last ring_n parents of every search (fields by update): as many
+      // iterations as fit in 4 GiB, 2 .. 128 (QIS_FIELD_RING overrides)
+      const size_t slot = (size_t)B * NP * sizeof(long long);
+      int rn = (int)std::min<size_t>(128, std::max<size_t>(2, (4ull << 30) / slot));
+      const char* e = getenv("QIS_FIELD_RING");
+      if (e && atoi(e) >= 2) rn = atoi(e);
+      P.ring_n = rn;
+      P.inc_on = ctx->fields_simt ? 0 : 1;
+      ALLOC(P.aq, (size_t)rn * B * NP);
       ALLOC(P.as32, B * NP);
       P.s16_stride = (long long)(ctx->R + 255) * NP;   // room for ceil(R / NT) tiles of any NT <= 256
       ALLOC(P.S16, (size_t)ctx->max_inst * P.s16_stride);
@@ -634,7 +648,7 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
     }
     for (int it = 0; it < n_iters; ++it) {
       CK(cudaGraphLaunch(ctx->graph_exec, s));
-      ctx->launches += (ctx->cfg.flips == QIS_FLIPS_SINGLE) ? 4 : 5;   // kernels in the graph
+      ctx->launches += ((ctx->cfg.flips == QIS_FLIPS_SINGLE) ? 4 : 5) + (P.inc_on ? 1 : 0);   // kernels in the graph
     }
   } else {
     for (int it = 0; it < n_iters; ++it) {
@@ -731,7 +745,10 @@ int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* 
     ord[k] = k;
     act |= !u[k];
   }
-  const int one[4] = {count, act, t, 0};
+  // fields by update need the generating parent's ring entry: none for imported entries
+  int t0 = t;
+  for (int k = 0; k < count; ++k) t0 = std::max(t0, (int)std::min<uint64_t>(st[k] >> 32, 0x7fffffff));
+  const int one[5] = {count, act, t, 0, t0};
   cudaStream_t s = ctx->stream;
   const DevPtrs& P = ctx->P;
   CK(cudaMemcpyAsync(P.lst_bits + base * Wm, lb.data(), lb.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
@@ -745,6 +762,7 @@ int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* 
   CK(cudaMemcpyAsync(P.active + b, &one[1], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.iter_t + b, &one[2], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P.surv_cnt + b, &one[3], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P.ring_t0 + b, &one[4], sizeof(int), cudaMemcpyHostToDevice, s));
   LAUNCH(launch_hash_list(P, b, count, s));
   CK(cudaStreamSynchronize(s));   // the host vectors above are the copies' sources
   return 0;
@@ -1099,6 +1117,18 @@ int qis_get_tuning(qis_ctx* ctx, qis_tuning* out) {
   *out = ctx->tune;
   if (out->scan_search_group == 0) out->scan_search_group = ctx->R;
   if (out->gemm_tile_searches == 0) out->gemm_tile_searches = gemm_tile_n(ctx->R, ctx->digits_used);
+  return 0;
+}
+
+int qis_set_incremental_fields(qis_ctx* ctx, int on) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (on != 0 && on != 1) return fail(ctx, QIS_ERR_INVALID_ARG, "on must be 0 or 1");
+  if (on && (ctx->mode == QIS_FP64 || ctx->fields_simt))
+    return fail(ctx, QIS_ERR_INVALID_ARG, "fields by update need the split modes and the tensor-core field GEMM");
+  if (ctx->P.inc_on != on) {
+    ctx->P.inc_on = on;
+    drop_graph(ctx);   // the iteration's kernel sequence changes
+  }
   return 0;
 }
 

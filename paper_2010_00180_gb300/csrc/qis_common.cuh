@@ -68,7 +68,13 @@ struct DevPtrs {
   uint64_t* par_hash;     // [b]
   int* active;            // [b]
   int* iter_t;            // [b] iterations done
-  long long* aq;          // [b][n_pad] exact a_i * 2^q (split modes)
+  long long* aq;          // [ring_n][b][NP] exact a_i * 2^q of the parent of iteration t in slot t % ring_n (split modes)
+  int ring_n;             // slots of the aq ring
+  long long ring_slot;    // elements of one slot (every search of the context)
+  int inc_on;             // local fields by incremental update from the generating parent's (split modes)
+  uint64_t* par_stamp;    // [b] stamp (t << 32 | c) of the parent: its generating iteration and flips
+  int* ring_t0;           // [b] iterations <= ring_t0 have no aq ring entry (imported lists)
+  int* full_tile;         // [inst][ceil(R / gemm_nt)] 1: a search of the tensor-core tile needs full fields
   float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
@@ -97,6 +103,11 @@ struct DevPtrs {
 };
 
 __host__ __device__ inline int words_of(int n) { return (n + 63) >> 6; }
+
+// aq of search b at iteration t (the ring slot of that iteration's parent)
+__host__ __device__ inline long long* aq_of(const DevPtrs& P, long long b, int t) {
+  return P.aq + (long long)(t % P.ring_n) * P.ring_slot + b * P.NP;
+}
 
 // Tensor-core operands are stored pre-tiled in the exact shared-memory image of a K-major
 // operand with 128-byte swizzle: a tile is rows x 64 FP16 (128 bytes per row), 8-row groups
@@ -140,9 +151,11 @@ __host__ __device__ inline void surv_decode(unsigned long long e, uint32_t& c, i
 __device__ inline void decode_candidate(int n, uint32_t c, int& i, int& j) {
   if (c < (uint32_t)n) { i = (int)c; j = -1; return; }
   long long r = (long long)c - n;
-  // row i holds n-1-i pairs; start(i) = i*n - i*(i+1)/2
-  double nn = 2.0 * n - 1.0;
-  int ii = (int)((nn - sqrt(nn * nn - 8.0 * (double)r)) * 0.5);
+  // row i holds n-1-i pairs; start(i) = i*n - i*(i+1)/2. The closed form in FP32 lands within
+  // a step or two of the row (r < 2^23); the integer loops below make it exact. (FP64 here
+  // would cost every thread a double square root on GB300's narrow FP64 pipe.)
+  const float nn = 2.f * n - 1.f;
+  int ii = (int)((nn - sqrtf(fmaxf(nn * nn - 8.f * (float)r, 0.f))) * 0.5f);
   if (ii < 0) ii = 0;
   if (ii > n - 2) ii = n - 2;
   while (ii > 0 && (long long)ii * n - (long long)ii * (ii + 1) / 2 > r) --ii;
@@ -279,6 +292,7 @@ cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s,
 cudaError_t launch_hash_list(const DevPtrs& P, int b, int count, cudaStream_t s);
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);
+cudaError_t launch_fields_inc(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, int RG, cudaStream_t s);

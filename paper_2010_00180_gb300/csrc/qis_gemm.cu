@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
   const int bytesB = NT * kKC * 2;
   const int stage_bytes = Dm * kTileBytesA + bytesB;   // same layout for every instance
   const int n_mt = G.NP / 128, n_nt = (G.R + NT - 1) / NT, tpi = n_mt * n_nt;
+  // with fields by update, only the tiles holding a search that needs full fields (every role
+  // reads the same flags, written by the previous kernel)
+  auto skip = [&](int tile) { return P.inc_on && !P.full_tile[(tile / tpi) * n_nt + tile % n_nt]; };
   const int n_tiles = G.n_inst * tpi;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
   __shared__ int s_err;
   __shared__ uint64_t s_pw[256][2];   // parent spin words of the tile's rows, per search of the tile
   __shared__ int s_act[256];          // active flag per search of the tile
+  __shared__ int s_it[256];           // its iteration (the aq ring slot)
   int ncols = 32;
   while (ncols < nbuf * Dm * NT) ncols <<= 1;
 
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
     for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int*)&s_err; tile += gridDim.x) {
       const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128, n0 = (tile % n_nt) * NT;
       const InstDesc d = P.inst[inst];
-      if (m0 >= d.n_pad) continue;
+      if (m0 >= d.n_pad || skip(tile)) continue;
       const int kc_total = d.n_pad / kKC;
       for (int kc = 0; kc < kc_total; ++kc, ++it) {
         const int s = it % S;
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128;
       const InstDesc d = P.inst[inst];
-      if (m0 >= d.n_pad) continue;
+      if (m0 >= d.n_pad || skip(tile)) continue;
       const int buf = lt % nbuf, use = lt / nbuf;
       if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1, t0)) {
         atomicOr(&s_err, 2);
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128, n0 = (tile % n_nt) * NT;
       const InstDesc d = P.inst[inst];
-      if (m0 >= d.n_pad) continue;
+      if (m0 >= d.n_pad || skip(tile)) continue;
       const int buf = lt % nbuf, use = lt / nbuf;
       // the tile's per-search inputs, staged while its accumulators are being computed
       epi_bar();   // every epilogue warp is done with the previous tile's copy
@@ -242,6 +246,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
         const long long b = d.first_search + r;
         const bool valid = r < G.R;
         s_act[t] = valid ? P.active[b] : 0;
+        s_it[t] = valid ? P.iter_t[b] : 0;
         s_pw[t][0] = valid ? P.par_bits[b * G.Wmax + w0] : 0ull;
         s_pw[t][1] = (valid && w0 + 1 < G.Wmax) ? P.par_bits[b * G.Wmax + w0 + 1] : 0ull;
       }
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
               // fl32(aq 2^-q) = fl32(aq) 2^-q: scaling by a power of two commutes with rounding
               as = make_float2(__ll2float_rn(aq) * scale_q, sg ? -1.f : 1.f);
             }
-            P.aq[b * P.NP + i] = aq;
+            aq_of(P, b, s_it[t])[i] = aq;
             P.as32[b * P.NP + i] = as;
           }
         }

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
     P.lst_count[b] = 1;
     P.active[b] = 1;
     P.iter_t[b] = 0;
+    if (P.ring_t0) P.ring_t0[b] = 0;
     P.surv_cnt[b] = 0;
   }
 }

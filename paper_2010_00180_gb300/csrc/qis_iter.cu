@@ -46,6 +46,9 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
   }
   if (lane == 0) {
     P.iter_t[b] += 1;
+    const int r = b % P.R;   // clear the tile's full-fields flag (set again by k_fields_inc)
+    if (P.gemm_nt > 0 && r % P.gemm_nt == 0)
+      P.full_tile[(b / P.R) * ((P.R + P.gemm_nt - 1) / P.gemm_nt) + r / P.gemm_nt] = 0;
     if (sel < 0) {
       P.active[b] = 0;
     } else {
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
       P.par_E[b] = P.lst_E[base + sel];
       if (P.mode != QIS_FP64) P.par_q[b] = P.lst_q[base + sel];
       P.par_hash[b] = P.lst_hash[base + sel];
+      P.par_stamp[b] = P.lst_stamp[base + sel];
       P.nprod[b] += 1;   // n(n-1)/2 pair and n single candidates, counted on query
     }
   }
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(128) k_fields_exact(DevPtrs P) {
       a32 = (float)ldexp((double)aq, -d.q);
       s32 = sg ? -1.f : 1.f;
     }
-    P.aq[(long long)b * P.NP + i] = aq;
+    aq_of(P, b, P.iter_t[b])[i] = aq;
     P.as32[(long long)b * P.NP + i] = make_float2(a32, s32);
   }
 }
@@ -246,6 +250,82 @@ __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist
   }
   block_min_max(dummy, mx);
   return mx;
+}
+
+// ---------------------------------------------------------------- fields by update (split modes)
+// A kept state x entered the list at iteration tg (its stamp) as a flip of site i, or of sites
+// i and j, of that iteration's parent g, whose exact fields are in the aq ring. With s_g the
+// spins of g (s_x with i, j flipped back) the exact integer fields of x follow in O(n):
+//   fq_k(x) = fq_k(g) - 2 s_g,i Jq_ki - 2 s_g,j Jq_kj        (Jq_kk = 0)
+// from fq_k(g) = -s_g,k aq_k(g) / 2, and aq_k(x) = -2 s_x,k fq_k(x). The result equals the
+// field GEMM's bit for bit (both exact). A parent without a ring entry of its generator (the
+// initial state, an imported list, a generator more than ring_n iterations back) marks its
+// tensor-core tile, and the GEMM computes that tile in full.
+__global__ void __launch_bounds__(256) k_fields_inc(DevPtrs P) {
+  const int b = blockIdx.x;
+  // every load that depends only on b, issued together
+  const int act = P.active[b], t = P.iter_t[b], t0 = P.ring_t0[b];
+  const uint64_t st = P.par_stamp[b];
+  const InstDesc d = P.inst[b / P.R];
+  __shared__ uint64_t xb[kMaxN / 64];
+  for (int w = threadIdx.x; w < P.Wmax; w += blockDim.x) xb[w] = P.par_bits[(long long)b * P.Wmax + w];
+  __syncthreads();
+  if (!act) return;
+  const int tg = (int)(st >> 32);
+  if (!(tg >= 1 && tg > t0 && tg < t && t - tg < P.ring_n)) {
+    if (threadIdx.x == 0) {
+      const int r = b % P.R;
+      P.full_tile[(b / P.R) * ((P.R + P.gemm_nt - 1) / P.gemm_nt) + r / P.gemm_nt] = 1;
+    }
+    return;
+  }
+  int i, j;
+  decode_candidate(d.n, (uint32_t)st, i, j);
+  // 2 s_g at the flipped sites: s_g = -s_x there, s_x = -1 where sigma = 1
+  const long long gi = sigma_of(xb, i) ? 2 : -2;
+  const long long gj = (j >= 0) ? (sigma_of(xb, j) ? 2 : -2) : 0;
+  const long long* __restrict__ ag = aq_of(P, b, tg);
+  long long* __restrict__ ax = aq_of(P, b, t);
+  float2* __restrict__ as = P.as32 + (long long)b * P.NP;
+  const long long* __restrict__ Ji = P.Jq + d.off_mat + (long long)i * d.n_pad;   // row i = column i
+  const long long* __restrict__ Jj = P.Jq + d.off_mat + (long long)max(j, 0) * d.n_pad;
+  const float scale_q = (float)d.inv_scale;
+  constexpr int U = 4;   // sites per thread and pass, their loads issued together
+  for (int k0 = 0; k0 < d.n_pad; k0 += U * 256) {
+    long long vg[U], vi[U], vj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * 256 + threadIdx.x;
+      vg[u] = vi[u] = vj[u] = 0;
+      if (k < d.n) {
+        vg[u] = ag[k];
+        vi[u] = Ji[k];
+        if (j >= 0) vj[u] = Jj[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * 256 + threadIdx.x;
+      if (k >= d.n_pad) break;
+      long long aq = 0;
+      float2 a = make_float2(0.f, 0.f);
+      if (k < d.n) {
+        const int sx = sigma_of(xb, k);
+        const int sg = sx ^ (k == i || k == j);
+        const long long fg = sg ? vg[u] / 2 : -(vg[u] / 2);   // aq = -2 s f, s = -1 where sigma = 1
+        const long long fx = fg - gi * vi[u] - gj * vj[u];
+        aq = sx ? 2 * fx : -2 * fx;
+        a = make_float2(__ll2float_rn(aq) * scale_q, sx ? -1.f : 1.f);   // as the GEMM epilogue
+      }
+      ax[k] = aq;
+      as[k] = a;
+    }
+  }
+}
+
+cudaError_t launch_fields_inc(const DevPtrs& P, cudaStream_t s) {
+  k_fields_inc<<<P.B, 256, 0, s>>>(P);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- per-search bound

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
         keep = e < T;
         kk = dkey(e);
       } else {
-        const long long* aq = P.aq + (long long)b * P.NP;
+        const long long* aq = aq_of(P, b, P.iter_t[b]);
         long long de = aq[i];
         if (j >= 0) {
           const long long jq = P.Jq[d.off_mat + (long long)i * d.n_pad + j];

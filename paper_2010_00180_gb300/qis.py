@@ -23,6 +23,7 @@ SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
            "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs",
+           "qis_set_incremental_fields",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
            "qis_select_candidates_noalloc",
@@ -111,6 +112,7 @@ def load():
         "qis_mlp_loss_grad": (I, [P, I, P, P, C.POINTER(C.c_double), P]),
         "qis_mlp_train": (I, [P, I, C.c_float, C.POINTER(C.c_double)]),
         "qis_init_states_learned": (I, [P, I, P]),
+        "qis_set_incremental_fields": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,6 +256,10 @@ class Context:
     def set_tuning(self, scan_chunk_nc: int = 8, scan_search_group: int = 0, gemm_tile_searches: int = 0):
         t = Tuning(scan_chunk_nc, scan_search_group, gemm_tile_searches)
         self._check(self.lib.qis_set_tuning(self.h, C.byref(t)))
+
+    def set_incremental_fields(self, on: bool):
+        """Local fields by update from the generating parent's (qis_set_incremental_fields)."""
+        self._check(self.lib.qis_set_incremental_fields(self.h, 1 if on else 0))
 
     def autotune(self, iters: int = 8) -> dict:
         """Pick the fastest launch shapes for the current instances (resets every search)."""
