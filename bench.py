@@ -50,6 +50,8 @@ WORKLOADS = {
     # flip-set variants (Sec. V outlook): spin exchanges; single flips only at a larger n
     "gaussian_n600_120x64_exchange": ("gaussian", 600, 120, 120, 64, 120, "split_bf16", "exchange"),
     "gaussian_n2048_32x64_single": ("gaussian", 2048, 32, 120, 64, 120, "split_bf16", "single"),
+    # a third of the headline workload (same n, K, R): the size of the full ncu captures
+    "gaussian_n600_40x64": ("gaussian", 600, 40, 120, 64, 120, "split_bf16"),
 }
 FLIP_CODES = {"single_pair": 0, "single": 1, "exchange": 2}
 
@@ -421,21 +423,24 @@ def scan_traffic():
         return None
 
 
-def roofline_fields(res, pk, src):
-    """Local-field GEMM against the measured HBM bandwidth (the dominant kernel when there is
-    no pair scan): the FP16 digit planes of every instance are read once per launch."""
-    ms, nl = res["prof"]["fields"]
+def roofline_bound(res, pk, src):
+    """Per-search bound kernel against the measured HBM bandwidth (the dominant kernel when
+    there is no pair scan): per search it reads {a_i, s_i} of the parent (8 bytes a site) and
+    the bits of every kept state (8 bytes a word) to find the near duplicates."""
+    ms, nl = res["prof"]["bound"]
     if nl == 0 or ms <= 0:
         return None
-    n_pad = (res["n"] + 127) // 128 * 128
-    bytes_per_launch = 2.0 * res["digits"] * n_pad * n_pad * res["n_inst"]
+    n, K1 = res["n"], res["K"] + 1
+    words = (n + 63) // 64
+    searches = res["n_inst"] * res["R"]
+    bytes_per_launch = float(searches * (8 * n + 8 * K1 * words))
     dur = ms / nl / 1e3
     achieved = bytes_per_launch / dur / 1e9
     peak = float(pk.get("hbm_gbs", 6800.0))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_fields_tc",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_bound",
             "launch_us": round(dur * 1e6, 2), "bytes_per_launch": bytes_per_launch,
-            "per_unit": "2 bytes per coupling and digit (FP16 digit planes, shared by the R searches)",
+            "per_unit": "8 bytes per site ({a_i, s_i}) + 8 bytes per word of each of the K+1 kept states, per search",
             "peak_source": src}
 
 
@@ -544,7 +549,7 @@ def main():
     if rank != 0:
         return
     pk, src = peaks()
-    rl = roofline(res, pk) if flips != "single" else roofline_fields(res, pk, src)
+    rl = roofline(res, pk) if flips != "single" else roofline_bound(res, pk, src)
     value = res["pairs"] / (res["ms"] / 1e3)
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,

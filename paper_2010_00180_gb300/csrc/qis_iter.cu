@@ -356,12 +356,9 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   __shared__ float s_thr;
   __shared__ double s_T, s_cap;
   const int cnt = P.lst_count[b];
-  // T: the last kept energy, from the rank-ordered keys (exact integers in the split modes)
-  double T = INFINITY;
-  if (cnt == P.K1) {
-    const unsigned long long kT = P.lst_key[base + P.K1 - 1];
-    T = fp64 ? dkey_inv(kT) : (double)(long long)(kT ^ (1ull << 63)) * d.inv_scale;
-  }
+  // key of T, the last kept energy (its value is formed by thread 0 alone: FP64 arithmetic
+  // runs on a narrow pipe)
+  const unsigned long long kT = (cnt == P.K1) ? P.lst_key[base + P.K1 - 1] : 0ull;
   const double Ep = P.par_E[b];
   const double* a64 = P.a64 + (long long)b * P.NP;
   // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory;
@@ -455,7 +452,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   __syncthreads();
   if (threadIdx.x == 0) P.dup_n[b] = s_near;
   const int k = P.K1 + s_near;
-  double U = INFINITY;
+  double U = INFINITY;   // FP64 mode
+  float Uf = INFINITY;   // split modes
   // candidates of the flip set: n singles; nu nd exchanges (nu up, nd = n - nu down spins);
   // or n singles and n(n-1)/2 pairs
   const int fl = P.flips;
@@ -587,10 +585,15 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
       }
       __syncthreads();
       if (fp64) U = dkey_inv(radix_select<unsigned long long>(subkey, M, k - 1, hist));
-      else U = (double)value_select_upper(reinterpret_cast<const float*>(subkey), M, k - 1, hist, vlo, vhi);
+      else Uf = value_select_upper(reinterpret_cast<const float*>(subkey), M, k - 1, hist, vlo, vhi);
     }
   }
   if (threadIdx.x == 0) {
+    // T from its key (exact integers E 2^q in the split modes)
+    const double T = (cnt != P.K1) ? INFINITY
+                     : fp64        ? dkey_inv(kT)
+                                   : (double)(long long)(kT ^ (1ull << 63)) * d.inv_scale;
+    if (!fp64) U = (double)Uf;
     if (fp64) {
       s_T = T;
       s_cap = U;
