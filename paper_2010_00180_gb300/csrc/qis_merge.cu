@@ -215,20 +215,23 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   __shared__ uint64_t pb[kMaxN / 64];
   __shared__ int s_nv, s_ocut, wsum[33];
   __shared__ unsigned long long s_kmin, s_kmax;
-  const int cnt = P.lst_count[b];
   const bool fp64 = P.mode == QIS_FP64;
-  // threshold and parent energy: FP64 values in the plain form, exact integers E 2^q otherwise
-  double T = INFINITY, Ep = 0.0;
-  long long Tq = LLONG_MAX, Epq = 0;
-  if (fp64) {
-    if (cnt == K1) T = P.lst_E[base + P.lst_ord[base + K1 - 1]];
-    Ep = P.par_E[b];
-  } else {
-    if (cnt == K1) Tq = P.lst_q[base + P.lst_ord[base + K1 - 1]];
-    Epq = P.par_q[b];
-  }
+  // every load that depends only on b is issued before the first barrier: list length, the key
+  // of the last kept entry (T), the parent, the old list's order and keys, and the candidate
+  // indices of the kept states one or two flips from the parent (from k_bound: the only
+  // candidates that can equal a kept state; one per thread here, any further ones below)
+  const int cnt = P.lst_count[b];
+  const unsigned long long kT = P.lst_key[base + K1 - 1];   // meaningful when cnt == K1
+  const double Ep = fp64 ? P.par_E[b] : 0.0;
+  const long long Epq = fp64 ? 0 : P.par_q[b];
   const uint64_t ph = P.par_hash[b];
+  const int ndup = P.dup_n[b];
+  const uint32_t dc0 = (threadIdx.x < K1) ? P.dup_c[base + threadIdx.x] : kNoCand;
   for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
+  for (int r = threadIdx.x; r < K1; r += blockDim.x) {   // two independent coalesced loads
+    oslot[r] = P.lst_ord[base + r];
+    okey[r] = P.lst_key[base + r];
+  }
   for (int k = threadIdx.x; k < HT; k += blockDim.x) htab[k] = kNoCand;
   if (threadIdx.x == 0) {
     s_nv = 0;
@@ -236,16 +239,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     s_kmin = ~0ull;
     s_kmax = 0;
   }
+  // threshold: FP64 values in the plain form, exact integers E 2^q otherwise (rank-ordered keys)
+  const double T = (cnt == K1 && fp64) ? dkey_inv(kT) : INFINITY;
+  const long long Tq = (cnt == K1 && !fp64) ? (long long)(kT ^ (1ull << 63)) : LLONG_MAX;
   __syncthreads();
-  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {   // two independent coalesced loads
-    oslot[r] = P.lst_ord[base + r];
-    okey[r] = P.lst_key[base + r];
-  }
-  // candidate indices of the kept states one or two flips from the parent (from k_bound): the
-  // only candidates that can equal a kept state
-  const int ndup = P.dup_n[b];
   for (int r = threadIdx.x; r < ndup; r += blockDim.x) {
-    const uint32_t c = P.dup_c[base + r];
+    const uint32_t c = (r == (int)threadIdx.x) ? dc0 : P.dup_c[base + r];
     uint32_t pos = chash(c) & (HT - 1);
     while (atomicCAS(&htab[pos], kNoCand, c) != kNoCand) pos = (pos + 1) & (HT - 1);
   }
