@@ -242,6 +242,36 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   // threshold: FP64 values in the plain form, exact integers E 2^q otherwise (rank-ordered keys)
   const double T = (cnt == K1 && fp64) ? dkey_inv(kT) : INFINITY;
   const long long Tq = (cnt == K1 && !fp64) ? (long long)(kT ^ (1ull << 63)) : LLONG_MAX;
+  // exact energy of survivor t and the threshold test E' < T (strict, Alg. 2); the candidate
+  // index c (Sec. III flip order) goes into the entry's low bits. Reads the parent's spins from
+  // global memory, so the first block of survivors is evaluated before the first barrier.
+  const unsigned long long* sv = P.surv + (long long)b * P.cap;
+  const uint64_t* pbg = P.par_bits + (long long)b * P.Wmax;
+  const long long* aqb = fp64 ? nullptr : aq_of(P, b, P.iter_t[b]);
+  auto eval = [&](int t, unsigned long long& kk, unsigned long long& ent) -> bool {
+    ent = sv[t];
+    int i, j;
+    surv_sites(ent, i, j);
+    ent |= (j < 0) ? (uint32_t)i : pair_index(d.n, i, j);
+    const int si = sigma_of(pbg, i), sj = (j >= 0) ? sigma_of(pbg, j) : 0;
+    if (fp64) {
+      const double* a = P.a64 + (long long)b * P.NP;
+      const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
+      const double e = __dadd_rn(Ep, de);
+      kk = dkey(e);
+      return e < T;
+    }
+    long long de = aqb[i];
+    if (j >= 0) {
+      const long long jq = P.Jq[d.off_mat + (long long)i * d.n_pad + j];
+      de += aqb[j] + ((si ^ sj) ? -4 * jq : 4 * jq);
+    }
+    const long long eq = Epq + de;
+    kk = qkey(eq);
+    return eq < Tq;
+  };
+  unsigned long long kk0 = 0, ent0 = 0;
+  const bool keep0 = (int)threadIdx.x < S && eval(threadIdx.x, kk0, ent0);
   __syncthreads();
   for (int r = threadIdx.x; r < ndup; r += blockDim.x) {
     const uint32_t c = (r == (int)threadIdx.x) ? dc0 : P.dup_c[base + r];
@@ -249,46 +279,28 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     while (atomicCAS(&htab[pos], kNoCand, c) != kNoCand) pos = (pos + 1) & (HT - 1);
   }
   __syncthreads();
-  // ---- 1. exact energy of every survivor of the filter; keep E' < T (strict, Alg. 2) that
-  //         is not a kept state (the binary search of Alg. 2: membership of its candidate
-  //         index among those of the near kept states); compact the kept ones (warp-aggregated)
-  const unsigned long long* sv = P.surv + (long long)b * P.cap;
+  // ---- 1. keep the survivors with E' < T that are not a kept state (the binary search of
+  //         Alg. 2: membership of the candidate index among those of the near kept states);
+  //         compact the kept ones (warp-aggregated)
   unsigned long long kmn = ~0ull, kmx = 0;   // range of this thread's kept keys
   for (int t0 = 0; t0 < S; t0 += blockDim.x) {
     const int t = t0 + threadIdx.x;
     bool keep = false;
     unsigned long long kk = 0, ent = 0;
-    if (t < S) {
-      ent = sv[t];
-      int i, j;
-      surv_sites(ent, i, j);
-      const uint32_t c = (j < 0) ? (uint32_t)i : pair_index(d.n, i, j);   // Sec. III flip order
-      ent |= c;
-      const int si = sigma_of(pb, i), sj = (j >= 0) ? sigma_of(pb, j) : 0;
-      if (fp64) {
-        const double* a = P.a64 + (long long)b * P.NP;
-        const double de = (j < 0) ? a[i] : dE64(a[i], a[j], P.J64[d.off_mat + (long long)i * d.n_pad + j], si ^ sj);
-        const double e = __dadd_rn(Ep, de);
-        keep = e < T;
-        kk = dkey(e);
-      } else {
-        const long long* aq = aq_of(P, b, P.iter_t[b]);
-        long long de = aq[i];
-        if (j >= 0) {
-          const long long jq = P.Jq[d.off_mat + (long long)i * d.n_pad + j];
-          de += aq[j] + ((si ^ sj) ? -4 * jq : 4 * jq);
+    if (t0 == 0) {
+      keep = keep0;
+      kk = kk0;
+      ent = ent0;
+    } else if (t < S) {
+      keep = eval(t, kk, ent);
+    }
+    if (keep) {
+      const uint32_t c = (uint32_t)ent;
+      for (uint32_t pos = chash(c) & (HT - 1); htab[pos] != kNoCand; pos = (pos + 1) & (HT - 1))
+        if (htab[pos] == c) {
+          keep = false;   // duplicate of a kept state
+          break;
         }
-        const long long eq = Epq + de;
-        keep = eq < Tq;
-        kk = qkey(eq);
-      }
-      if (keep) {
-        for (uint32_t pos = chash(c) & (HT - 1); htab[pos] != kNoCand; pos = (pos + 1) & (HT - 1))
-          if (htab[pos] == c) {
-            keep = false;   // duplicate of a kept state
-            break;
-          }
-      }
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (bal) {
