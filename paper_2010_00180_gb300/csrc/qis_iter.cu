@@ -407,11 +407,22 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     float mn = INFINITY, mx = -INFINITY;
     if (!fp64) {
       const float2* g = P.as32 + (long long)b * P.NP;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 v = g[i];
-        as[i] = v;
-        mn = fminf(mn, v.x);
-        mx = fmaxf(mx, v.x);
+      for (int i0 = 0; i0 < n; i0 += 8 * 128) {   // eight loads in flight per thread, then stores
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 128 + threadIdx.x;
+          v[u] = (i < n) ? g[i] : make_float2(INFINITY, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * 128 + threadIdx.x;
+          if (i < n) {
+            as[i] = v[u];
+            mn = fminf(mn, v[u].x);
+            mx = fmaxf(mx, v[u].x);
+          }
+        }
       }
     } else {
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -554,45 +565,70 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
     __syncthreads();
     const int mm = min(s_nsites, lim0), m2 = min(s_n2, t1);
     const int M = fl == QIS_FLIPS_SINGLE ? min(s_nsites, kSubMax) : ex ? mm * m2 : mm + mm * (mm - 1) / 2;
-    if (M >= k) {
-#pragma unroll 2
-      for (int t = threadIdx.x; t < M && fl != QIS_FLIPS_SINGLE; t += blockDim.x) {
-        int i, j = -1;
-        if (ex) {
-          i = sites[t / m2];
-          j = sites[lim0 + t % m2];
-        } else if (t < mm) {
-          i = sites[t];
-        } else {
-          // pair rank r -> (x, y), x < y < mm: row x starts at x mm - x(x+1)/2 (closed form,
-          // then corrected by one step either way)
-          const int r = t - mm;
-          const float q = 2.f * mm - 1.f;
-          int x = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)r, 0.f))) * 0.5f);
-          x = max(0, min(x, mm - 2));
-          while (x > 0 && x * mm - x * (x + 1) / 2 > r) --x;
-          while (x < mm - 2 && (x + 1) * mm - (x + 1) * (x + 2) / 2 <= r) ++x;
-          const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
-          i = sites[x];
-          j = sites[y];
+    // site pair of subset member t (t < M; not for single flips, whose members are written above)
+    auto member = [&](int t, int& i, int& j) {
+      j = -1;
+      if (ex) {
+        i = sites[t / m2];
+        j = sites[lim0 + t % m2];
+      } else if (t < mm) {
+        i = sites[t];
+      } else {
+        // pair rank r -> (x, y), x < y < mm: row x starts at x mm - x(x+1)/2 (closed form,
+        // then corrected by one step either way)
+        const int r = t - mm;
+        const float q = 2.f * mm - 1.f;
+        int x = (int)((q - sqrtf(fmaxf(q * q - 8.f * (float)r, 0.f))) * 0.5f);
+        x = max(0, min(x, mm - 2));
+        while (x > 0 && x * mm - x * (x + 1) / 2 > r) --x;
+        while (x < mm - 2 && (x + 1) * mm - (x + 1) * (x + 2) / 2 <= r) ++x;
+        const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
+        i = sites[x];
+        j = sites[y];
+      }
+      if (j >= 0 && i > j) { const int tmp = i; i = j; j = tmp; }
+    };
+    if (M >= k && !fp64 && fl != QIS_FLIPS_SINGLE) {
+      // split modes: four members per thread and pass, their coupling gathers issued together
+      for (int t0 = 0; t0 < M; t0 += 4 * 128) {
+        int mi[4], mj[4];
+        float j4v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = t0 + u * 128 + threadIdx.x;
+          mi[u] = 0;
+          mj[u] = -1;
+          j4v[u] = 0.f;
+          if (t < M) {
+            member(t, mi[u], mj[u]);
+            if (mj[u] >= 0) j4v[u] = P.J4[d.off_mat + (long long)mi[u] * d.n_pad + mj[u]];
+          }
         }
-        if (j >= 0 && i > j) { const int tmp = i; i = j; j = tmp; }
-        if (fp64) {
-          double de = a64[i];
-          if (j >= 0) de = dE64(a64[i], a64[j], P.J64[d.off_mat + (long long)i * d.n_pad + j],
-                                sigma_of(pb, i) ^ sigma_of(pb, j));
-          subkey[t] = dkey(__dadd_rn(Ep, de));
-        } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = t0 + u * 128 + threadIdx.x;
+          if (t >= M) break;
+          const int i = mi[u], j = mj[u];
           float de = as[i].x;
           if (j >= 0) {
             const float2 vj = as[j];
-            const float j4 = P.J4[d.off_mat + (long long)i * d.n_pad + j];
-            de = as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x);
+            de = as[i].x + fmaf((sigma_of(pb, i) ? -j4v[u] : j4v[u]), vj.y, vj.x);
           }
           vlo = fminf(vlo, de);
           vhi = fmaxf(vhi, de);
           reinterpret_cast<float*>(subkey)[t] = de;
         }
+      }
+    }
+    if (M >= k) {
+#pragma unroll 2
+      for (int t = threadIdx.x; t < M && fp64 && fl != QIS_FLIPS_SINGLE; t += blockDim.x) {
+        int i, j;
+        member(t, i, j);
+        double de = a64[i];
+        if (j >= 0) de = dE64(a64[i], a64[j], P.J64[d.off_mat + (long long)i * d.n_pad + j],
+                              sigma_of(pb, i) ^ sigma_of(pb, j));
+        subkey[t] = dkey(__dadd_rn(Ep, de));
       }
       __syncthreads();
       if (fp64) U = dkey_inv(radix_select<unsigned long long>(subkey, M, k - 1, hist));
