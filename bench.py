@@ -247,8 +247,8 @@ def run_ours(args, rank, world, device):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             ctx.clear_instances()
-            for J, h, phi in data:
-                iid = ctx.create_instance(J, h)
+            ids = ctx.create_instances([(J, h) for J, h, _ in data])
+            for iid, (_, _, phi) in zip(ids, data):
                 ctx.init_states(iid, phi)
             ctx.iterate(I_)
             for k in range(n_inst):

@@ -104,6 +104,13 @@ const char* qis_last_error(const qis_ctx* ctx);
  * Synchronises the library stream (validation result). */
 int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id);
 
+/* Add `count` instances at once (Eq. (1)), as `count` calls of qis_create_instance would, but
+ * with one validation read-back for the whole batch: n[k], J[k], h[k] as there; ids
+ * (may be NULL) receive the new ids. If any instance is invalid, none of the batch is added
+ * and the error names the first. Synchronises the library stream once. */
+int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* const* J, const double* const* h,
+                         int* instance_ids);
+
 /* Remove every instance (ids restart at 0); device buffers stay allocated. */
 int qis_clear_instances(qis_ctx* ctx);
 

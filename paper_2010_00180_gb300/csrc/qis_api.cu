@@ -46,6 +46,7 @@ struct qis_ctx {
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
   double* stats = nullptr;
+  double* jstage = nullptr;   // [max_n * max_n] one instance's J as copied from the host
   int4* work = nullptr;    // FP64 scan: 64 x 64 tiles x groups of searches
   int n_work = 0;
   int4* tasks = nullptr;   // FP32 scan: warp tasks (instance, strip, first column, chunk width)
@@ -53,6 +54,8 @@ struct qis_ctx {
   size_t tasks_cap = 0;
   bool work_dirty = true;
   bool merged_fresh = false;
+  bool counts_valid = false;      // mrg_counts holds the counts of the current merge (status checked)
+  std::vector<int> mrg_counts;
   uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
   double* scratch_E = nullptr;
   int scratch_states = 0;
@@ -316,7 +319,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
       ALLOC(ctx->hq, ctx->pool_vec);
     }
     ALLOC(ctx->zob, kMaxN);
-    ALLOC(ctx->stats, kMaxN + 8);
+    ALLOC(ctx->stats, (size_t)ctx->max_inst * (NP + 8));   // validation statistics of every instance
+    ALLOC(ctx->jstage, (size_t)cfg->max_n * cfg->max_n);
     ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2) *
                          ((ctx->R + kScan64Group - 1) / kScan64Group));
     ctx->tasks_cap = (size_t)ctx->max_inst * (NP / 8) * (NP / 32 + 2);
@@ -431,32 +435,45 @@ void qis_destroy(qis_ctx* ctx) {
 
 const char* qis_last_error(const qis_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
-int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id) {
-  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+namespace {
+
+// Argument checks of one instance that is to become id `id`.
+int check_instance_args(qis_ctx* ctx, int id, int n, const double* J, const double* h) {
   if (!J || !h) return fail(ctx, QIS_ERR_INVALID_ARG, "J and h must not be NULL");
   if (n < 2 || n > ctx->cfg.max_n) return fail(ctx, QIS_ERR_INVALID_ARG, "n must be in [2, max_n]");
-  if ((int)ctx->inst.size() >= ctx->max_inst) return fail(ctx, QIS_ERR_INVALID_ARG, "instance table full");
+  if (id >= ctx->max_inst) return fail(ctx, QIS_ERR_INVALID_ARG, "instance table full");
   if (n < 63 && (uint64_t)ctx->cfg.K >= (1ull << n))
     return fail(ctx, QIS_ERR_INVALID_ARG, "K must be below 2^n (Alg. 2 requires 1 <= K < 2^N)");
-  CK(cudaSetDevice(ctx->cfg.device));
-  const int id = (int)ctx->inst.size();
-  InstDesc d{};
+  return 0;
+}
+
+// Copy J and h of instance id to the device and validate them into stats slot `slot`
+// (asynchronous on the library stream).
+int upload_instance(qis_ctx* ctx, int id, int slot, int n, const double* J, const double* h) {
+  const long long off_mat = (long long)id * ctx->NP * ctx->NP, off_vec = (long long)id * ctx->NP;
+  const int n_pad = pad_of(n);
+  cudaStream_t s = ctx->stream;
+  // one contiguous copy (a pitched copy from pageable memory goes row by row), then the
+  // padded layout on the device; a copy from pageable memory first waits for the stream, so
+  // the staging buffer is free again
+  CK(cudaMemcpyAsync(ctx->jstage, J, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, s));
+  LAUNCH(launch_restride(ctx->jstage, n, n_pad, ctx->J64 + off_mat, s));
+  CK(cudaMemsetAsync(ctx->h64 + off_vec, 0, sizeof(double) * n_pad, s));
+  CK(cudaMemcpyAsync(ctx->h64 + off_vec, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  LAUNCH(launch_validate(ctx->P, id, n, off_mat, off_vec, ctx->stats + (size_t)slot * (ctx->NP + 8), s));
+  return 0;
+}
+
+// The descriptor of instance id from its validation statistics (host): the checks of J and
+// h, the fixed-point grid 2^-q and the number of base-4096 digits.
+int describe_instance(qis_ctx* ctx, int id, int n, const double* st, InstDesc& d) {
+  d = InstDesc{};
   d.n = n;
   d.n_pad = pad_of(n);
   d.W = words_of(n);
   d.first_search = id * ctx->R;
   d.off_mat = (long long)id * ctx->NP * ctx->NP;
   d.off_vec = (long long)id * ctx->NP;
-  cudaStream_t s = ctx->stream;
-  CK(cudaMemsetAsync(ctx->J64 + d.off_mat, 0, sizeof(double) * (size_t)d.n_pad * d.n_pad, s));
-  CK(cudaMemsetAsync(ctx->h64 + d.off_vec, 0, sizeof(double) * d.n_pad, s));
-  CK(cudaMemcpy2DAsync(ctx->J64 + d.off_mat, sizeof(double) * d.n_pad, J, sizeof(double) * n, sizeof(double) * n, n,
-                       cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(ctx->h64 + d.off_vec, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  LAUNCH(launch_validate(ctx->P, id, n, d.off_mat, d.off_vec, ctx->stats, s));
-  std::vector<double> st(n + 5);
-  CK(cudaMemcpyAsync(st.data(), ctx->stats, sizeof(double) * (n + 5), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
   int bad, maxfrac;
   uint64_t mjb, mhb;
   memcpy(&bad, &st[0], sizeof(int));
@@ -503,18 +520,66 @@ int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, i
     d.inv_scale = ldexp(1.0, -q);
     d.j4max = (float)(4.0 * ldexp(rint(maxJq), -q)) * (1.0f + 1e-6f);
   }
-  CK(cudaMemcpyAsync(ctx->inst_d + id, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, s));
-  if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, id, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
-  CK(cudaStreamSynchronize(s));
-  ctx->inst.push_back(d);
-  if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
-  ctx->inst_ready.push_back(0);
+  return 0;
+}
+
+// Register described instances ids first .. first+count-1: descriptors to the device, the
+// fixed-point planes, the host tables (asynchronous on the library stream).
+int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->inst_d + first, ds.data(), sizeof(InstDesc) * ds.size(), cudaMemcpyHostToDevice, s));
+  for (size_t k = 0; k < ds.size(); ++k) {
+    const InstDesc& d = ds[k];
+    if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, first + (int)k, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+    ctx->inst.push_back(d);
+    if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
+    ctx->inst_ready.push_back(0);
+  }
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
   ctx->work_dirty = true;
   drop_graph(ctx);
   ctx->merged_fresh = false;
-  if (instance_id) *instance_id = id;
+  return 0;
+}
+
+}  // namespace
+
+int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id) {
+  const double* Jp[1] = {J};
+  const double* hp[1] = {h};
+  return qis_create_instances(ctx, 1, &n, Jp, hp, instance_id);
+}
+
+int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* const* J, const double* const* h,
+                         int* instance_ids) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (count < 0 || (count > 0 && (!n || !J || !h))) return fail(ctx, QIS_ERR_INVALID_ARG, "bad arrays");
+  if (count == 0) return 0;
+  const int first = (int)ctx->inst.size();
+  for (int k = 0; k < count; ++k) {
+    const int rc = check_instance_args(ctx, first + k, n[k], J[k], h[k]);
+    if (rc) return rc;
+  }
+  CK(cudaSetDevice(ctx->cfg.device));
+  // every copy and validation first, then one read-back of all statistics
+  for (int k = 0; k < count; ++k) {
+    const int rc = upload_instance(ctx, first + k, k, n[k], J[k], h[k]);
+    if (rc) return rc;
+  }
+  const size_t stride = (size_t)ctx->NP + 8;
+  std::vector<double> st(stride * count);
+  CK(cudaMemcpyAsync(st.data(), ctx->stats, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<InstDesc> ds(count);
+  for (int k = 0; k < count; ++k) {
+    const int rc = describe_instance(ctx, first + k, n[k], st.data() + stride * k, ds[k]);
+    if (rc) return rc;   // no instance of the batch is added
+  }
+  const int rc = register_instances(ctx, first, ds);
+  if (rc) return rc;
+  if (instance_ids)
+    for (int k = 0; k < count; ++k) instance_ids[k] = first + k;
   return 0;
 }
 
@@ -581,9 +646,9 @@ int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
   CK(cudaMemcpyAsync(ctx->P.init_bits + (size_t)d.first_search * Wm, h.data(), h.size() * sizeof(uint64_t),
                      cudaMemcpyHostToDevice, ctx->stream));
   LAUNCH(launch_init_search(ctx->P, d.first_search, R, ctx->stream));
+  // no synchronisation: a copy from pageable host memory has left `h` once it returns
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
-  CK(cudaStreamSynchronize(ctx->stream));
   return 0;
 }
 
@@ -1020,12 +1085,17 @@ int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, do
   if (!ctx->merged_fresh) {
     LAUNCH(launch_final_merge(ctx->P, s));
     ctx->merged_fresh = true;
+    ctx->counts_valid = false;
   }
-  int rc = sync_and_check(ctx);
-  if (rc) return rc;
+  if (!ctx->counts_valid) {   // once per merge: the status check and every instance's count
+    int rc = sync_and_check(ctx);
+    if (rc) return rc;
+    ctx->mrg_counts.assign(ctx->inst.size(), 0);
+    CK(cudaMemcpy(ctx->mrg_counts.data(), ctx->P.mrg_count, sizeof(int) * ctx->inst.size(), cudaMemcpyDeviceToHost));
+    ctx->counts_valid = true;
+  }
   const InstDesc& d = ctx->inst[instance_id];
-  int cnt = 0;
-  CK(cudaMemcpy(&cnt, ctx->P.mrg_count + instance_id, sizeof(int), cudaMemcpyDeviceToHost));
+  const int cnt = ctx->mrg_counts[instance_id];
   const int m = k < cnt ? k : cnt;
   for (int off = 0; off < m; off += ctx->scratch_states) {
     const int c = (m - off < ctx->scratch_states) ? m - off : ctx->scratch_states;
@@ -1037,10 +1107,11 @@ int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, do
     if (bits_out) CK(cudaMemcpyAsync(bits_out + (size_t)off * d.W, ctx->scratch_bits, sizeof(uint64_t) * c * d.W,
                                      cudaMemcpyDeviceToHost, s));
     if (E_out) CK(cudaMemcpyAsync(E_out + off, ctx->scratch_E, sizeof(double) * c, cudaMemcpyDeviceToHost, s));
+    if (src_out && off == 0)
+      CK(cudaMemcpyAsync(src_out, ctx->P.mrg_src + (size_t)instance_id * ctx->K1, sizeof(uint64_t) * m,
+                         cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
-  if (src_out && m > 0)
-    CK(cudaMemcpy(src_out, ctx->P.mrg_src + (size_t)instance_id * ctx->K1, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost));
   if (n_out) *n_out = m;
   return 0;
 }
@@ -1051,6 +1122,7 @@ int qis_merge(qis_ctx* ctx) {
   CK(cudaSetDevice(ctx->cfg.device));
   LAUNCH(launch_final_merge(ctx->P, ctx->stream));
   ctx->merged_fresh = true;
+  ctx->counts_valid = false;
   return 0;
 }
 

@@ -281,6 +281,7 @@ cudaError_t mlp_propose_states(qis_mlp* m, const double* J64, long long stride, 
 int mlp_max_n(const qis_mlp* m);
 
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
+cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cudaStream_t s);
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,

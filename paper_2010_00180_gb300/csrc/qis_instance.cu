@@ -6,6 +6,8 @@
 //   J4   fl32(4 * Jq * 2^-q): the candidate filter's coupling term
 //   D16  Jq written in balanced base-4096 digits, Jq = sum_d 4096^d D_d, D_d in [-2048, 2047],
 //        one FP16 plane per digit (every digit is an exact FP16 integer)
+#include <algorithm>
+
 #include "qis_common.cuh"
 
 namespace qis {
@@ -68,6 +70,24 @@ cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat
   cudaMemsetAsync(stats, 0, 4 * sizeof(double), s);
   const int np = pad_of(n);
   k_validate<<<(n + 127) / 128, 128, 0, s>>>(P.J64 + off_mat, P.h64 + off_vec, n, np, stats);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- padded layout
+// J (n x n, contiguous, as copied from the host) into the padded n_pad x n_pad plane; zeros
+// past n.
+__global__ void k_restride(const double* src, int n, int n_pad, double* dst) {
+  const long long total = (long long)n_pad * n_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n_pad), j = (int)(e % n_pad);
+    dst[e] = (i < n && j < n) ? src[(long long)i * n + j] : 0.0;
+  }
+}
+
+cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cudaStream_t s) {
+  const long long total = (long long)n_pad * n_pad;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  k_restride<<<blocks, 256, 0, s>>>(src, n, n_pad, dst);
   return cudaGetLastError();
 }
 
@@ -185,31 +205,69 @@ cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s,
 // ---------------------------------------------------------------- FP64 rescoring
 // E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i from scratch in FP64 (one block per state;
 // thread t owns rows t, t+256, ...; fixed reduction tree, so the result is reproducible).
-__global__ void __launch_bounds__(256) k_rescore(const double* J64, const double* h64, int n, int n_pad,
-                                                 const uint64_t* states, int Wn, double* E_out) {
-  const uint64_t* bits = states + (long long)blockIdx.x * Wn;
-  __shared__ double red[256];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double* row = J64 + (long long)i * n_pad;
-    double r = 0.0;
-    for (int j = i + 1; j < n; ++j) r += sigma_of(bits, j) ? -row[j] : row[j];
-    r += h64[i];
-    acc += sigma_of(bits, i) ? -r : r;
-  }
-  red[threadIdx.x] = acc;
+// One block per state: the state's bits staged in shared memory; warp w takes rows w, w+8, ...
+// and its lanes the columns j > i of a row (coalesced, several loads in flight), s_i times the
+// partial row sum accumulated per lane; block reduction at the end.
+template <typename T>
+__device__ __forceinline__ T block_sum256(T v, T* red) {
+  red[threadIdx.x] = v;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) E_out[blockIdx.x] = red[0];
+  return red[0];
+}
+
+__global__ void __launch_bounds__(256) k_rescore(const double* J64, const double* h64, int n, int n_pad,
+                                                 const uint64_t* states, int Wn, double* E_out) {
+  __shared__ uint64_t sb[kMaxN / 64];
+  __shared__ double red[256];
+  for (int w = threadIdx.x; w < Wn; w += blockDim.x) sb[w] = states[(long long)blockIdx.x * Wn + w];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc = 0.0;
+  for (int i = warp; i < n; i += 8) {
+    const double* row = J64 + (long long)i * n_pad;
+    double r = (lane == 0) ? h64[i] : 0.0;
+#pragma unroll 4
+    for (int j = i + 1 + lane; j < n; j += 32) r += sigma_of(sb, j) ? -row[j] : row[j];
+    acc += sigma_of(sb, i) ? -r : r;
+  }
+  const double E = block_sum256(acc, red);
+  if (threadIdx.x == 0) E_out[blockIdx.x] = E;
+}
+
+// The same energy from the exact fixed-point couplings (split modes, instances on their grid
+// 2^-q): E 2^q = sum_{i<j} s_i s_j Jq_ij + sum_i s_i hq_i in int64, exact, so E = (E 2^q) 2^-q
+// is the value every FP64 summation order of these grid numbers gives (their partial sums are
+// exact), at integer instead of FP64 throughput.
+__global__ void __launch_bounds__(256) k_rescore_q(const long long* Jq, const long long* hq, int n, int n_pad,
+                                                   double inv_scale, const uint64_t* states, int Wn, double* E_out) {
+  __shared__ uint64_t sb[kMaxN / 64];
+  __shared__ long long red[256];
+  for (int w = threadIdx.x; w < Wn; w += blockDim.x) sb[w] = states[(long long)blockIdx.x * Wn + w];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long acc = 0;
+  for (int i = warp; i < n; i += 8) {
+    const long long* row = Jq + (long long)i * n_pad;
+    long long r = (lane == 0) ? hq[i] : 0;
+#pragma unroll 4
+    for (int j = i + 1 + lane; j < n; j += 32) r += sigma_of(sb, j) ? -row[j] : row[j];
+    acc += sigma_of(sb, i) ? -r : r;
+  }
+  const long long Eq = block_sum256(acc, red);
+  if (threadIdx.x == 0) E_out[blockIdx.x] = (double)Eq * inv_scale;
 }
 
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  k_rescore<<<count, 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, bits, Wn, E_out);
+  if (P.mode != QIS_FP64 && !d.rounded)
+    k_rescore_q<<<count, 256, 0, s>>>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, d.inv_scale, bits, Wn, E_out);
+  else
+    k_rescore<<<count, 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, bits, Wn, E_out);
   return cudaGetLastError();
 }
 

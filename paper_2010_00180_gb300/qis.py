@@ -19,7 +19,8 @@ PRECISIONS = {"fp64": QIS_FP64, "split_bf16": QIS_SPLIT_BF16, "pm1_fp8": QIS_PM1
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "CAPACITY", -6: "STATE"}
 
 # the entry points of include/qis.h
-SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_clear_instances",
+SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_create_instances",
+           "qis_clear_instances",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
            "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs",
@@ -75,6 +76,7 @@ def load():
         "qis_destroy": (None, [P]),
         "qis_last_error": (C.c_char_p, [P]),
         "qis_create_instance": (I, [P, I, P, P, C.POINTER(I)]),
+        "qis_create_instances": (I, [P, I, P, P, P, P]),
         "qis_clear_instances": (I, [P]),
         "qis_instance_info": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "qis_init_states": (I, [P, I, P]),
@@ -191,6 +193,24 @@ class Context:
         self._check(self.lib.qis_create_instance(self.h, n, _ptr(J), _ptr(h), C.byref(iid)))
         self.n[iid.value] = n
         return iid.value
+
+    def create_instances(self, pairs) -> list:
+        """Add several instances [(J, h), ...] with one validation read-back (qis_create_instances)."""
+        Js = [np.ascontiguousarray(J, dtype=np.float64) for J, _ in pairs]
+        hs = [np.ascontiguousarray(h, dtype=np.float64) for _, h in pairs]
+        cnt = len(Js)
+        if cnt == 0:
+            return []
+        ns = np.array([h.shape[0] for h in hs], dtype=np.int32)
+        for J, n in zip(Js, ns):
+            assert J.shape == (n, n)
+        Jp = (C.c_void_p * cnt)(*[J.ctypes.data for J in Js])
+        hp = (C.c_void_p * cnt)(*[h.ctypes.data for h in hs])
+        ids = np.zeros(cnt, dtype=np.int32)
+        self._check(self.lib.qis_create_instances(self.h, cnt, _ptr(ns), Jp, hp, _ptr(ids)))
+        for iid, n in zip(ids, ns):
+            self.n[int(iid)] = int(n)
+        return [int(i) for i in ids]
 
     def clear_instances(self):
         self._check(self.lib.qis_clear_instances(self.h))

@@ -1,0 +1,104 @@
+"""Batched instance creation (one validation read-back for many instances) and the exact
+integer rescoring of grid instances: the same instances, descriptors and searches as one call
+per instance; an invalid member adds nothing; energies equal numpy's FP64 ones."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2010_00180_gb300 import build, inputs as I, qis
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    qis.load()
+
+
+def energy_np(J, h, S):
+    return np.einsum("mi,ij,mj->m", S, np.triu(J, 1), S) + S @ h
+
+
+@pytest.mark.parametrize("prec,ens", [("split_bf16", "gaussian"), ("pm1_fp8", "pm1"), ("fp64", "gaussian")])
+def test_batch_equals_one_by_one(prec, ens):
+    ns, K, R, iters = [90, 150, 64, 121], 24, 6, 20
+    data = [I.instance(ens, n, seed=400, inst=k) for k, n in enumerate(ns)]
+    phis = [I.random_states(n, R, seed=401, inst=k) for k, n in enumerate(ns)]
+    out = []
+    for batched in (True, False):
+        ctx = qis.Context(K=K, R=R, precision=prec, max_n=max(ns), max_instances=len(ns))
+        if batched:
+            ids = ctx.create_instances(data)
+        else:
+            ids = [ctx.create_instance(J, h) for J, h in data]
+        assert ids == list(range(len(ns)))
+        infos = [ctx.instance_info(k) for k in ids]
+        for k in ids:
+            ctx.init_states(k, phis[k])
+        ctx.iterate(iters)
+        lists = [[ctx.search_list(k, r) for r in range(R)] for k in ids]
+        tops = [ctx.topk_states(k, K + 1) for k in ids]
+        out.append((infos, lists, tops))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    for k in range(len(ns)):
+        for r in range(R):
+            for key in ("count", "bits", "E", "stamp", "used"):
+                assert np.array_equal(out[0][1][k][r][key], out[1][1][k][r][key]), (k, r, key)
+        for key in ("count", "bits", "E", "src"):
+            assert np.array_equal(out[0][2][k][key], out[1][2][k][key]), (k, key)
+    # and the searches are the oracle's
+    J, h = data[1]
+    for r in range(R):
+        ref = O.qi_search(J, h, K, iters, phis[1][r])
+        got = out[0][1][1][r]
+        assert np.array_equal(got["bits"], ref["bits"][: ref["count"]])
+
+
+def test_invalid_member_adds_nothing():
+    ctx = qis.Context(K=8, R=2, precision="split_bf16", max_n=40, max_instances=4)
+    good = I.instance("gaussian", 30, seed=410)
+    J, h = I.instance("gaussian", 30, seed=411)
+    J = J.copy()
+    J[3, 5] += 1.0   # no longer symmetric
+    with pytest.raises(qis.QISError) as e:
+        ctx.create_instances([good, (J, h), good])
+    assert e.value.name == "INVALID_ARG"
+    assert ctx.create_instances([good]) == [0]   # nothing of the failed batch was added
+    ctx.close()
+
+
+@pytest.mark.parametrize("ens", ["gaussian", "uniform", "pm1"])
+def test_exact_rescoring_equals_fp64_energies(ens):
+    """Grid instances are rescored in exact integers; the result is the FP64 energy (every
+    partial sum of grid numbers is exact), for any summation order."""
+    n = 200
+    prec = "pm1_fp8" if ens == "pm1" else "split_bf16"
+    J, h = I.instance(ens, n, seed=420)
+    ctx = qis.Context(K=8, R=2, precision=prec, max_n=n, max_instances=1)
+    ctx.create_instance(J, h)
+    assert ctx.instance_info(0)[2] == 0   # on its grid: not rounded
+    bits = I.random_states(n, 300, seed=421)
+    E = ctx.energies(0, bits)
+    S = 1.0 - 2.0 * I.unpack_bits(bits, n).astype(np.float64)
+    assert np.array_equal(E, energy_np(J, h, S))
+    ctx.close()
+
+
+def test_rounded_instance_keeps_fp64_rescoring():
+    """Couplings off any usable grid are rounded for the search, but energies are still the
+    FP64 energies of the given couplings."""
+    n = 60
+    rng = np.random.default_rng(430)
+    J = np.triu(rng.standard_normal((n, n)), 1)
+    J = J + J.T
+    h = rng.standard_normal(n)
+    ctx = qis.Context(K=8, R=2, precision="split_bf16", max_n=n, max_instances=1)
+    ctx.create_instance(J, h)
+    assert ctx.instance_info(0)[2] == 1
+    bits = I.random_states(n, 50, seed=431)
+    E = ctx.energies(0, bits)
+    S = 1.0 - 2.0 * I.unpack_bits(bits, n).astype(np.float64)
+    np.testing.assert_allclose(E, energy_np(J, h, S), rtol=1e-12, atol=1e-12)
+    ctx.close()
