@@ -573,6 +573,9 @@ int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* co
   CK(cudaStreamSynchronize(ctx->stream));
   std::vector<InstDesc> ds(count);
   for (int k = 0; k < count; ++k) {
+    double sh = 0.0;   // sum_i |h_i| in index order
+    for (int i = 0; i < n[k]; ++i) sh += fabs(h[k][i]);
+    st[stride * k + 4 + n[k]] = sh;
     const int rc = describe_instance(ctx, first + k, n[k], st.data() + stride * k, ds[k]);
     if (rc) return rc;   // no instance of the batch is added
   }

@@ -14,53 +14,66 @@ namespace qis {
 
 // ---------------------------------------------------------------- validation
 // stats layout (doubles): [0] bad flags (as bits of an int), [1] max frac bits, [2] max|J| bits,
-// [3] max|h| bits, [4 .. 4+n) row sums sum_{j>i} |J_ij| in j order, [4+n] sum_i |h_i|.
+// [3] max|h| bits, [4 .. 4+n) row sums sum_{j>i} |J_ij|; the host adds [4+n] = sum_i |h_i|.
+// Fraction bits of x: the smallest f >= 0 with x 2^f an integer, from the bit pattern
+// (|x| = M 2^(e - 1075) with the 53-bit significand M for a normal x, m 2^-1074 for a
+// subnormal one; the lowest set bit of the significand decides).
 __device__ inline int frac_bits(double x) {
-  if (x == 0.0) return 0;
-  int ex;
-  double f = frexp(fabs(x), &ex);                 // |x| = f 2^ex, f in [0.5, 1)
-  unsigned long long M = (unsigned long long)ldexp(f, 53);
-  int tz = __ffsll((long long)M) - 1;
-  int fb = 53 - tz - ex;
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  if (u == 0) return 0;
+  const int e = (int)(u >> 52);
+  const unsigned long long m = u & 0xfffffffffffffull;
+  const int fb = (e == 0) ? 1074 - (__ffsll((long long)m) - 1)
+                          : 1075 - e - (__ffsll((long long)(m | (1ull << 52))) - 1);
   return fb > 0 ? fb : 0;
 }
 
-__global__ void k_validate(const double* J64, const double* h64, int n, int n_pad, double* stats) {
+// One warp per row i (its lanes over the columns, coalesced): finiteness, zero diagonal,
+// bitwise symmetry, fraction bits and max |J_ij| (as the bit patterns of non-negative
+// doubles, which order as integers), and the row sum of |J_ij|, j > i, reduced in a fixed
+// shuffle order (deterministic). Sum of |h| is formed on the host.
+__global__ void __launch_bounds__(256) k_validate(const double* J64, const double* h64, int n, int n_pad, double* stats) {
   int* bad = reinterpret_cast<int*>(stats);
   int* maxfrac = reinterpret_cast<int*>(stats + 1);
   unsigned long long* maxJ = reinterpret_cast<unsigned long long*>(stats + 2);
   unsigned long long* maxh = reinterpret_cast<unsigned long long*>(stats + 3);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const double* row = J64 + (long long)i * n_pad;
-    double rs = 0.0;
-    int fb = 0, b = 0;
-    double mj = 0.0;
-    for (int j = 0; j < n; ++j) {
-      double x = row[j];
-      if (!isfinite(x)) b |= 1;
-      if (j == i) {
-        if (x != 0.0) b |= 2;
-        continue;
-      }
-      if (__double_as_longlong(x) != __double_as_longlong(J64[(long long)j * n_pad + i])) b |= 4;
-      fb = max(fb, frac_bits(x));
-      mj = fmax(mj, fabs(x));
-      if (j > i) rs += fabs(x);
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;   // warp-uniform
+  const double* row = J64 + (long long)i * n_pad;
+  double rs = 0.0;
+  int fb = 0, b = 0;
+  unsigned long long mj = 0;
+  for (int j = lane; j < n; j += 32) {
+    const double x = row[j];
+    const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    if (ax >= 0x7ff0000000000000ull) b |= 1;   // Inf or NaN
+    if (j == i) {
+      if (ax != 0) b |= 2;
+      continue;
     }
-    double hv = h64[i];
-    if (!isfinite(hv)) b |= 8;
+    if (__double_as_longlong(x) != __double_as_longlong(J64[(long long)j * n_pad + i])) b |= 4;
+    fb = max(fb, frac_bits(x));
+    mj = max(mj, ax);
+    if (j > i) rs += fabs(x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    fb = max(fb, __shfl_xor_sync(0xffffffffu, fb, o));
+    mj = max(mj, __shfl_xor_sync(0xffffffffu, mj, o));
+    b |= __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    const double hv = h64[i];
+    const unsigned long long ah = (unsigned long long)__double_as_longlong(hv) & 0x7fffffffffffffffull;
+    if (ah >= 0x7ff0000000000000ull) b |= 8;
     fb = max(fb, frac_bits(hv));
     stats[4 + i] = rs;
     if (b) atomicOr(bad, b);
     atomicMax(maxfrac, fb);
-    atomicMax(maxJ, (unsigned long long)__double_as_longlong(mj));
-    atomicMax(maxh, (unsigned long long)__double_as_longlong(fabs(hv)));
-  }
-  if (i == 0) {
-    double sh = 0.0;
-    for (int k = 0; k < n; ++k) sh += fabs(h64[k]);
-    stats[4 + n] = sh;
+    atomicMax(maxJ, mj);
+    atomicMax(maxh, ah);
   }
 }
 
@@ -69,7 +82,7 @@ cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat
   (void)inst;
   cudaMemsetAsync(stats, 0, 4 * sizeof(double), s);
   const int np = pad_of(n);
-  k_validate<<<(n + 127) / 128, 128, 0, s>>>(P.J64 + off_mat, P.h64 + off_vec, n, np, stats);
+  k_validate<<<(n + 7) / 8, 256, 0, s>>>(P.J64 + off_mat, P.h64 + off_vec, n, np, stats);
   return cudaGetLastError();
 }
 
@@ -142,14 +155,20 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
     E0 = P.init_E[b];
     if (threadIdx.x == 0) red[0] = P.init_q[b];
   } else if (P.mode != QIS_FP64) {
+    // exact E 2^q: a warp per row i, its lanes over the columns j > i (coalesced)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long acc = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = warp; i < n; i += 8) {
       const long long* row = P.Jq + d.off_mat + (long long)i * np;
       const int si = sigma_of(bits, i);
       long long r = 0;
-      for (int j = i + 1; j < n; ++j) r += (si ^ sigma_of(bits, j)) ? -row[j] : row[j];
-      long long hv = P.hq[d.off_vec + i];
-      acc += r + (si ? -hv : hv);
+#pragma unroll 4
+      for (int j = i + 1 + lane; j < n; j += 32) r += (si ^ sigma_of(bits, j)) ? -row[j] : row[j];
+      if (lane == 0) {
+        const long long hv = P.hq[d.off_vec + i];
+        r += si ? -hv : hv;
+      }
+      acc += r;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
