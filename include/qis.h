@@ -172,14 +172,24 @@ int qis_save(qis_ctx* ctx, const char* path);
  * mismatch; QIS_ERR_STATE if the context already holds instances. */
 int qis_load(qis_ctx* ctx, const char* path);
 
-/* Alg. 4 merge of the R lists of an instance followed by FP64 rescoring: the first
+/* Alg. 4 merge of the R lists of an instance followed by rescoring: the first
  * min(k, count) states of the union of the R lists (each state at its first occurrence
  * in search order), ordered by (E, search index, position in that search's list).
- *   bits_out: k*W words; E_out: k energies recomputed from scratch in FP64 from J, h;
+ *   bits_out: k*W words; E_out: k energies recomputed from scratch from J, h (Eq. (1)): in
+ *             exact integer arithmetic for an instance on its grid 2^-q in the split modes
+ *             (the value of any FP64 summation of those grid numbers), else in FP64;
  *   src_out (may be NULL): (r << 32) | position of each state's first occurrence;
  *   n_out: number of states written. */
 int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out,
                     uint64_t* src_out, int* n_out);
+
+/* qis_topk_states for every instance at once (one merge, one rescoring launch, one copy):
+ *   bits_out: n_inst*k*Wmax words, state r of instance i at (i*k + r)*Wmax (Wmax = words of
+ *             max_n; words past the instance's own W are zero);
+ *   E_out, src_out (each may be NULL): n_inst*k values, entry i*k + r;
+ *   n_out (may be NULL): n_inst counts, min(k, merged count of instance i).
+ * 0 <= k <= K+1. Synchronises. */
+int qis_topk_states_all(qis_ctx* ctx, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out, int* n_out);
 
 /* Alg. 4 merge of every instance on the device, asynchronously, into a library buffer
  * that the next qis_topk_states reads without merging again. */

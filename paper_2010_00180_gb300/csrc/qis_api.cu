@@ -46,7 +46,9 @@ struct qis_ctx {
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
   double* stats = nullptr;
-  double* jstage = nullptr;   // [max_n * max_n] one instance's J as copied from the host
+  double* jstage = nullptr;
+  uint64_t* all_bits = nullptr;   // [max_inst][K1][Wmax] every instance's merged states
+  double* all_E = nullptr;        // [max_inst][K1]   // [max_n * max_n] one instance's J as copied from the host
   int4* work = nullptr;    // FP64 scan: 64 x 64 tiles x groups of searches
   int n_work = 0;
   int4* tasks = nullptr;   // FP32 scan: warp tasks (instance, strip, first column, chunk width)
@@ -321,6 +323,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(ctx->zob, kMaxN);
     ALLOC(ctx->stats, (size_t)ctx->max_inst * (NP + 8));   // validation statistics of every instance
     ALLOC(ctx->jstage, (size_t)cfg->max_n * cfg->max_n);
+    ALLOC(ctx->all_bits, (size_t)ctx->max_inst * K1 * W);
+    ALLOC(ctx->all_E, (size_t)ctx->max_inst * K1);
     ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2) *
                          ((ctx->R + kScan64Group - 1) / kScan64Group));
     ctx->tasks_cap = (size_t)ctx->max_inst * (NP / 8) * (NP / 32 + 2);
@@ -1116,6 +1120,36 @@ int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, do
     CK(cudaStreamSynchronize(s));
   }
   if (n_out) *n_out = m;
+  return 0;
+}
+
+int qis_topk_states_all(qis_ctx* ctx, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out, int* n_out) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (k < 0 || k > ctx->K1) return fail(ctx, QIS_ERR_INVALID_ARG, "k must be in [0, K+1]");
+  if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = ctx->stream;
+  if (!ctx->merged_fresh) {
+    LAUNCH(launch_final_merge(ctx->P, s));
+    ctx->merged_fresh = true;
+    ctx->counts_valid = false;
+  }
+  const int ni = (int)ctx->inst.size(), Wm = ctx->Wmax;
+  if (k > 0) LAUNCH(launch_topk_all(ctx->P, k, ctx->all_bits, ctx->all_E, s));
+  int rc = sync_and_check(ctx);
+  if (rc) return rc;
+  ctx->mrg_counts.assign(ni, 0);
+  CK(cudaMemcpy(ctx->mrg_counts.data(), ctx->P.mrg_count, sizeof(int) * ni, cudaMemcpyDeviceToHost));
+  ctx->counts_valid = true;
+  if (k > 0) {
+    if (bits_out) CK(cudaMemcpyAsync(bits_out, ctx->all_bits, sizeof(uint64_t) * (size_t)ni * k * Wm, cudaMemcpyDeviceToHost, s));
+    if (E_out) CK(cudaMemcpyAsync(E_out, ctx->all_E, sizeof(double) * (size_t)ni * k, cudaMemcpyDeviceToHost, s));
+    if (src_out) CK(cudaMemcpy2DAsync(src_out, sizeof(uint64_t) * k, ctx->P.mrg_src, sizeof(uint64_t) * ctx->K1,
+                                      sizeof(uint64_t) * k, ni, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (n_out)
+    for (int i = 0; i < ni; ++i) n_out[i] = std::min(k, ctx->mrg_counts[i]);
   return 0;
 }
 

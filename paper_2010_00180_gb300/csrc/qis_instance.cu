@@ -307,6 +307,58 @@ cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- every instance's merged list
+// Block (inst, r) for r < min(k, count of inst): state r of the merged list, its bits into
+// out[inst][r][Wmax] and its energy rescored as above (exact integers for instances on their
+// grid in the split modes, FP64 otherwise) into E[inst][r].
+__global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, uint64_t* out, double* E) {
+  const int inst = blockIdx.x / k, r = blockIdx.x % k;
+  if (r >= P.mrg_count[inst]) return;
+  const InstDesc d = P.inst[inst];
+  const int ref = P.mrg_ref[inst * P.K1 + r];
+  const int b = ref / P.K1, slot = ref % P.K1;
+  __shared__ uint64_t sb[kMaxN / 64];
+  __shared__ double redd[256];
+  __shared__ long long redq[256];
+  const long long o = ((long long)inst * k + r) * P.Wmax;
+  for (int w = threadIdx.x; w < P.Wmax; w += blockDim.x) {
+    const uint64_t v = (w < d.W) ? P.lst_bits[((long long)b * P.K1 + slot) * P.Wmax + w] : 0ull;
+    sb[w] = v;
+    out[o + w] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = d.n;
+  if (P.mode != QIS_FP64 && !d.rounded) {
+    long long acc = 0;
+    for (int i = warp; i < n; i += 8) {
+      const long long* row = P.Jq + d.off_mat + (long long)i * d.n_pad;
+      long long rr = (lane == 0) ? P.hq[d.off_vec + i] : 0;
+#pragma unroll 4
+      for (int j = i + 1 + lane; j < n; j += 32) rr += sigma_of(sb, j) ? -row[j] : row[j];
+      acc += sigma_of(sb, i) ? -rr : rr;
+    }
+    const long long Eq = block_sum256(acc, redq);
+    if (threadIdx.x == 0) E[(long long)inst * k + r] = (double)Eq * d.inv_scale;
+  } else {
+    double acc = 0.0;
+    for (int i = warp; i < n; i += 8) {
+      const double* row = P.J64 + d.off_mat + (long long)i * d.n_pad;
+      double rr = (lane == 0) ? P.h64[d.off_vec + i] : 0.0;
+#pragma unroll 4
+      for (int j = i + 1 + lane; j < n; j += 32) rr += sigma_of(sb, j) ? -row[j] : row[j];
+      acc += sigma_of(sb, i) ? -rr : rr;
+    }
+    const double Ev = block_sum256(acc, redd);
+    if (threadIdx.x == 0) E[(long long)inst * k + r] = Ev;
+  }
+}
+
+cudaError_t launch_topk_all(const DevPtrs& P, int k, uint64_t* out, double* E, cudaStream_t s) {
+  if (k <= 0 || P.n_inst <= 0) return cudaSuccess;
+  k_topk_all<<<P.n_inst * k, 256, 0, s>>>(P, k, out, E);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- imported lists
 // Zobrist hash of the first `count` slots of search b's list (the bits were copied in by the
 // host): the same key the merge and the dedup use for states generated on the device.

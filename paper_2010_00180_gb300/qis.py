@@ -20,7 +20,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DEVICE_TIMEOUT", -5: "C
 
 # the entry points of include/qis.h
 SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance", "qis_create_instances",
-           "qis_clear_instances",
+           "qis_clear_instances", "qis_topk_states_all",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
            "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs",
@@ -77,6 +77,7 @@ def load():
         "qis_last_error": (C.c_char_p, [P]),
         "qis_create_instance": (I, [P, I, P, P, C.POINTER(I)]),
         "qis_create_instances": (I, [P, I, P, P, P, P]),
+        "qis_topk_states_all": (I, [P, I, P, P, P, P]),
         "qis_clear_instances": (I, [P]),
         "qis_instance_info": (I, [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "qis_init_states": (I, [P, I, P]),
@@ -307,6 +308,23 @@ class Context:
         self._check(self.lib.qis_topk_states(self.h, iid, k, _ptr(bits), _ptr(E), _ptr(src), C.byref(cnt)))
         c = cnt.value
         return dict(bits=bits[:c], E=E[:c], src=src[:c], count=c)
+
+    def topk_states_all(self, k: int) -> list:
+        """topk_states of every instance at once (qis_topk_states_all): one dict per instance."""
+        ni = len(self.n)
+        wm = words(self.cfg.max_n)
+        bits = np.zeros((max(ni * k, 1), wm), np.uint64)
+        E = np.zeros(max(ni * k, 1))
+        src = np.zeros(max(ni * k, 1), np.uint64)
+        cnt = np.zeros(max(ni, 1), np.int32)
+        self._check(self.lib.qis_topk_states_all(self.h, k, _ptr(bits), _ptr(E), _ptr(src), _ptr(cnt)))
+        out = []
+        for i in range(ni):
+            c = int(cnt[i])
+            w = words(self.n[i])
+            out.append(dict(bits=bits[i * k:i * k + c, :w].copy(), E=E[i * k:i * k + c].copy(),
+                            src=src[i * k:i * k + c].copy(), count=c))
+        return out
 
     def merge(self):
         self._check(self.lib.qis_merge(self.h))

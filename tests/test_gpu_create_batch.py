@@ -102,3 +102,22 @@ def test_rounded_instance_keeps_fp64_rescoring():
     S = 1.0 - 2.0 * I.unpack_bits(bits, n).astype(np.float64)
     np.testing.assert_allclose(E, energy_np(J, h, S), rtol=1e-12, atol=1e-12)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,ens", [("split_bf16", "gaussian"), ("fp64", "gaussian"), ("pm1_fp8", "pm1")])
+def test_topk_all_equals_per_instance(prec, ens):
+    ns, K, R, iters = [70, 130, 45], 20, 5, 15
+    ctx = qis.Context(K=K, R=R, precision=prec, max_n=max(ns), max_instances=len(ns))
+    data = [I.instance(ens, n, seed=440, inst=k) for k, n in enumerate(ns)]
+    ctx.create_instances(data)
+    for k, n in enumerate(ns):
+        ctx.init_states(k, I.random_states(n, R, seed=441, inst=k))
+    ctx.iterate(iters)
+    for kk in (K + 1, 7):
+        every = ctx.topk_states_all(kk)
+        for k in range(len(ns)):
+            one = ctx.topk_states(k, kk)
+            assert every[k]["count"] == one["count"]
+            for key in ("bits", "E", "src"):
+                assert np.array_equal(every[k][key], one[key]), (kk, k, key)
+    ctx.close()
