@@ -127,7 +127,9 @@ int qis_instance_n(qis_ctx* ctx, int instance_id, int* n);
  *   bits: R*W words (search r's state at bits + r*W), or NULL to draw every bit from the
  *         library's SplitMix64 stream: bit i of search r of instance id is the top bit of
  *         value (r*n + i) of the stream keyed by key(seed, id), i.e. rand_between(0, 2^n-1)
- *         of Alg. 4. */
+ *         of Alg. 4.
+ * The searches start (initial energies, lists) with one launch for every instance set since,
+ * at the next call that reads or advances them; the caller's buffer is free on return. */
 int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits);
 
 /* Reset every search of every instance to its stored initial state (device-side, no host

@@ -56,6 +56,7 @@ struct qis_ctx {
   size_t tasks_cap = 0;
   bool work_dirty = true;
   bool merged_fresh = false;
+  std::vector<char> init_pending;  // instance whose searches wait for their start (one launch for all)
   bool counts_valid = false;      // mrg_counts holds the counts of the current merge (status checked)
   std::vector<int> mrg_counts;
   uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
@@ -538,6 +539,7 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
     ctx->inst.push_back(d);
     if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
     ctx->inst_ready.push_back(0);
+    ctx->init_pending.push_back(0);
   }
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
@@ -548,6 +550,34 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
 }
 
 }  // namespace
+
+namespace {
+
+// Start (Alg. 3: the initial state as the only list entry) every search whose instance got new
+// initial states since the last flush: one launch per run of consecutive such instances.
+// Called first by every entry point that reads or changes the searches.
+int flush_init(qis_ctx* ctx) {
+  const int ni = (int)ctx->init_pending.size();
+  for (int a = 0; a < ni;) {
+    if (!ctx->init_pending[a]) {
+      ++a;
+      continue;
+    }
+    int e = a;
+    while (e < ni && ctx->init_pending[e]) ctx->init_pending[e++] = 0;
+    LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream));
+    a = e;
+  }
+  return 0;
+}
+
+}  // namespace
+
+#define FLUSH_INIT(ctx)              \
+  do {                               \
+    const int rc_ = flush_init(ctx); \
+    if (rc_) return rc_;             \
+  } while (0)
 
 int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id) {
   const double* Jp[1] = {J};
@@ -604,6 +634,7 @@ int qis_clear_instances(qis_ctx* ctx) {
   }
   ctx->inst.clear();
   ctx->inst_ready.clear();
+  ctx->init_pending.clear();
   ctx->P.n_inst = 0;
   ctx->P.B = 0;
   ctx->work_dirty = true;
@@ -652,8 +683,9 @@ int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
   }
   CK(cudaMemcpyAsync(ctx->P.init_bits + (size_t)d.first_search * Wm, h.data(), h.size() * sizeof(uint64_t),
                      cudaMemcpyHostToDevice, ctx->stream));
-  LAUNCH(launch_init_search(ctx->P, d.first_search, R, ctx->stream));
-  // no synchronisation: a copy from pageable host memory has left `h` once it returns
+  // the searches start at the next entry point that needs them (one launch for every instance
+  // set since); no synchronisation: a copy from pageable host memory has left `h` once it returns
+  ctx->init_pending[instance_id] = 1;
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   return 0;
@@ -672,7 +704,7 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
   CK(mlp_propose_states(m, ctx->J64 + d.off_mat, d.n_pad, ctx->h64 + d.off_vec, d.n, ctx->R, key,
                         ctx->P.init_bits + (size_t)d.first_search * ctx->Wmax, ctx->Wmax, ctx->stream));
   ctx->launches += 5;
-  LAUNCH(launch_init_search(ctx->P, d.first_search, ctx->R, ctx->stream));
+  ctx->init_pending[instance_id] = 1;
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -681,6 +713,7 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
 
 int qis_reset(qis_ctx* ctx) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   for (size_t i = 0; i < ctx->inst.size(); ++i)
     if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
   CK(cudaMemsetAsync(ctx->P.status, 0, sizeof(int), ctx->stream));
@@ -691,6 +724,7 @@ int qis_reset(qis_ctx* ctx) {
 
 int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (n_iters < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "n_iters must be >= 0");
   if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
   for (size_t i = 0; i < ctx->inst.size(); ++i)
@@ -756,6 +790,7 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
 int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double* E, uint8_t* used,
                     uint64_t* stamp, int* count) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
   if (r < 0 || r >= ctx->R) return fail(ctx, QIS_ERR_INVALID_ARG, "bad search index");
   int rc = sync_and_check(ctx);
@@ -789,8 +824,14 @@ namespace {
 
 // Write one search's kept list (entries in key order) into the device list of search b. The
 // caller has validated the arguments; hashes are computed on the device from the bits.
+int flush_init(qis_ctx* ctx);
+
 int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* bits, const double* E,
                   const uint8_t* used, const uint64_t* stamp, int t) {
+  {   // a pending start of the instance's searches comes first (its initial energies stay)
+    const int rc = flush_init(ctx);
+    if (rc) return rc;
+  }
   const int K1 = ctx->K1, Wm = ctx->Wmax;
   const size_t base = (size_t)b * K1;
   std::vector<uint64_t> lb((size_t)K1 * Wm, 0ull), st(K1, 0ull);
@@ -865,6 +906,7 @@ int check_list(qis_ctx* ctx, int n, int count, const uint64_t* bits, const doubl
 int qis_set_search_list(qis_ctx* ctx, int instance_id, int r, int count, const uint64_t* bits, const double* E,
                         const uint8_t* used, const uint64_t* stamp, int t) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
   if (r < 0 || r >= ctx->R) return fail(ctx, QIS_ERR_INVALID_ARG, "bad search index");
   if (t < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "iteration counter must be >= 0");
@@ -928,6 +970,7 @@ struct Reader {
 
 int qis_save(qis_ctx* ctx, const char* path) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (!path) return fail(ctx, QIS_ERR_INVALID_ARG, "path is NULL");
   CK(cudaSetDevice(ctx->cfg.device));
   int rc = sync_and_check(ctx);
@@ -1085,6 +1128,7 @@ int qis_load(qis_ctx* ctx, const char* path) {
 int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out,
                     int* n_out) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (instance_id < 0 || instance_id >= (int)ctx->inst.size()) return fail(ctx, QIS_ERR_INVALID_ARG, "bad instance id");
   if (k < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "k must be >= 0");
   CK(cudaSetDevice(ctx->cfg.device));
@@ -1125,6 +1169,7 @@ int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, do
 
 int qis_topk_states_all(qis_ctx* ctx, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out, int* n_out) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (k < 0 || k > ctx->K1) return fail(ctx, QIS_ERR_INVALID_ARG, "k must be in [0, K+1]");
   if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
   CK(cudaSetDevice(ctx->cfg.device));
@@ -1155,6 +1200,7 @@ int qis_topk_states_all(qis_ctx* ctx, int k, uint64_t* bits_out, double* E_out, 
 
 int qis_merge(qis_ctx* ctx) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
   CK(cudaSetDevice(ctx->cfg.device));
   LAUNCH(launch_final_merge(ctx->P, ctx->stream));
@@ -1182,6 +1228,7 @@ int qis_energies(qis_ctx* ctx, int instance_id, int count, const uint64_t* bits,
 
 int qis_synchronize(qis_ctx* ctx) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   return sync_and_check(ctx);
 }
 
@@ -1194,6 +1241,7 @@ int qis_kernel_launches(qis_ctx* ctx, uint64_t* count) {
 
 int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   CK(cudaStreamSynchronize(ctx->stream));
   uint64_t c[2];
   int rc = count_candidates(ctx, c);
@@ -1205,6 +1253,7 @@ int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
 
 int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs) {
   if (!ctx || !pairs) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  FLUSH_INIT(ctx);
   CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->mode == QIS_FP64) {   // the plain form evaluates every pair
     uint64_t c[2];
@@ -1268,6 +1317,7 @@ int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t) {
 
 int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  FLUSH_INIT(ctx);
   if (iters < 1) return fail(ctx, QIS_ERR_INVALID_ARG, "iters must be >= 1");
   if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
   for (size_t i = 0; i < ctx->inst.size(); ++i)
