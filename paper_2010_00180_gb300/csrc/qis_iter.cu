@@ -24,11 +24,14 @@ namespace qis {
 __device__ inline float fl32_up(double x) { return __double2float_ru(x); }
 
 // ---------------------------------------------------------------- parent pick (Alg. 3)
-__global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
-  const int b = blockIdx.x;
+// One warp per search, four searches per block (more searches resident than with one-warp
+// blocks: the per-search chain of dependent loads is what takes the time).
+__global__ void __launch_bounds__(128) k_pick(DevPtrs P) {
+  const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (b >= P.B) return;   // warp-uniform
   const InstDesc d = P.inst[b / P.R];
   const long long base = (long long)b * P.K1;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   int sel = -1;
   if (P.active[b]) {
     const int cnt = P.lst_count[b];
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(32) k_pick(DevPtrs P) {
 }
 
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s) {
-  k_pick<<<P.B, 32, 0, s>>>(P);
+  k_pick<<<(P.B + 3) / 4, 128, 0, s>>>(P);
   return cudaGetLastError();
 }
 
