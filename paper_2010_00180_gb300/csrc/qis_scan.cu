@@ -201,16 +201,19 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       live64 &= ~(0xffull << (8 * p));
       const int s = u * kPer + p;
       const float cp = (p >> 2) ? cv[1] : cv[0];
-      float aj[NC], sj[NC], am[EX ? NC : 1];
+      // column values: {a_j, s_j}; under exchanges a_j twice, masked by the partner's spin
+      // (every valid pair has s_i s_j = -1, so y = a_j - 4J~ and s_j is not needed)
+      float aj[NC], sj[EX ? 1 : NC], am[EX ? NC : 1];
       {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           const float2 v = sm.col[q][p][32 * k + lane];
-          aj[k] = v.x;
-          sj[k] = v.y;
           if constexpr (EX) {
             aj[k] = (v.y < 0.f) ? v.x : qnan;   // partners of rows with s_i = +1
             am[k] = (v.y > 0.f) ? v.x : qnan;   // partners of rows with s_i = -1
+          } else {
+            aj[k] = v.x;
+            sj[k] = v.y;
           }
         }
       }
@@ -221,12 +224,20 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
           if (!((live >> r) & 1u)) continue;   // uniform
           const float c = __shfl_sync(0xffffffffu, cp, (p & 3) * 8 + r);
           float y[NC];
-          if ((smask >> r) & 1u) {
+          if constexpr (EX) {   // fl(a_j - 4J~): the same rounding as the FMA with s_i s_j = -1
+            if ((smask >> r) & 1u) {
 #pragma unroll
-            for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[k], EX ? am[EX ? k : 0] : aj[k]);
+              for (int k = 0; k < NC; ++k) y[k] = __fsub_rn(am[EX ? k : 0], J[r][k]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < NC; ++k) y[k] = __fsub_rn(aj[k], J[r][k]);
+            }
+          } else if ((smask >> r) & 1u) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) y[k] = fmaf(-J[r][k], sj[EX ? 0 : k], aj[k]);
           } else {
 #pragma unroll
-            for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[k], aj[k]);
+            for (int k = 0; k < NC; ++k) y[k] = fmaf(J[r][k], sj[EX ? 0 : k], aj[k]);
           }
           if (rowmin<NC>(y) <= c) {   // this lane has a hit in row r: which columns
 #pragma unroll
@@ -274,7 +285,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
 // task.x = instance, task.y = first row of the 32-row block, task.z = first column,
 // task.w = NC | (search group << 8); a group is RG consecutive searches of the instance
 template <bool EX>
-__global__ void __launch_bounds__(128, EX ? 4 : 5) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
+__global__ void __launch_bounds__(128, 5) k_scan_pairs(DevPtrs P, const int4* tasks, int n_tasks, int RG) {
   __shared__ ScanRing sm;
   const int4 w = tasks[blockIdx.x];
   const InstDesc d = P.inst[w.x];
