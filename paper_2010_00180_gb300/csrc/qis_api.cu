@@ -396,6 +396,17 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.dup_c, (size_t)B * K1);
     ALLOC(P.dup_n, B);
     ALLOC(P.surv, B * (size_t)ctx->cap);
+    {
+      size_t pc = 256;
+      while (pc < (size_t)ctx->cap) pc <<= 1;
+      ALLOC(P.mrg_scratch, B * 2 * pc);
+      P.merge_cand = 512;
+      const char* e = getenv("QIS_MERGE_SMEM_CAND");
+      if (e) {
+        const int v = atoi(e);
+        if (v >= 32 && v <= 512 && (v & (v - 1)) == 0) P.merge_cand = v;
+      }
+    }
     ALLOC(P.init_bits, B * W);
     ALLOC(P.init_E, B);
     ALLOC(P.init_q, B);

@@ -86,6 +86,8 @@ struct DevPtrs {
   uint32_t* dup_c;        // [b][K1] candidate index of every kept state one or two flips from the parent
   int* dup_n;             // [b] their number
   unsigned long long* surv;  // [b][cap] survivor entries {i, j} (surv_entry; c filled by the merge)
+  int merge_cand;         // kept candidates the merge holds in shared memory (512; power of two)
+  unsigned long long* mrg_scratch;  // [b][2][next_pow2(max(cap, 256))] the merge's keys and entries when they exceed shared memory
   __half* S16;            // +-1 spins of the parents (0 past n), tensor-core operand, tiled (s16_offset)
   long long s16_stride;   // halves of one instance's region of S16
   int gemm_nt;            // searches per tensor-core tile (the S16 tiling)
@@ -301,7 +303,7 @@ cudaError_t launch_scan64(const DevPtrs& P, const int4* work, int n_work, cudaSt
 void scan_tasks_for(int inst, int n, int nc_max, int R, int RG, std::vector<int4>& out);
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_final_merge(const DevPtrs& P, cudaStream_t s);
-size_t merge_smem(int K1, int cap);
+size_t merge_smem(int K1, int cap, int merge_cand);
 size_t final_merge_smem(int K1);
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s);

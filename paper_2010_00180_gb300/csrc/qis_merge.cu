@@ -189,6 +189,13 @@ __device__ inline uint64_t flip_mask(int x, int i, int j) {
 }
 
 constexpr int kMergeThreads = 256;
+// kept candidates held in shared memory: min(next_pow2(max(cap, 256)), P.merge_cand), where
+// merge_cand is 512 (QIS_MERGE_SMEM_CAND, a power of two in [32, 512], lowers it: a test uses
+// it to run the global-memory path)
+__host__ __device__ inline int merge_smem_cand(int cap, int merge_cand) {
+  const int pc = next_pow2(cap > kMergeThreads ? cap : kMergeThreads);
+  return pc < merge_cand ? pc : merge_cand;
+}
 
 __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   const int b = blockIdx.x;
@@ -202,13 +209,21 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
     if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
     return;
   }
-  const int PC = next_pow2(max(P.cap, kMergeThreads));
+  // kept candidates (key, entry): in shared memory for up to kMergeSmemCand of them (the usual
+  // case; a small footprint keeps eight blocks per SM), else in the search's global scratch
+  const int PCs = merge_smem_cand(P.cap, P.merge_cand);
+  const bool big = S > PCs;
   const int HT = next_pow2(2 * K1);
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* okey = reinterpret_cast<unsigned long long*>(smem);   // [K1]
-  unsigned long long* sk = okey + K1;                                       // [PC] keys of valid candidates
-  unsigned long long* se = sk + PC;                                         // [PC] their survivor entries
-  unsigned long long* sk2 = se + PC;                                        // [kMergeThreads] sorted keys
+  unsigned long long* sk = okey + K1;                                       // [PCs] keys of valid candidates
+  unsigned long long* se = sk + PCs;                                        // [PCs] their survivor entries
+  if (big) {
+    const long long stride = next_pow2(max(P.cap, kMergeThreads));
+    sk = P.mrg_scratch + (long long)b * 2 * stride;
+    se = sk + stride;
+  }
+  unsigned long long* sk2 = okey + K1 + 2 * PCs;                            // [kMergeThreads] sorted keys
   unsigned long long* se2 = sk2 + kMergeThreads;                            // [kMergeThreads] sorted entries
   int* oslot = reinterpret_cast<int*>(se2 + kMergeThreads);                 // [K1] slot of old rank r
   uint32_t* htab = reinterpret_cast<uint32_t*>(oslot + K1);                // [HT] duplicate candidates
@@ -309,7 +324,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
       wb = __shfl_sync(0xffffffffu, wb, 0);
       if (keep) {
         const int slot = wb + __popc(bal & ((1u << lane) - 1));
-        sk[slot] = kk;          // slot < S <= cap <= PC
+        sk[slot] = kk;          // slot < S <= the buffer's size
         se[slot] = ent;
         kmn = min(kmn, kk);
         kmx = max(kmx, kk);
@@ -442,13 +457,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
   if (threadIdx.x == 0) P.lst_count[b] = min(K1, cnt + nv);
 }
 
-size_t merge_smem(int K1, int cap) {
-  const int PC = next_pow2(cap > kMergeThreads ? cap : kMergeThreads), HT = next_pow2(2 * K1);
-  return (size_t)K1 * 8 + (size_t)PC * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 4 + (size_t)HT * 4;
+size_t merge_smem(int K1, int cap, int merge_cand) {
+  const int PCs = merge_smem_cand(cap, merge_cand), HT = next_pow2(2 * K1);
+  return (size_t)K1 * 8 + (size_t)PCs * 16 + (size_t)kMergeThreads * 16 + (size_t)K1 * 4 + (size_t)HT * 4;
 }
 
 cudaError_t launch_merge(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = merge_smem(P.K1, P.cap);
+  const size_t sm = merge_smem(P.K1, P.cap, P.merge_cand);
   static size_t attr = 0;
   if (attr < sm) {
     cudaError_t e = cudaFuncSetAttribute(k_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -121,3 +121,28 @@ def test_topk_all_equals_per_instance(prec, ens):
             for key in ("bits", "E", "src"):
                 assert np.array_equal(every[k][key], one[key]), (kk, k, key)
     ctx.close()
+
+
+@pytest.mark.parametrize("smem_cand", ["32", "512"])
+def test_merge_overflow_buffer_pm1_ties(smem_cand, monkeypatch):
+    """+-J couplings with h = 0 tie many candidates at the threshold, so a search keeps more
+    survivors than the merge holds in shared memory (32 slots forced here; 512 is the default):
+    the overflow buffer in global memory must give the same lists as the oracle."""
+    monkeypatch.setenv("QIS_MERGE_SMEM_CAND", smem_cand)
+    n, K, R, iters = 300, 120, 3, 6
+    J, _ = I.instance("pm1", n, seed=450)
+    h = np.zeros(n)
+    phi = I.random_states(n, R, seed=451)
+    ctx = qis.Context(K=K, R=R, precision="pm1_fp8", max_n=n, max_instances=1, survivor_cap=16384)
+    ctx.create_instance(J, h)
+    ctx.init_states(0, phi)
+    for t in range(1, iters + 1):
+        ctx.iterate(1)
+        for r in range(R):
+            ref = O.qi_search(J, h, K, t, phi[r])
+            got = ctx.search_list(0, r)
+            c = ref["count"]
+            assert got["count"] == c
+            for key in ("bits", "E", "used", "stamp"):
+                assert np.array_equal(got[key], ref[key][:c]), (t, r, key)
+    ctx.close()
