@@ -365,7 +365,7 @@ __device__ __forceinline__ long long near_code(const uint64_t* x, const uint64_t
 constexpr int kSubSites = 64;   // at most this many low-a sites in the subset (2080 candidates)
 constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
 
-__global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
+__global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) {
     if (threadIdx.x == 0) {
@@ -404,7 +404,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
   // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory;
   // the range of a_i is taken on the way (a ~ fl32 of the exact value in FP64 mode too: only
   // used to bin sites)
-  float2* as = reinterpret_cast<float2*>(subkey + kSubMax);   // [NP]
+  // [NP], after the subset values: kSubMax FP64 keys in the FP64 mode, kSubMax floats otherwise
+  float2* as = reinterpret_cast<float2*>(subkey + (fp64 ? kSubMax : kSubMax / 2));
   __shared__ float wmn[4], wmx[4];
   {
     float mn = INFINITY, mx = -INFINITY;
@@ -701,7 +702,8 @@ __global__ void __launch_bounds__(128, 8) k_bound(DevPtrs P) {
 }
 
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {
-  const size_t sm = (size_t)kSubMax * 8 + (size_t)P.NP * sizeof(float2);
+  // the split modes keep the subset as floats: a smaller footprint, ten blocks per SM
+  const size_t sm = (size_t)kSubMax * (P.mode == QIS_FP64 ? 8 : 4) + (size_t)P.NP * sizeof(float2);
   static size_t attr = 0;
   if (attr < sm) {
     cudaError_t e = cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -197,7 +197,7 @@ __host__ __device__ inline int merge_smem_cand(int cap, int merge_cand) {
   return pc < merge_cand ? pc : merge_cand;
 }
 
-__global__ void __launch_bounds__(kMergeThreads) k_merge(DevPtrs P) {
+__global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
   const int b = blockIdx.x;
   if (!P.active[b]) return;
   const InstDesc d = P.inst[b / P.R];
