@@ -264,7 +264,7 @@ __device__ float value_select_upper(const float* v, int cnt, int rank, int* hist
 // field GEMM's bit for bit (both exact). A parent without a ring entry of its generator (the
 // initial state, an imported list, a generator more than ring_n iterations back) marks its
 // tensor-core tile, and the GEMM computes that tile in full.
-__global__ void __launch_bounds__(256) k_fields_inc(DevPtrs P) {
+__global__ void __launch_bounds__(256, 8) k_fields_inc(DevPtrs P) {
   const int b = blockIdx.x;
   // every load that depends only on b, issued together
   const int act = P.active[b], t = P.iter_t[b], t0 = P.ring_t0[b];
