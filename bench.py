@@ -260,7 +260,7 @@ def run_ours(args, rank, world, device):
     ctx.close()
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
-                digits=digits)
+                digits=digits, workload=args.workload)
 
 
 def _timed_run(ctx, stream, iters):
@@ -408,14 +408,14 @@ def run_warmstart(args, device=0):
     print(json.dumps(line))
 
 
-def scan_traffic():
+def scan_traffic(workload):
     """DRAM bytes per launch of the candidate scan from its last ncu capture, or None when the
-    kernel source has changed since that capture."""
+    kernel source has changed since that capture or the capture was of another workload."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k_scan_pairs_traffic.json")))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec.get("workload") != workload:
             return None
         return rec["traffic_bytes_per_launch"]
     except Exception:
@@ -470,7 +470,7 @@ def roofline(res, pk):
     peak = 152 * 128 * clk * 1e6 / 1e12
     ev = 2.0 * res["evald"] / max(1, nl) / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": scan_traffic(), "kernel": "k_scan_pairs",
+            "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload")), "kernel": "k_scan_pairs",
             "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch,
             "per_unit": "2 operations per pair candidate decided (signed FMA + compare)",
             "evaluated_ops_per_launch": 2.0 * res["evald"] / max(1, nl), "achieved_evaluated": round(ev, 3),
