@@ -465,17 +465,28 @@ int check_instance_args(qis_ctx* ctx, int id, int n, const double* J, const doub
 
 // Copy J and h of instance id to the device and validate them into stats slot `slot`
 // (asynchronous on the library stream).
-int upload_instance(qis_ctx* ctx, int id, int slot, int n, const double* J, const double* h) {
+// Copy J of instance id to the device (asynchronous on the library stream) as one contiguous
+// block (a pitched copy from pageable memory goes row by row), into `stage`.
+int copy_instance(qis_ctx* ctx, int n, const double* J, double* stage) {
+  CK(cudaMemcpyAsync(stage, J, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, ctx->stream));
+  return 0;
+}
+
+// h of instances first .. first+count-1, zero padded to NP, in one copy (their regions are
+// consecutive). A copy from pageable memory has left `hall` once it returns.
+int copy_fields_h(qis_ctx* ctx, int first, int count, const int* n, const double* const* h) {
+  std::vector<double> hall((size_t)count * ctx->NP, 0.0);
+  for (int k = 0; k < count; ++k) memcpy(hall.data() + (size_t)k * ctx->NP, h[k], sizeof(double) * n[k]);
+  CK(cudaMemcpyAsync(ctx->h64 + (long long)first * ctx->NP, hall.data(), sizeof(double) * hall.size(),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  return 0;
+}
+
+// The padded layout of instance id's J from `stage`, and its validation into stats slot `slot`.
+int lay_out_instance(qis_ctx* ctx, int id, int slot, int n, const double* stage) {
   const long long off_mat = (long long)id * ctx->NP * ctx->NP, off_vec = (long long)id * ctx->NP;
-  const int n_pad = pad_of(n);
   cudaStream_t s = ctx->stream;
-  // one contiguous copy (a pitched copy from pageable memory goes row by row), then the
-  // padded layout on the device; a copy from pageable memory first waits for the stream, so
-  // the staging buffer is free again
-  CK(cudaMemcpyAsync(ctx->jstage, J, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, s));
-  LAUNCH(launch_restride(ctx->jstage, n, n_pad, ctx->J64 + off_mat, s));
-  CK(cudaMemsetAsync(ctx->h64 + off_vec, 0, sizeof(double) * n_pad, s));
-  CK(cudaMemcpyAsync(ctx->h64 + off_vec, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  LAUNCH(launch_restride(stage, n, pad_of(n), ctx->J64 + off_mat, s));
   LAUNCH(launch_validate(ctx->P, id, n, off_mat, off_vec, ctx->stats + (size_t)slot * (ctx->NP + 8), s));
   return 0;
 }
@@ -607,10 +618,31 @@ int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* co
     if (rc) return rc;
   }
   CK(cudaSetDevice(ctx->cfg.device));
-  // every copy and validation first, then one read-back of all statistics
-  for (int k = 0; k < count; ++k) {
-    const int rc = upload_instance(ctx, first + k, k, n[k], J[k], h[k]);
+  // every copy, then every layout and validation, then one read-back of all statistics. In the
+  // split modes each instance is staged in its own region of the fixed-point pool (written
+  // from J64 later), so the copies run back to back; the FP64 mode stages one instance at a
+  // time (a copy from pageable memory first waits for the stream, so the buffer is free again).
+  {
+    const int rc = copy_fields_h(ctx, first, count, n, h);
     if (rc) return rc;
+  }
+  if (ctx->mode != QIS_FP64) {
+    for (int k = 0; k < count; ++k) {
+      double* stage = reinterpret_cast<double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
+      const int rc = copy_instance(ctx, n[k], J[k], stage);
+      if (rc) return rc;
+    }
+    for (int k = 0; k < count; ++k) {
+      const double* stage = reinterpret_cast<const double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
+      const int rc = lay_out_instance(ctx, first + k, k, n[k], stage);
+      if (rc) return rc;
+    }
+  } else {
+    for (int k = 0; k < count; ++k) {
+      int rc = copy_instance(ctx, n[k], J[k], ctx->jstage);
+      if (!rc) rc = lay_out_instance(ctx, first + k, k, n[k], ctx->jstage);
+      if (rc) return rc;
+    }
   }
   const size_t stride = (size_t)ctx->NP + 8;
   std::vector<double> st(stride * count);
