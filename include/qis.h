@@ -59,7 +59,7 @@ typedef struct {
   int K;             /* each search keeps K+1 states (Alg. 2 requires 1 <= K < 2^n) */
   int R;             /* searches (initial states) per instance: L of Alg. 4 */
   int precision;     /* QIS_FP64 | QIS_SPLIT_BF16 | QIS_PM1_FP8 */
-  int max_n;         /* largest n of any instance added to this context (2 <= n <= 4096) */
+  int max_n;         /* largest n of any instance added to this context (2 <= n <= 16384) */
   int max_instances; /* capacity of the instance table */
   int survivor_cap;  /* per-search candidate buffer (0 = default 2048) */
   int device;        /* CUDA device ordinal */

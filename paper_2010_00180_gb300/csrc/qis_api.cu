@@ -269,7 +269,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   *out = nullptr;
   if (cfg->K < 1 || cfg->K + 1 > 4096) return fail(nullptr, QIS_ERR_INVALID_ARG, "K must satisfy 1 <= K and K+1 <= 4096");
   if (cfg->R < 1 || cfg->R > 65536) return fail(nullptr, QIS_ERR_INVALID_ARG, "R must be in [1, 65536]");
-  if (cfg->max_n < 2 || cfg->max_n > kMaxN) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_n must be in [2, 4096]");
+  if (cfg->max_n < 2 || cfg->max_n > kMaxN) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_n must be in [2, 16384]");
   if (cfg->max_instances < 1) return fail(nullptr, QIS_ERR_INVALID_ARG, "max_instances must be >= 1");
   if (cfg->precision != QIS_FP64 && cfg->precision != QIS_SPLIT_BF16 && cfg->precision != QIS_PM1_FP8)
     return fail(nullptr, QIS_ERR_INVALID_ARG, "unknown precision mode");
@@ -323,7 +323,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     }
     ALLOC(ctx->zob, kMaxN);
     ALLOC(ctx->stats, (size_t)ctx->max_inst * (NP + 8));   // validation statistics of every instance
-    ALLOC(ctx->jstage, (size_t)cfg->max_n * cfg->max_n);
+    if (ctx->mode == QIS_FP64) ALLOC(ctx->jstage, (size_t)cfg->max_n * cfg->max_n);   // the split modes stage in Jq
     ALLOC(ctx->all_bits, (size_t)ctx->max_inst * K1 * W);
     ALLOC(ctx->all_E, (size_t)ctx->max_inst * K1);
     ALLOC(ctx->work, (size_t)ctx->max_inst * ((NP / kTile) * (NP / kTile + 1) / 2) *
@@ -538,9 +538,11 @@ int describe_instance(qis_ctx* ctx, int id, int n, const double* st, InstDesc& d
     }
     if (q < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "couplings too large for exact 64-bit energies");
     const double maxJq = ldexp(maxJ, q);
+    const int dbits = (d.n_pad <= 8192) ? 12 : 11;   // exact FP32 partial sums of the digit GEMM
     int digits = 1;
-    while (digits < kMaxDigits && ldexp(1.0, 12 * digits - 1) <= maxJq + 0.5) ++digits;
-    if (ldexp(1.0, 12 * digits - 1) <= maxJq + 0.5) return fail(ctx, QIS_ERR_INVALID_ARG, "coupling range too wide");
+    while (digits < kMaxDigits && ldexp(1.0, dbits * digits - 1) <= maxJq + 0.5) ++digits;
+    if (ldexp(1.0, dbits * digits - 1) <= maxJq + 0.5) return fail(ctx, QIS_ERR_INVALID_ARG, "coupling range too wide");
+    d.dbits = dbits;
     if (ctx->mode == QIS_PM1_FP8) digits = 1;
     d.q = q;
     d.digits = digits;

@@ -13,7 +13,7 @@ namespace qis {
 constexpr int kTile = 64;        // scan tile edge (sites)
 constexpr int kPad = 128;        // n is padded to a multiple of this (tensor-core M tile)
 constexpr int kMaxDigits = 5;    // 12-bit signed digits (base 4096) of the fixed-point couplings
-constexpr int kMaxN = 4096;
+constexpr int kMaxN = 16384;
 constexpr int kScan64Group = 4;  // searches per block of the FP64 pair scan
 
 // Device error flags (bit mask in ctx status word).
@@ -27,7 +27,9 @@ struct InstDesc {
   int n_pad;        // n rounded up to kPad
   int W;            // words per state
   int q;            // fixed-point exponent: Jq = J * 2^q  (-1 in FP64 mode)
-  int digits;       // number of base-4096 digits of Jq
+  int digits;       // number of balanced base-2^dbits digits of Jq
+  int dbits;        // digit width: 12 bits, 11 above n_pad = 8192 (FP32 partial sums of the digit
+                    // GEMM stay below 2^24: |digit| <= 2^(dbits-1), n_pad terms)
   int first_search; // global index of search r = 0 of this instance
   long long off_mat;  // element offset of this instance's n_pad x n_pad matrices
   long long off_vec;  // element offset of this instance's n_pad vectors
@@ -133,17 +135,18 @@ __host__ __device__ inline int pad_of(int n) { return (n + kPad - 1) / kPad * kP
 __host__ __device__ inline uint32_t pair_index(int n, int i, int j) {
   return (uint32_t)n + (uint32_t)((long long)i * n - (long long)i * (i + 1) / 2 + (j - i - 1));
 }
-// Survivor entry: bits 32-43 site i, bits 44-55 site j, bit 56 set for a single flip (no j);
-// n <= 4096 keeps i and j in 12 bits. The candidate filters (singles by k_bound, pairs by the
+// Survivor entry: bits 32-45 site i, bits 46-59 site j, bit 60 set for a single flip (no j);
+// n <= 16384 keeps i and j in 14 bits. The candidate filters (singles by k_bound, pairs by the
 // scans) write the sites only; the merge fills bits 0-31 with the candidate index c (the
 // tie-break of equal energies) when it reads the entry.
+constexpr int kSurvJ = 46;   // bit position of site j
 __host__ __device__ inline unsigned long long surv_entry(int i, int j) {
   return ((unsigned long long)(unsigned)i << 32) |
-         (j < 0 ? (1ull << 56) : ((unsigned long long)(unsigned)j << 44));
+         (j < 0 ? (1ull << 60) : ((unsigned long long)(unsigned)j << kSurvJ));
 }
 __host__ __device__ inline void surv_sites(unsigned long long e, int& i, int& j) {
-  i = (int)((e >> 32) & 0xfffu);
-  j = ((e >> 56) & 1u) ? -1 : (int)((e >> 44) & 0xfffu);
+  i = (int)((e >> 32) & 0x3fffu);
+  j = ((e >> 60) & 1u) ? -1 : (int)((e >> kSurvJ) & 0x3fffu);
 }
 __host__ __device__ inline void surv_decode(unsigned long long e, uint32_t& c, int& i, int& j) {
   c = (uint32_t)e;

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int u = 0; u < 16; ++u) acc[u] += wdig * (long long)__float2int_rn(__uint_as_float(v[u]));
-          wdig *= 4096;
+          wdig <<= d.dbits;
         }
         if (i < d.n_pad) {
 #pragma unroll

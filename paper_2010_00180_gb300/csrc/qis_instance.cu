@@ -107,7 +107,7 @@ cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cu
 // ---------------------------------------------------------------- fixed point + digits
 // D16 holds, per digit and instance, an NP x NP plane in the tiled layout of d16_offset.
 __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pad, int NP, int q, int digits,
-                           long long plane, __half* D16, long long* Jq, float* J4, long long* hq) {
+                           int dbits, long long plane, __half* D16, long long* Jq, float* J4, long long* hq) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)n_pad * n_pad;
   if (e < tot) {
@@ -117,11 +117,12 @@ __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pa
     Jq[e] = v;
     J4[e] = (float)(4.0 * ldexp((double)v, -q));
     long long x = v;
+    const long long base = 1ll << dbits;
     for (int d = 0; d < digits; ++d) {
-      long long r = x & 4095;                 // x mod 4096 in [0, 4095]
-      if (r >= 2048) r -= 4096;               // balanced digit in [-2048, 2047]
+      long long r = x & (base - 1);           // x mod base
+      if (r >= base / 2) r -= base;           // balanced digit in [-base/2, base/2)
       D16[d * plane + d16_offset(i, j, NP)] = __float2half_rn((float)r);
-      x = (x - r) >> 12;                      // exact
+      x = (x - r) >> dbits;                   // exact
     }
   }
   if (e < n_pad) hq[e] = (e < n) ? __double2ll_rn(ldexp(h64[e], q)) : 0;
@@ -131,7 +132,7 @@ cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __hal
                             float* J4, long long* hq, cudaStream_t s) {
   const long long tot = (long long)d.n_pad * d.n_pad;
   k_quantize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, P.NP, d.q, d.digits, P.pool_mat,
+      P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, P.NP, d.q, d.digits, d.dbits, P.pool_mat,
       D16 + (long long)inst * P.NP * P.NP, Jq + d.off_mat, J4 + d.off_mat, hq + d.off_vec);
   return cudaGetLastError();
 }

@@ -383,9 +383,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
   __shared__ int hist[256], hist2[256];
   __shared__ int sites[kSubSites];
-  __shared__ float gmin[kMaxN / 32];   // min a_j of each 32-column group
   __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near;
-  __shared__ uint64_t pb[kMaxN / 64];
   __shared__ float s_thr;
   __shared__ double s_T, s_cap;
   const int cnt = P.lst_count[b];
@@ -406,6 +404,9 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   // used to bin sites)
   // [NP], after the subset values: kSubMax FP64 keys in the FP64 mode, kSubMax floats otherwise
   float2* as = reinterpret_cast<float2*>(subkey + (fp64 ? kSubMax : kSubMax / 2));
+  // then the parent's words and the minimum a_j of each 32-column group (sized by the context)
+  uint64_t* pb = reinterpret_cast<uint64_t*>(as + P.NP);     // [Wmax]
+  float* gmin = reinterpret_cast<float*>(pb + P.Wmax);        // [NP / 32]
   __shared__ float wmn[4], wmx[4];
   {
     float mn = INFINITY, mx = -INFINITY;
@@ -703,7 +704,8 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
 
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {
   // the split modes keep the subset as floats: a smaller footprint, ten blocks per SM
-  const size_t sm = (size_t)kSubMax * (P.mode == QIS_FP64 ? 8 : 4) + (size_t)P.NP * sizeof(float2);
+  const size_t sm = (size_t)kSubMax * (P.mode == QIS_FP64 ? 8 : 4) + (size_t)P.NP * sizeof(float2) +
+                    (size_t)P.Wmax * 8 + (size_t)(P.NP / 32) * 4;
   static size_t attr = 0;
   if (attr < sm) {
     cudaError_t e = cudaFuncSetAttribute(k_bound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

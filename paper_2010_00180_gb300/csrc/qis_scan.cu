@@ -252,7 +252,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
           do {
             const int bit = __ffsll((long long)cm) - 1;
             cm &= cm - 1;
-            if (slot < cap) dst[slot] = e0 + ((unsigned long long)(bit >> 3) << 32) + ((unsigned long long)(bit & 7) << 49);
+            if (slot < cap) dst[slot] = e0 + ((unsigned long long)(bit >> 3) << 32) + ((unsigned long long)(bit & 7) << (kSurvJ + 5));
             ++slot;
           } while (cm);
         }
