@@ -50,6 +50,8 @@ WORKLOADS = {
     # flip-set variants (Sec. V outlook): spin exchanges; single flips only at a larger n
     "gaussian_n600_120x64_exchange": ("gaussian", 600, 120, 120, 64, 120, "split_bf16", "exchange"),
     "gaussian_n2048_32x64_single": ("gaussian", 2048, 32, 120, 64, 120, "split_bf16", "single"),
+    # single flips at the size the Sec. V outlook has in mind (N ~ 10^4)
+    "uniform_n10000_4x64_single": ("uniform", 10000, 4, 120, 64, 120, "split_bf16", "single"),
     # a third of the headline workload (same n, K, R): the size of the full ncu captures
     "gaussian_n600_40x64": ("gaussian", 600, 40, 120, 64, 120, "split_bf16"),
 }
