@@ -11,19 +11,22 @@
 // c0 + 32k + l, so every coupling load is a coalesced 128-byte row segment.
 //
 // Per search the block needs {a_j, s_j} of the chunk's columns and of its rows and a control
-// word; one thread stages them with TMA bulk copies into a ring of kRing slots of kPer
-// searches each (completion counted on the slot's mbarrier). The warps do not synchronise with
-// each other: each waits for its next slot, works through its searches and releases it; the
-// fourth release refills the slot kRing slots ahead. A warp that meets many hits may fall
-// behind the others by up to kRing slots without stalling them.
+// word; one warp stages them with TMA bulk copies (lane p issues search p's three copies) into
+// a ring of kRing slots of kPer searches each (completion counted on the slot's mbarrier). The
+// warps do not synchronise with each other: each waits for its next slot, works through its
+// searches and releases it; the fourth release refills the slot kRing slots ahead. A warp that
+// meets many hits may fall behind the others by up to kRing slots without stalling them.
 //
-// Per search and row (warp-uniform) each lane computes y_ij = fma(+-4J~_ij, s_j, a_j) -- the
-// row spin, taken from a ballot so the branch is provably uniform, picks the operand sign --
-// reduces min_j y_ij with three-input minima and compares it with c_i. Pairs that must not be
-// evaluated (j <= i, j >= n) hold NaN couplings: the FMA propagates NaN and min ignores it.
-// Rows whose c_i lies below a lower bound of every y_ij of the search are skipped whole. When a
-// row's minimum passes, the lane marks which of its columns pass from the same values, and
-// appends one survivor entry per passing pair.
+// Per slot a warp first votes which of its 8 rows can hit, four searches per ballot: every
+// y_ij of the chunk is at least RD(w - max_j |4J~_ij|) (w: minimum a_j over the chunk's
+// 256-column window, from the control word; the row maximum of |4J~| from the coupling
+// registers), so rows with c_i below it are skipped whole. For each live row (warp-uniform)
+// each lane computes y_ij = fma(+-4J~_ij, s_j, a_j) -- the row spin, taken from a ballot so the
+// branch is provably uniform, picks the operand sign -- reduces min_j y_ij with three-input
+// minima and compares it with c_i. Pairs that must not be evaluated (j <= i, j >= n) hold NaN
+// couplings: the FMA propagates NaN and min ignores it. When a row's minimum passes, the lane
+// marks which of its columns pass from the same values, and appends one survivor entry per
+// passing pair.
 #include "qis_common.cuh"
 
 namespace qis {
