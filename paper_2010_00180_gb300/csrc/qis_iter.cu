@@ -2,11 +2,13 @@
 //
 // Per iteration:
 //   k_pick        parent = first unused kept state in key order (Alg. 3), marked used
-//   k_fields_*    local fields of the parent; a_i = -2 s_i f_i (energy change of flip i)
-//   k_bound       per-search filter threshold; single flips dE_i = a_i tested here
+//   k_fields_*    local fields of the parent (by update from its generator's exact fields,
+//                 else the tensor-core GEMM); a_i = -2 s_i f_i (energy change of flip i)
+//   k_bound       per-search filter threshold; single flips dE_i = a_i tested here; the
+//                 candidate indices of the kept states one or two flips from the parent
 //   k_scan_*      pair flips dE_ij = a_i + a_j + 4 s_i s_j J_ij; survivors appended
-//   k_merge       exact energies of the survivors, duplicate removal (Zobrist hash + full
-//                 compare), new list = first K+1 of old list + survivors by (E, stamp)
+//   k_merge       exact energies of the survivors, duplicate removal (by candidate index),
+//                 new list = first K+1 of old list + survivors by (E, stamp)
 //
 // Why a threshold suffices: a candidate enters the list only if its energy is below the
 // last kept energy T (Alg. 2, strict <), and a state that leaves the list never comes back

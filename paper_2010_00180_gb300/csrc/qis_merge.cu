@@ -1,7 +1,8 @@
 // qis_merge.cu -- the exact list update of one iteration (Alg. 2), one block per search.
 //
-// Input: the survivor buffer of the search (entries {c, i, j} of the single flips from k_bound
-// and of the pairs that passed the scan's filter). Output: the new kept list.
+// Input: the survivor buffer of the search (entries {i, j} of the single flips from k_bound
+// and of the pairs that passed the scan's filter; the candidate index c is added here).
+// Output: the new kept list.
 //
 //  1. Every candidate gets its exact energy: in the split modes from exact fixed-point
 //     integers, E'q = E_pq + aq_i (+ aq_j + 4 s_i s_j Jq_ij), compared as integers with the
