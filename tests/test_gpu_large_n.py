@@ -63,3 +63,20 @@ def test_pairs_n5000_wide_sites():
     assert top["count"] == ref["count"]
     assert np.array_equal(top["bits"], ref["bits"][: ref["count"]])
     ctx.close()
+
+
+def test_single_flips_maximum_size():
+    """n = 16384, the largest instance a context takes (max_n): a few iterations equal the
+    oracle."""
+    n, K, R, iters = 16384, 8, 1, 3
+    J, h = grid_instance(n, 520, 18)
+    phi = I.random_states(n, R, seed=521)
+    ctx = qis.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=1, flips="single")
+    ctx.create_instance(J, h)
+    assert not ctx.instance_info(0)[2]
+    ctx.init_states(0, phi)
+    ctx.iterate(iters)
+    same(ctx.search_list(0, 0), O.qi_search(J, h, K, iters, phi[0], flips=1))
+    ctx.close()
+    with pytest.raises(qis.QISError):
+        qis.Context(K=K, R=R, precision="split_bf16", max_n=n + 1, max_instances=1)
