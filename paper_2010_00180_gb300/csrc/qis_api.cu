@@ -42,6 +42,7 @@ struct qis_ctx {
   float* J4 = nullptr;
   __half* D16 = nullptr;
   int digits_used = 1;     // most digits of any instance (sizes the tensor-core pipeline)
+  bool dense_scan = false;   // QIS_DENSE_SCAN=1: the register-tile pair scan at every size
   bool fields_simt = false;  // QIS_FIELDS_SIMT=1: exact int64 SIMT fields instead of tcgen05
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
@@ -211,6 +212,8 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
     // no pair candidates: nothing to scan
   } else if (ctx->mode == QIS_FP64) {
     LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
+  } else if (!ctx->dense_scan && P.NP <= kSparseMaxNP) {
+    LAUNCH(launch_scan_sparse(P, s));   // output-sensitive: work proportional to the survivors
   } else {
     LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R, s));
   }
@@ -298,6 +301,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
   {
     const char* e = getenv("QIS_FIELDS_SIMT");
     ctx->fields_simt = e && e[0] == '1';
+    const char* ds = getenv("QIS_DENSE_SCAN");
+    ctx->dense_scan = ds && ds[0] == '1';
     const char* g = getenv("QIS_NO_GRAPH");
     ctx->use_graph = !(g && g[0] == '1');
   }
@@ -387,6 +392,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
       ALLOC(P.amin64, B);
     }
     ALLOC(P.thr32, B);
+    ALLOC(P.amin32, B);
+    if (ctx->mode != QIS_FP64) ALLOC(P.rm4, (size_t)ctx->pool_vec);
     if (ctx->mode != QIS_FP64) {
       ALLOC(P.sctl, B * (size_t)(NP / 32));
     }
@@ -559,7 +566,10 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
   CK(cudaMemcpyAsync(ctx->inst_d + first, ds.data(), sizeof(InstDesc) * ds.size(), cudaMemcpyHostToDevice, s));
   for (size_t k = 0; k < ds.size(); ++k) {
     const InstDesc& d = ds[k];
-    if (ctx->mode != QIS_FP64) LAUNCH(launch_quantize(ctx->P, d, first + (int)k, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+    if (ctx->mode != QIS_FP64) {
+      LAUNCH(launch_quantize(ctx->P, d, first + (int)k, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+      LAUNCH(launch_rowmax4(ctx->P, d, s));
+    }
     ctx->inst.push_back(d);
     if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
     ctx->inst_ready.push_back(0);

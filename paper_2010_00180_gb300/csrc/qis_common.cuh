@@ -80,6 +80,8 @@ struct DevPtrs {
   float2* as32;           // [b][n_pad] {fl32(a_i), s_i} (split modes)
   double* a64;            // [b][n_pad] FP64 a_i (FP64 mode)
   float* thr32;           // [b] scan threshold on dE (split modes)
+  float* amin32;          // [b] min_i fl32(a_i) of the parent (split modes; the sparse scan's row bound)
+  float* rm4;             // [off_vec + i] max_j |4J~_ij| of row i (split modes, per instance)
   float4* sctl;           // [b][NP/32] scan control word per 32-column group (k_bound)
   double* thrE;           // [b] FP64 mode: E' must be < thrE[b] ...
   double* capE;           // [b] ... and <= capE[b]
@@ -287,6 +289,9 @@ int mlp_max_n(const qis_mlp* m);
 
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
 cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cudaStream_t s);
+cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s);
+cudaError_t launch_scan_sparse(const DevPtrs& P, cudaStream_t s);
+constexpr int kSparseMaxNP = 4096;   // the sparse pair scan's largest padded n (shared-memory lists)
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,

@@ -137,6 +137,25 @@ cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __hal
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- row maxima of the filter couplings
+// rm4_i = max_j |4J~_ij| (the FP32 couplings of the scan), a warp per row.
+__global__ void __launch_bounds__(256) k_rowmax4(const float* J4, int n, int n_pad, float* rm4) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n_pad) return;   // warp-uniform
+  float m = 0.f;
+  if (i < n)
+    for (int j = lane; j < n; j += 32) m = fmaxf(m, fabsf(J4[(long long)i * n_pad + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) rm4[i] = m;
+}
+
+cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s) {
+  k_rowmax4<<<(d.n_pad + 7) / 8, 256, 0, s>>>(P.J4 + d.off_mat, d.n, d.n_pad, P.rm4 + d.off_vec);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- search initialisation
 // Alg. 3 initial list: [psi0, K placeholders], E(psi0) from Eq. (1), nothing used.
 // Split modes: E0 = (sum_{i<j} Jq_ij s_i s_j + sum_i hq_i s_i) 2^-q in exact int64.

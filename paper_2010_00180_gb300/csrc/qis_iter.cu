@@ -664,6 +664,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
       const double t2 = U + 2.0 * delta;
       s_thr = fl32_up(fmin(t1, t2));
       P.thr32[b] = s_thr;
+      P.amin32[b] = amin;
     }
   }
   __syncthreads();

@@ -312,6 +312,155 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- output-sensitive pair scan
+// The same filter decided per search with work proportional to its answer (the pruning of the
+// Sec. III dE form): for a pair i < j, y_ij = fl(a_j +- 4J~_ij) >= RD(a_j - rm_i) with rm_i =
+// max_j |4J~_ij| (rounding is monotone), so
+//   - row i can hit only if c_i = fl32(thr - a_i) >= RD(amin - rm_i)  (the live rows), and
+//   - with the columns sorted by a_j, row i's candidates are the prefix RD(a_j - rm_i) <= c_i.
+// Every pair outside those prefixes fails y_ij <= c_i, and every pair inside is tested with
+// exactly the dense scan's arithmetic, so the survivors are the same set. One block per search:
+// stage {a_j, s_j}; list the live rows and a column cut B (no prefix reaches past it); sort the
+// columns a_j <= B by (a_j, j); prefix lengths by binary search; then the flat list of
+// (row, column) prefix pairs, one thread each.
+__device__ __forceinline__ uint32_t fkey32(float x) {   // order-preserving key of a finite float
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey32_inv(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+template <bool EX>
+__global__ void __launch_bounds__(128) k_scan_sparse(DevPtrs P) {
+  const int b = blockIdx.x;
+  if (!P.active[b]) return;
+  const InstDesc d = P.inst[b / P.R];
+  const int n = d.n, NP = P.NP, NP2 = next_pow2(P.NP);
+  const float thr = P.thr32[b], amin = P.amin32[b];
+  extern __shared__ unsigned long long ck[];                   // [NP2] sorted column keys
+  float2* sa = reinterpret_cast<float2*>(ck + NP2);           // [NP] {a_j, s_j}
+  int* li = reinterpret_cast<int*>(sa + NP);                  // [NP] live rows
+  int* pc = li + NP;                                          // [NP + 1] prefix offsets
+  __shared__ int s_nl, s_nc, s_tot;
+  __shared__ double wB[4];
+  const float2* g = P.as32 + (long long)b * NP;
+  const float* rm = P.rm4 + d.off_vec;
+  if (threadIdx.x == 0) {
+    s_nl = 0;
+    s_nc = 0;
+  }
+  __syncthreads();
+  // 1. stage; live rows; the column cut B = max over live rows of nextup(c_i) + rm_i (a_j at
+  //    or above it fails every live row: RD(a_j - rm_i) <= c_i implies a_j - rm_i < nextup(c_i);
+  //    the sum of two floats is exact in FP64)
+  double bl = -INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float2 v = g[i];
+    sa[i] = v;
+    const float c = __fsub_rn(thr, v.x), r = rm[i];
+    if (c >= __fsub_rd(amin, r)) {
+      li[atomicAdd(&s_nl, 1)] = i;
+      bl = fmax(bl, (double)nextafterf(c, INFINITY) + (double)r);   // exact; +inf for c = +inf
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bl = fmax(bl, __shfl_xor_sync(0xffffffffu, bl, o));
+  if ((threadIdx.x & 31) == 0) wB[threadIdx.x >> 5] = bl;
+  __syncthreads();
+  const int nl = s_nl;
+  if (nl == 0) return;   // block-uniform
+  const double B = fmax(fmax(wB[0], wB[1]), fmax(wB[2], wB[3]));
+  // 2. columns below the cut, keyed (a_j, j), sorted ascending (bitonic, padded with ~0)
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if ((double)sa[j].x < B) ck[atomicAdd(&s_nc, 1)] = ((unsigned long long)fkey32(sa[j].x) << 32) | (unsigned)j;
+  __syncthreads();
+  const int nc = s_nc, m2 = next_pow2(max(nc, 2));
+  for (int k = nc + threadIdx.x; k < m2; k += blockDim.x) ck[k] = ~0ull;
+  __syncthreads();
+  for (int kk = 2; kk <= m2; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < m2; t += blockDim.x) {
+        const int u = t ^ jj;
+        if (u > t) {
+          const unsigned long long x = ck[t], y = ck[u];
+          if ((x > y) == ((t & kk) == 0)) {
+            ck[t] = y;
+            ck[u] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // 3. prefix length of each live row: the columns with RD(a_j - rm_i) <= c_i
+  for (int r = threadIdx.x; r < nl; r += blockDim.x) {
+    const int i = li[r];
+    const float c = __fsub_rn(thr, sa[i].x), rr = rm[i];
+    int lo = 0, hi = nc;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__fsub_rd(fkey32_inv((uint32_t)(ck[mid] >> 32)), rr) <= c) lo = mid + 1; else hi = mid;
+    }
+    pc[r] = lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {   // exclusive offsets (nl is small: the live rows)
+    int acc = 0;
+    for (int r = 0; r < nl; ++r) {
+      const int v = pc[r];
+      pc[r] = acc;
+      acc += v;
+    }
+    pc[nl] = acc;
+    s_tot = acc;
+  }
+  __syncthreads();
+  // 4. the prefix pairs, one thread each; a pair is tested in the row of its smaller site
+  const int tot = s_tot, cap = P.cap;
+  const float* J4 = P.J4 + d.off_mat;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    int lo = 0, hi = nl;   // the row r with pc[r] <= t < pc[r + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pc[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int i = li[lo];
+    const int j = (int)(uint32_t)ck[t - pc[lo]];
+    if (j <= i) continue;
+    const float2 vi = sa[i], vj = sa[j];
+    if (EX && (vi.y == vj.y)) continue;   // exchanges: opposite spins only
+    const float c = __fsub_rn(thr, vi.x);
+    const float j4 = J4[(long long)i * d.n_pad + j];
+    float y;
+    if constexpr (EX) y = __fsub_rn(vj.x, j4);   // s_i s_j = -1: the dense scan's value
+    else y = fmaf(vi.y < 0.f ? -j4 : j4, vj.y, vj.x);
+    if (y <= c) {
+      const int slot = atomicAdd(P.surv_cnt + b, 1);
+      if (slot < cap) P.surv[(long long)b * cap + slot] = surv_entry(i, j);
+    }
+  }
+}
+
+size_t scan_sparse_smem(int NP) {
+  return (size_t)next_pow2(NP) * 8 + (size_t)NP * 8 + (size_t)NP * 4 + (size_t)(NP + 1) * 4;
+}
+
+cudaError_t launch_scan_sparse(const DevPtrs& P, cudaStream_t s) {
+  const size_t sm = scan_sparse_smem(P.NP);
+  static size_t attr[2] = {0, 0};
+  const int ex = P.flips == QIS_FLIPS_EXCHANGE;
+  if (attr[ex] < sm) {
+    cudaError_t e = ex ? cudaFuncSetAttribute(k_scan_sparse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                       : cudaFuncSetAttribute(k_scan_sparse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr[ex] = sm;
+  }
+  if (ex) k_scan_sparse<true><<<P.B, 128, sm, s>>>(P);
+  else k_scan_sparse<false><<<P.B, 128, sm, s>>>(P);
+  return cudaGetLastError();
+}
+
 // Host: cover the pairs (i < j) of an n-spin instance with block tasks. Block a holds rows
 // [32a, 32a+32); its w = n - 32a columns (from 32a: the 32 x 32 diagonal block is masked inside
 // the task) are split into m = ceil(w / (32 nc_max)) chunks of equal width 32 NC,
