@@ -11,8 +11,9 @@ run I iterations of Alg. 3 on all 7680 searches, merge the R lists of every inst
   e2e    the same metric through the C ABI with host buffers: each step copies J, h and
          the initial states to the device, iterates, and copies back the merged K+1 states
          of every instance with FP64 energies
-  roofline  the candidate-scan kernel against the SM issue rate (2 ALU operations per
-         pair candidate: signed add and compare)
+  roofline  the candidate-scan kernel: the output-sensitive scan (one block per search)
+         against HBM bandwidth (12 bytes per site and search + 4 bytes per pair tested); the
+         dense tile scan against the SM issue rate (2 ALU operations per pair candidate)
   cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores)
 
 --impl reference times the oracle (the CPU reference of this tier) on the same metric.
@@ -259,10 +260,11 @@ def run_ours(args, rank, world, device):
                    h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
     clocks = clk.summary(device)
     digits = ctx.instance_info(0)[1] if n_inst else 0
+    pair_scan = ctx.tuning()["pair_scan"]   # 1 output-sensitive, 2 dense tiles (or the FP64 form)
     ctx.close()
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
-                digits=digits, workload=args.workload)
+                digits=digits, workload=args.workload, pair_scan=pair_scan)
 
 
 def _timed_run(ctx, stream, iters):
@@ -410,12 +412,12 @@ def run_warmstart(args, device=0):
     print(json.dumps(line))
 
 
-def scan_traffic(workload):
-    """DRAM bytes per launch of the candidate scan from its last ncu capture, or None when the
+def scan_traffic(workload, kernel):
+    """DRAM bytes per launch of a scan kernel from its last ncu capture, or None when the
     kernel source has changed since that capture or the capture was of another workload."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "k_scan_pairs_traffic.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec.get("workload") != workload:
             return None
@@ -446,7 +448,8 @@ def roofline_bound(res, pk, src):
 
 
 def roofline(res, pk):
-    """Candidate scan (dominant kernel) against the SM issue rate."""
+    """Candidate scan (dominant kernel): the output-sensitive scan against HBM bandwidth, the
+    dense tile scan against the SM issue rate, the plain FP64 form against the FP64 rate."""
     ms, nl = res["prof"]["scan"]
     if nl == 0 or ms <= 0:
         return None
@@ -465,14 +468,35 @@ def roofline(res, pk):
                 "per_unit": "6 FP64-pipe operations per pair candidate decided (3 adds, 1 multiply, 2 compares)",
                 "peak_source": "nominal FP64 rate (no measured FP64 peak on this pool)",
                 "note": "rows whose FP64 lower bound fails are decided without per-pair work"}
-    ops_per_launch = 2.0 * pairs_per_launch       # signed add + compare per pair candidate
     dur = ms / nl / 1e3
+    if res.get("pair_scan") == 1:
+        # output-sensitive scan: one block per search reads {a_j, s_j} and rm_j of every site and
+        # one coupling 4J~_ij per pair tested (survivor writes not counted)
+        if res["flips"] == "single_pair":
+            searches = pairs_per_launch / (n * (n - 1) / 2)      # active searches per launch
+        else:
+            searches = float(n_inst * R)
+        tested = res["evald"] / max(1, nl)
+        bytes_per_launch = searches * 12.0 * n + 4.0 * tested
+        achieved = bytes_per_launch / dur / 1e9
+        peak = float(pk.get("hbm_gbs", 6800.0))
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload"), "k_scan_sparse"),
+                "kernel": "k_scan_sparse", "launch_us": round(dur * 1e6, 2),
+                "bytes_per_launch": bytes_per_launch, "searches_per_launch": round(searches, 1),
+                "tested_pairs_per_launch": tested,
+                "per_unit": "12 bytes per site and search ({a_j, s_j}, rm_j) + 4 bytes per pair tested (4J~_ij)",
+                "decided_pairs_per_s": pairs_per_launch / dur,
+                "note": "one block per search: a chain of short dependent steps (staging, live rows, sort, "
+                        "prefixes, tests); neither DRAM nor the issue rate is near its peak"}
+    ops_per_launch = 2.0 * pairs_per_launch       # signed add + compare per pair candidate
     achieved = ops_per_launch / dur / 1e12
     clk = pk.get("sm_max_mhz", 2070.0)
     peak = 152 * 128 * clk * 1e6 / 1e12
     ev = 2.0 * res["evald"] / max(1, nl) / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload")), "kernel": "k_scan_pairs",
+            "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload"), "k_scan_pairs"),
+            "kernel": "k_scan_pairs",
             "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch,
             "per_unit": "2 operations per pair candidate decided (signed FMA + compare)",
             "evaluated_ops_per_launch": 2.0 * res["evald"] / max(1, nl), "achieved_evaluated": round(ev, 3),

@@ -219,18 +219,28 @@ int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles);
  *   scan_search_group: searches of an instance per scan task (0 = all R; smaller groups
  *                  give more, shorter tasks for few instances);
  *   gemm_tile_searches: searches per tensor-core tile of the local-field GEMM (multiple of
- *                  16, at most 256, digits * it <= 512; 0 = automatic). */
+ *                  16, at most 256, digits * it <= 512; 0 = automatic);
+ *   pair_scan:     which form of the split modes' FP32 pair filter runs: 1 = output-sensitive
+ *                  (one block per search: the live rows c_i >= RD(min_j a_j - rm_i), with
+ *                  rm_i = max_j |4J~_ij|, and each live row's prefix of the columns sorted by
+ *                  a_j; needs a padded size of at most 4096), 2 = dense register tiles (shaped
+ *                  by scan_chunk_nc and scan_search_group), 0 = automatic (1 where allowed,
+ *                  else 2; the environment variable QIS_DENSE_SCAN=1 makes 2 the default).
+ *                  Both give the same survivor set. QIS_FP64 scans every pair in its plain
+ *                  FP64 form whatever this says; qis_get_tuning reports 2 there. */
 typedef struct {
   int scan_chunk_nc;
   int scan_search_group;
   int gemm_tile_searches;
+  int pair_scan;
 } qis_tuning;
 
 /* Current launch shapes (automatic values resolved). */
 int qis_get_tuning(qis_ctx* ctx, qis_tuning* out);
 
 /* Set the launch shapes for the current and later instances. QIS_ERR_INVALID_ARG for values
- * out of range or a scan task list larger than the context holds (the setting is unchanged). */
+ * out of range, pair_scan 1 where the output-sensitive scan cannot run (QIS_FP64, padded size
+ * above 4096) or a scan task list larger than the context holds (the setting is unchanged). */
 int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t);
 
 /* Autotuner: times `iters` iterations from the initial states for candidate launch shapes
@@ -254,7 +264,9 @@ int qis_set_incremental_fields(qis_ctx* ctx, int on);
  * split modes the scan skips every row whose bound c_i = thr - a_i lies below a lower bound
  * of all its pair terms, and counts (rows evaluated) x (chunk width, masked entries
  * included); in QIS_FP64 every pair is evaluated (the qis_candidate_count pairs). The pairs
- * of qis_candidate_count are all decided exactly either way. Synchronises the stream. */
+ * of qis_candidate_count are all decided exactly either way. The output-sensitive scan
+ * (pair_scan 1) counts the pairs it tests one by one (those in the live rows' prefixes, each
+ * once). Synchronises the stream. */
 int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs);
 
 /* The library's CUDA stream (a cudaStream_t), so callers can order their own work and

@@ -42,7 +42,6 @@ struct qis_ctx {
   float* J4 = nullptr;
   __half* D16 = nullptr;
   int digits_used = 1;     // most digits of any instance (sizes the tensor-core pipeline)
-  bool dense_scan = false;   // QIS_DENSE_SCAN=1: the register-tile pair scan at every size
   bool fields_simt = false;  // QIS_FIELDS_SIMT=1: exact int64 SIMT fields instead of tcgen05
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
@@ -67,7 +66,7 @@ struct qis_ctx {
   uint64_t cand_acc[2] = {0, 0};
   // tunables (results never depend on them): scan chunk width 32 * tune_nc columns, searches
   // per scan task (0 = all R of the instance), searches per GEMM tile (0 = automatic)
-  qis_tuning tune{8, 0, 0};  // candidates of instances removed by qis_clear_instances
+  qis_tuning tune{8, 0, 0, 0};  // candidates of instances removed by qis_clear_instances
   // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
   bool profiling = false;
   bool use_graph = true;                    // QIS_NO_GRAPH=1 launches the kernels one by one
@@ -193,6 +192,11 @@ cudaError_t prof_end(qis_ctx* ctx, int k) {
 }
 
 // The five kernels of one iteration of Alg. 3 (each bracketed by timing events when profiling).
+// The output-sensitive pair scan runs in the split modes up to a padded size of 4096 (its
+// per-search shared-memory arrays), by default or when asked for; the dense tiles otherwise.
+static bool sparse_allowed(const qis_ctx* ctx) { return ctx->mode != QIS_FP64 && ctx->NP <= kSparseMaxNP; }
+static bool sparse_scan(const qis_ctx* ctx) { return sparse_allowed(ctx) && ctx->tune.pair_scan != 2; }
+
 int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   const DevPtrs& P = ctx->P;
   CK(prof_begin(ctx, 0));
@@ -212,7 +216,7 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
     // no pair candidates: nothing to scan
   } else if (ctx->mode == QIS_FP64) {
     LAUNCH(launch_scan64(P, ctx->work, ctx->n_work, s));
-  } else if (!ctx->dense_scan && P.NP <= kSparseMaxNP) {
+  } else if (sparse_scan(ctx)) {
     LAUNCH(launch_scan_sparse(P, s));   // output-sensitive: work proportional to the survivors
   } else {
     LAUNCH(launch_scan_pairs(P, ctx->tasks, ctx->n_tasks, ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R, s));
@@ -302,7 +306,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     const char* e = getenv("QIS_FIELDS_SIMT");
     ctx->fields_simt = e && e[0] == '1';
     const char* ds = getenv("QIS_DENSE_SCAN");
-    ctx->dense_scan = ds && ds[0] == '1';
+    if (ds && ds[0] == '1') ctx->tune.pair_scan = 2;   // the register-tile pair scan by default
     const char* g = getenv("QIS_NO_GRAPH");
     ctx->use_graph = !(g && g[0] == '1');
   }
@@ -1328,6 +1332,7 @@ int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs) {
 int qis_get_tuning(qis_ctx* ctx, qis_tuning* out) {
   if (!ctx || !out) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
   *out = ctx->tune;
+  out->pair_scan = sparse_scan(ctx) ? 1 : 2;
   if (out->scan_search_group == 0) out->scan_search_group = ctx->R;
   if (out->gemm_tile_searches == 0) out->gemm_tile_searches = gemm_tile_n(ctx->R, ctx->digits_used);
   return 0;
@@ -1353,6 +1358,9 @@ int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t) {
   const int nt = t->gemm_tile_searches;
   if (nt != 0 && (nt % 16 != 0 || nt < 16 || nt > 256 || ctx->digits_used * nt > 512))
     return fail(ctx, QIS_ERR_INVALID_ARG, "gemm_tile_searches must be a multiple of 16 in [16, 256] with digits * it <= 512");
+  if (t->pair_scan < 0 || t->pair_scan > 2) return fail(ctx, QIS_ERR_INVALID_ARG, "pair_scan must be 0, 1 or 2");
+  if (t->pair_scan == 1 && !sparse_allowed(ctx))
+    return fail(ctx, QIS_ERR_INVALID_ARG, "the output-sensitive scan needs a split mode and a padded size <= 4096");
   CK(cudaSetDevice(ctx->cfg.device));
   CK(cudaStreamSynchronize(ctx->stream));
   const qis_tuning old = ctx->tune;
@@ -1418,13 +1426,21 @@ int qis_autotune(qis_ctx* ctx, int iters, qis_tuning* best, double* best_ms) {
       rc = r;
     }
   };
-  // coordinate search: chunk width, search group, GEMM tile, each with the others fixed
+  // coordinate search: scan form, then chunk width and search group (the dense form's
+  // shapes), GEMM tile, each with the others fixed
+  cur.pair_scan = sparse_scan(ctx) ? 1 : 2;
+  if (sparse_allowed(ctx)) {
+    qis_tuning t = cur;
+    t.pair_scan = 3 - cur.pair_scan;
+    consider(t);
+  }
   for (int nc : {8, 6, 4, 2}) {
+    if (cur.pair_scan == 1) break;
     qis_tuning t = cur;
     t.scan_chunk_nc = nc;
     if (nc != cur.scan_chunk_nc) consider(t);
   }
-  for (int div = 2; div <= 16; div *= 2) {
+  for (int div = 2; div <= 16 && cur.pair_scan != 1; div *= 2) {
     qis_tuning t = cur;
     t.scan_search_group = (ctx->R + div - 1) / div;
     if (t.scan_search_group >= 4 && t.scan_search_group != cur.scan_search_group) consider(t);

@@ -321,8 +321,12 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 // Every pair outside those prefixes fails y_ij <= c_i, and every pair inside is tested with
 // exactly the dense scan's arithmetic, so the survivors are the same set. One block per search:
 // stage {a_j, s_j}; list the live rows and a column cut B (no prefix reaches past it); sort the
-// columns a_j <= B by (a_j, j); prefix lengths by binary search; then the flat list of
-// (row, column) prefix pairs, one thread each.
+// columns a_j < B by (a_j, j) (by rank when at most 256, else bitonic); prefix lengths by binary
+// search and a block scan; then the flat list of (row, column) prefix pairs, one thread each,
+// their coupling loads issued four at a time, survivors appended with one atomic per warp. The
+// per-search work is a few live rows times their prefixes (about 2000 pairs a search for
+// n = 600, K = 120, against n(n-1)/2 = 179700), so the kernel is a chain of short dependent
+// steps: the loads it cannot avoid are grouped so that each step waits once.
 __device__ __forceinline__ uint32_t fkey32(float x) {   // order-preserving key of a finite float
   const uint32_t u = __float_as_uint(x);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -332,114 +336,198 @@ __device__ __forceinline__ float fkey32_inv(uint32_t k) {
 }
 
 template <bool EX>
-__global__ void __launch_bounds__(128) k_scan_sparse(DevPtrs P) {
+__global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
+  constexpr int SB = 5;   // sites staged per thread and pass (n = 600: one pass)
+  constexpr int PB = 4;   // prefix pairs per thread and pass (their coupling loads issued together)
   const int b = blockIdx.x;
   if (!P.active[b]) return;
   const InstDesc d = P.inst[b / P.R];
-  const int n = d.n, NP = P.NP, NP2 = next_pow2(P.NP);
+  const int n = d.n, NP = P.NP, NP2 = next_pow2(P.NP), tid = threadIdx.x, lane = tid & 31;
   const float thr = P.thr32[b], amin = P.amin32[b];
-  extern __shared__ unsigned long long ck[];                   // [NP2] sorted column keys
+  extern __shared__ unsigned long long ck[];                   // [NP2] column keys
   float2* sa = reinterpret_cast<float2*>(ck + NP2);           // [NP] {a_j, s_j}
   int* li = reinterpret_cast<int*>(sa + NP);                  // [NP] live rows
-  int* pc = li + NP;                                          // [NP + 1] prefix offsets
-  __shared__ int s_nl, s_nc, s_tot;
+  int* pc = li + NP;                                          // [NP + 1] rm of each live row, then prefix offsets
+  __shared__ int s_nl, s_nc, s_w[4];
   __shared__ double wB[4];
   const float2* g = P.as32 + (long long)b * NP;
   const float* rm = P.rm4 + d.off_vec;
-  if (threadIdx.x == 0) {
+  // 1. stage {a, s} (the first pass's loads are issued before the first barrier); live rows;
+  //    the column cut B = max over live rows of nextup(c_i) + rm_i (a_j at or above it fails
+  //    every live row: RD(a_j - rm_i) <= c_i implies a_j - rm_i < nextup(c_i); the sum of two
+  //    floats is exact in FP64)
+  float2 v[SB];
+  float r[SB];
+#pragma unroll
+  for (int u = 0; u < SB; ++u) {
+    const int i = tid + u * 128;
+    if (i < n) {
+      v[u] = g[i];
+      r[u] = rm[i];
+    }
+  }
+  if (tid == 0) {
     s_nl = 0;
     s_nc = 0;
   }
   __syncthreads();
-  // 1. stage; live rows; the column cut B = max over live rows of nextup(c_i) + rm_i (a_j at
-  //    or above it fails every live row: RD(a_j - rm_i) <= c_i implies a_j - rm_i < nextup(c_i);
-  //    the sum of two floats is exact in FP64)
   double bl = -INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float2 v = g[i];
-    sa[i] = v;
-    const float c = __fsub_rn(thr, v.x), r = rm[i];
-    if (c >= __fsub_rd(amin, r)) {
-      li[atomicAdd(&s_nl, 1)] = i;
-      bl = fmax(bl, (double)nextafterf(c, INFINITY) + (double)r);   // exact; +inf for c = +inf
+  for (int base = 0; base < n; base += SB * 128) {
+    if (base > 0) {
+#pragma unroll
+      for (int u = 0; u < SB; ++u) {
+        const int i = base + tid + u * 128;
+        if (i < n) {
+          v[u] = g[i];
+          r[u] = rm[i];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SB; ++u) {
+      const int i = base + tid + u * 128;
+      if (i < n) {
+        sa[i] = v[u];
+        const float c = __fsub_rn(thr, v[u].x);
+        if (c >= __fsub_rd(amin, r[u])) {
+          const int q = atomicAdd(&s_nl, 1);
+          li[q] = i;
+          pc[q] = __float_as_int(r[u]);
+          bl = fmax(bl, (double)nextafterf(c, INFINITY) + (double)r[u]);   // exact; +inf for c = +inf
+        }
+      }
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) bl = fmax(bl, __shfl_xor_sync(0xffffffffu, bl, o));
-  if ((threadIdx.x & 31) == 0) wB[threadIdx.x >> 5] = bl;
+  if (lane == 0) wB[tid >> 5] = bl;
   __syncthreads();
   const int nl = s_nl;
   if (nl == 0) return;   // block-uniform
   const double B = fmax(fmax(wB[0], wB[1]), fmax(wB[2], wB[3]));
-  // 2. columns below the cut, keyed (a_j, j), sorted ascending (bitonic, padded with ~0)
-  for (int j = threadIdx.x; j < n; j += blockDim.x)
+  // 2. columns below the cut, keyed (a_j, j) (distinct keys), sorted ascending: by rank into
+  //    the upper half of the key array when they are few, else bitonic in place
+  for (int j = tid; j < n; j += 128)
     if ((double)sa[j].x < B) ck[atomicAdd(&s_nc, 1)] = ((unsigned long long)fkey32(sa[j].x) << 32) | (unsigned)j;
   __syncthreads();
-  const int nc = s_nc, m2 = next_pow2(max(nc, 2));
-  for (int k = nc + threadIdx.x; k < m2; k += blockDim.x) ck[k] = ~0ull;
-  __syncthreads();
-  for (int kk = 2; kk <= m2; kk <<= 1) {
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int t = threadIdx.x; t < m2; t += blockDim.x) {
-        const int u = t ^ jj;
-        if (u > t) {
-          const unsigned long long x = ck[t], y = ck[u];
-          if ((x > y) == ((t & kk) == 0)) {
-            ck[t] = y;
-            ck[u] = x;
+  const int nc = s_nc;
+  const unsigned long long* cs = ck;
+  if (nc <= 256 && 2 * nc <= NP2) {   // block-uniform
+    unsigned long long* out = ck + NP2 / 2;
+    for (int t = tid; t < nc; t += 128) {
+      const unsigned long long x = ck[t];
+      int rk = 0;
+#pragma unroll 4
+      for (int k = 0; k < nc; ++k) rk += ck[k] < x;
+      out[rk] = x;
+    }
+    cs = out;
+  } else {
+    const int m2 = next_pow2(max(nc, 2));
+    for (int k = nc + tid; k < m2; k += 128) ck[k] = ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= m2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int t = tid; t < m2; t += 128) {
+          const int u = t ^ jj;
+          if (u > t) {
+            const unsigned long long x = ck[t], y = ck[u];
+            if ((x > y) == ((t & kk) == 0)) {
+              ck[t] = y;
+              ck[u] = x;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
   // 3. prefix length of each live row: the columns with RD(a_j - rm_i) <= c_i
-  for (int r = threadIdx.x; r < nl; r += blockDim.x) {
-    const int i = li[r];
-    const float c = __fsub_rn(thr, sa[i].x), rr = rm[i];
+  for (int q = tid; q < nl; q += 128) {
+    const int i = li[q];
+    const float c = __fsub_rn(thr, sa[i].x), rr = __int_as_float(pc[q]);
     int lo = 0, hi = nc;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (__fsub_rd(fkey32_inv((uint32_t)(ck[mid] >> 32)), rr) <= c) lo = mid + 1; else hi = mid;
+      if (__fsub_rd(fkey32_inv((uint32_t)(cs[mid] >> 32)), rr) <= c) lo = mid + 1; else hi = mid;
     }
-    pc[r] = lo;
+    pc[q] = lo;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {   // exclusive offsets (nl is small: the live rows)
-    int acc = 0;
-    for (int r = 0; r < nl; ++r) {
-      const int v = pc[r];
-      pc[r] = acc;
-      acc += v;
+  // exclusive offsets: each thread a run of consecutive rows, then a warp and a block scan
+  {
+    const int per = (nl + 127) >> 7, q0 = min(nl, tid * per), q1 = min(nl, q0 + per);
+    int sum = 0;
+    for (int q = q0; q < q1; ++q) sum += pc[q];
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
     }
-    pc[nl] = acc;
-    s_tot = acc;
+    if (lane == 31) s_w[tid >> 5] = inc;
+    __syncthreads();
+    int acc = inc - sum;
+    for (int w = 0; w < (tid >> 5); ++w) acc += s_w[w];
+    for (int q = q0; q < q1; ++q) {
+      const int x = pc[q];
+      pc[q] = acc;
+      acc += x;
+    }
   }
   __syncthreads();
-  // 4. the prefix pairs, one thread each; a pair is tested in the row of its smaller site
-  const int tot = s_tot, cap = P.cap;
+  // 4. the prefix pairs, one thread each, PB at a time; a pair is tested in the row of its
+  //    smaller site; survivors appended with one atomic per warp
+  const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3], cap = P.cap;
   const float* J4 = P.J4 + d.off_mat;
-  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    int lo = 0, hi = nl;   // the row r with pc[r] <= t < pc[r + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (pc[mid] <= t) lo = mid; else hi = mid;
+  unsigned long long* surv = P.surv + (long long)b * cap;
+  int nev = 0;
+  for (int t0 = 0; t0 < tot; t0 += PB * 128) {   // block-uniform trip count
+    float cv[PB], av[PB], pv[PB], jv[PB];
+    int ij[PB];
+    bool ok[PB];
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int t = t0 + u * 128 + tid;
+      ok[u] = false;
+      if (t < tot) {
+        int lo = 0, hi = nl;   // the row q with pc[q] <= t < pc[q + 1]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (pc[mid] <= t) lo = mid; else hi = mid;
+        }
+        const int i = li[lo], j = (int)(uint32_t)cs[t - pc[lo]];
+        const float2 vi = sa[i], vj = sa[j];
+        ij[u] = i | (j << 16);   // n <= 16384
+        cv[u] = __fsub_rn(thr, vi.x);
+        av[u] = vj.x;
+        pv[u] = vi.y * vj.y;   // s_i s_j
+        ok[u] = j > i && (!EX || pv[u] < 0.f);   // exchanges: opposite spins only
+        if (ok[u]) jv[u] = J4[(long long)i * d.n_pad + j];
+      }
     }
-    const int i = li[lo];
-    const int j = (int)(uint32_t)ck[t - pc[lo]];
-    if (j <= i) continue;
-    const float2 vi = sa[i], vj = sa[j];
-    if (EX && (vi.y == vj.y)) continue;   // exchanges: opposite spins only
-    const float c = __fsub_rn(thr, vi.x);
-    const float j4 = J4[(long long)i * d.n_pad + j];
-    float y;
-    if constexpr (EX) y = __fsub_rn(vj.x, j4);   // s_i s_j = -1: the dense scan's value
-    else y = fmaf(vi.y < 0.f ? -j4 : j4, vj.y, vj.x);
-    if (y <= c) {
-      const int slot = atomicAdd(P.surv_cnt + b, 1);
-      if (slot < cap) P.surv[(long long)b * cap + slot] = surv_entry(i, j);
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      bool hit = false;
+      if (ok[u]) {
+        ++nev;
+        hit = fmaf(pv[u], jv[u], av[u]) <= cv[u];   // fl(a_j + s_i s_j 4J~_ij): the dense scan's value
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(P.surv_cnt + b, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const int slot = base + __popc(m & ((1u << lane) - 1u));
+        if (hit && slot < cap) surv[slot] = surv_entry(ij[u] & 0xffff, ij[u] >> 16);
+      }
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
+  if (lane == 0 && nev) atomicAdd(P.eval_cnt + (b & 63), (unsigned long long)nev);
 }
 
 size_t scan_sparse_smem(int NP) {

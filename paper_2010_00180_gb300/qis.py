@@ -47,7 +47,8 @@ class MLPConfig(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("scan_chunk_nc", C.c_int), ("scan_search_group", C.c_int), ("gemm_tile_searches", C.c_int)]
+    _fields_ = [("scan_chunk_nc", C.c_int), ("scan_search_group", C.c_int), ("gemm_tile_searches", C.c_int),
+                ("pair_scan", C.c_int)]
 
 
 class Config(C.Structure):
@@ -274,8 +275,10 @@ class Context:
         self._check(self.lib.qis_get_tuning(self.h, C.byref(t)))
         return {k: getattr(t, k) for k, _ in Tuning._fields_}
 
-    def set_tuning(self, scan_chunk_nc: int = 8, scan_search_group: int = 0, gemm_tile_searches: int = 0):
-        t = Tuning(scan_chunk_nc, scan_search_group, gemm_tile_searches)
+    def set_tuning(self, scan_chunk_nc: int = 8, scan_search_group: int = 0, gemm_tile_searches: int = 0,
+                   pair_scan: int = 0):
+        """pair_scan: 1 output-sensitive, 2 dense register tiles, 0 automatic."""
+        t = Tuning(scan_chunk_nc, scan_search_group, gemm_tile_searches, pair_scan)
         self._check(self.lib.qis_set_tuning(self.h, C.byref(t)))
 
     def set_incremental_fields(self, on: bool):
