@@ -198,6 +198,7 @@ static bool sparse_allowed(const qis_ctx* ctx) { return ctx->mode != QIS_FP64 &&
 static bool sparse_scan(const qis_ctx* ctx) { return sparse_allowed(ctx) && ctx->tune.pair_scan != 2; }
 
 int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
+  ctx->P.dense_ctl = !sparse_scan(ctx);   // the output-sensitive scan reads no control words
   const DevPtrs& P = ctx->P;
   CK(prof_begin(ctx, 0));
   LAUNCH(launch_pick(P, s));

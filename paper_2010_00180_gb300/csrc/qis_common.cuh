@@ -45,6 +45,7 @@ struct DevPtrs {
   int n_inst, R, K1, Wmax, cap, mode, B;
   int NP;                 // row stride of per-search site arrays (max n_pad)
   int flips;              // QIS_FLIPS_*: the candidate set
+  int dense_ctl;          // 1: k_bound writes the dense pair scan's control words (sctl)
   // instance pools
   const double* J64;      // [off_mat + i*n_pad + j]
   const long long* Jq;    // fixed-point couplings

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
     if (threadIdx.x == 0) {
       P.surv_cnt[b] = 0;
     }
-    if (P.mode != QIS_FP64)
+    if (P.mode != QIS_FP64 && P.dense_ctl)
       for (int g = threadIdx.x; g < P.NP / 32; g += blockDim.x)
         P.sctl[(long long)b * (P.NP / 32) + g] = make_float4(-INFINITY, 0.f, 0.f, 0.f);
     return;
@@ -668,8 +668,8 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
     }
   }
   __syncthreads();
-  if (!fp64) {
-    // the scan's control word of every 32-column group g: {thr, active, RD(min_j a_j - j4max),
+  if (!fp64 && P.dense_ctl) {
+    // the dense scan's control word of every 32-column group g: {thr, active, RD(min_j a_j - j4max),
     // min of a_j over the groups g .. g+7 (columns < n)}. A scan chunk of at most 8 groups
     // starting at g bounds every pair term y_ij = fl(a_j +- 4J~_ij) of row i from below by
     // RD(w - max_j |4J~_ij|) (rounding is monotone), and skips rows with c_i below it.

@@ -314,48 +314,49 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 
 // ---------------------------------------------------------------- output-sensitive pair scan
 // The same filter decided per search with work proportional to its answer (the pruning of the
-// Sec. III dE form): for a pair i < j, y_ij = fl(a_j +- 4J~_ij) >= RD(a_j - rm_i) with rm_i =
-// max_j |4J~_ij| (rounding is monotone), so
+// Sec. III dE form). For a pair i < j, y_ij = fl(a_j + s_i s_j 4J~_ij) >= RD(a_j - rm_i) with
+// rm_i = max_j |4J~_ij| (rounding is monotone), so
 //   - row i can hit only if c_i = fl32(thr - a_i) >= RD(amin - rm_i)  (the live rows), and
-//   - with the columns sorted by a_j, row i's candidates are the prefix RD(a_j - rm_i) <= c_i.
-// Every pair outside those prefixes fails y_ij <= c_i, and every pair inside is tested with
-// exactly the dense scan's arithmetic, so the survivors are the same set. One block per search:
-// stage {a_j, s_j}; list the live rows and a column cut B (no prefix reaches past it); sort the
-// columns a_j < B by (a_j, j) (by rank when at most 256, else bitonic); prefix lengths by binary
-// search and a block scan; then the flat list of (row, column) prefix pairs, one thread each,
-// their coupling loads issued four at a time, survivors appended with one atomic per warp. The
-// per-search work is a few live rows times their prefixes (about 2000 pairs a search for
-// n = 600, K = 120, against n(n-1)/2 = 179700), so the kernel is a chain of short dependent
-// steps: the loads it cannot avoid are grouped so that each step waits once.
-__device__ __forceinline__ uint32_t fkey32(float x) {   // order-preserving key of a finite float
-  const uint32_t u = __float_as_uint(x);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float fkey32_inv(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+//   - its partners j satisfy RD(a_j - rm_i) <= c_i, hence a_j < t_i = nextup(c_i) + rm_i
+//     (exact in FP64): no partner of any live row lies at or above B = max_i t_i.
+// The columns a_j < B are ordered by a monotone bucket of a_j (kSparseNB equal-width buckets
+// over [amin, B), a counting sort), so the columns with a_j < t_i all lie in the buckets up to
+// bucket(t_i): that bucket prefix is row i's candidate list (a superset of its partners, every
+// member tested exactly). Every pair outside those lists fails y_ij <= c_i, every pair inside
+// is tested with exactly the dense scan's arithmetic, so the survivors are the same set.
+// One block per search: stage {a_j, s_j} and rm_j; list the live rows and B; count, scan and
+// scatter the columns by bucket; each live row's list length from its bucket; offsets by a
+// block scan; then the flat list of (row, column) pairs, one thread each, their coupling loads
+// issued four at a time, survivors appended with one atomic per warp. The per-search work is
+// the live rows times their lists (about a thousand pairs a search for n = 600, K = 120,
+// against n(n-1)/2 = 179700), a chain of short dependent steps: the loads it cannot avoid are
+// grouped so that each step waits once.
+constexpr int kSparseNB = 128;   // buckets of a_j
+
+__device__ __forceinline__ int sparse_bucket(float x, float lo, float inv) {
+  const float f = __fmul_rn(__fsub_rn(x, lo), inv);   // monotone in x; NaN for inf * 0
+  return f < (float)kSparseNB ? max(0, (int)f) : kSparseNB - 1;
 }
 
 template <bool EX>
-__global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
+__global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   constexpr int SB = 5;   // sites staged per thread and pass (n = 600: one pass)
-  constexpr int PB = 4;   // prefix pairs per thread and pass (their coupling loads issued together)
+  constexpr int PB = 4;   // listed pairs per thread and pass (their coupling loads issued together)
   const int b = blockIdx.x;
   if (!P.active[b]) return;
   const InstDesc d = P.inst[b / P.R];
-  const int n = d.n, NP = P.NP, NP2 = next_pow2(P.NP), tid = threadIdx.x, lane = tid & 31;
+  const int n = d.n, NP = P.NP, tid = threadIdx.x, lane = tid & 31;
   const float thr = P.thr32[b], amin = P.amin32[b];
-  extern __shared__ unsigned long long ck[];                   // [NP2] column keys
-  float2* sa = reinterpret_cast<float2*>(ck + NP2);           // [NP] {a_j, s_j}
+  extern __shared__ float2 sa[];                              // [NP] {a_j, s_j}
   int* li = reinterpret_cast<int*>(sa + NP);                  // [NP] live rows
-  int* pc = li + NP;                                          // [NP + 1] rm of each live row, then prefix offsets
-  __shared__ int s_nl, s_nc, s_w[4];
+  int* pc = li + NP;                                          // [NP] rm of each live row, then list offsets
+  int* cj = pc + NP;                                          // [NP] columns in bucket order
+  __shared__ int s_nl, s_w[4], bs[kSparseNB + 1], bcur[kSparseNB];
   __shared__ double wB[4];
   const float2* g = P.as32 + (long long)b * NP;
   const float* rm = P.rm4 + d.off_vec;
-  // 1. stage {a, s} (the first pass's loads are issued before the first barrier); live rows;
-  //    the column cut B = max over live rows of nextup(c_i) + rm_i (a_j at or above it fails
-  //    every live row: RD(a_j - rm_i) <= c_i implies a_j - rm_i < nextup(c_i); the sum of two
-  //    floats is exact in FP64)
+  // 1. stage {a, s} (the first pass's loads are issued before the first barrier); live rows
+  //    with their rm; B
   float2 v[SB];
   float r[SB];
 #pragma unroll
@@ -366,10 +367,8 @@ __global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
       r[u] = rm[i];
     }
   }
-  if (tid == 0) {
-    s_nl = 0;
-    s_nc = 0;
-  }
+  if (tid == 0) s_nl = 0;
+  for (int k = tid; k < kSparseNB; k += 128) bcur[k] = 0;
   __syncthreads();
   double bl = -INFINITY;
   for (int base = 0; base < n; base += SB * 128) {
@@ -405,54 +404,45 @@ __global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
   const int nl = s_nl;
   if (nl == 0) return;   // block-uniform
   const double B = fmax(fmax(wB[0], wB[1]), fmax(wB[2], wB[3]));
-  // 2. columns below the cut, keyed (a_j, j) (distinct keys), sorted ascending: by rank into
-  //    the upper half of the key array when they are few, else bitonic in place
+  // 2. bucket of every column a_j < B: equal widths over [amin, B) (one bucket when that range
+  //    is not finite); count, exclusive scan (warp 0), scatter
+  const float hi = __double2float_ru(B), span = __fsub_ru(hi, amin);
+  const float inv = (span > 0.f && span < INFINITY) ? __fdiv_rn((float)kSparseNB, span) : 0.f;
   for (int j = tid; j < n; j += 128)
-    if ((double)sa[j].x < B) ck[atomicAdd(&s_nc, 1)] = ((unsigned long long)fkey32(sa[j].x) << 32) | (unsigned)j;
+    if ((double)sa[j].x < B) atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1);
   __syncthreads();
-  const int nc = s_nc;
-  const unsigned long long* cs = ck;
-  if (nc <= 256 && 2 * nc <= NP2) {   // block-uniform
-    unsigned long long* out = ck + NP2 / 2;
-    for (int t = tid; t < nc; t += 128) {
-      const unsigned long long x = ck[t];
-      int rk = 0;
-#pragma unroll 4
-      for (int k = 0; k < nc; ++k) rk += ck[k] < x;
-      out[rk] = x;
+  if (tid < 32) {
+    int x[kSparseNB / 32], s = 0;
+#pragma unroll
+    for (int k = 0; k < kSparseNB / 32; ++k) {
+      x[k] = bcur[lane * (kSparseNB / 32) + k];
+      s += x[k];
     }
-    cs = out;
-  } else {
-    const int m2 = next_pow2(max(nc, 2));
-    for (int k = nc + tid; k < m2; k += 128) ck[k] = ~0ull;
-    __syncthreads();
-    for (int kk = 2; kk <= m2; kk <<= 1) {
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int t = tid; t < m2; t += 128) {
-          const int u = t ^ jj;
-          if (u > t) {
-            const unsigned long long x = ck[t], y = ck[u];
-            if ((x > y) == ((t & kk) == 0)) {
-              ck[t] = y;
-              ck[u] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
+    int inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
     }
+    int acc = inc - s;
+#pragma unroll
+    for (int k = 0; k < kSparseNB / 32; ++k) {
+      bs[lane * (kSparseNB / 32) + k] = acc;
+      bcur[lane * (kSparseNB / 32) + k] = acc;
+      acc += x[k];
+    }
+    if (lane == 31) bs[kSparseNB] = acc;
   }
   __syncthreads();
-  // 3. prefix length of each live row: the columns with RD(a_j - rm_i) <= c_i
+  for (int j = tid; j < n; j += 128)
+    if ((double)sa[j].x < B) cj[atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1)] = j;
+  // each live row's list: the buckets up to that of t_i = nextup(c_i) + rm_i (rounded up to
+  // FP32, so a_j < t_i gives bucket(a_j) <= bucket(t_i))
   for (int q = tid; q < nl; q += 128) {
     const int i = li[q];
     const float c = __fsub_rn(thr, sa[i].x), rr = __int_as_float(pc[q]);
-    int lo = 0, hi = nc;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (__fsub_rd(fkey32_inv((uint32_t)(cs[mid] >> 32)), rr) <= c) lo = mid + 1; else hi = mid;
-    }
-    pc[q] = lo;
+    const float t = __double2float_ru((double)nextafterf(c, INFINITY) + (double)rr);
+    pc[q] = bs[sparse_bucket(t, amin, inv) + 1];
   }
   __syncthreads();
   // exclusive offsets: each thread a run of consecutive rows, then a warp and a block scan
@@ -477,7 +467,7 @@ __global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
     }
   }
   __syncthreads();
-  // 4. the prefix pairs, one thread each, PB at a time; a pair is tested in the row of its
+  // 3. the listed pairs, one thread each, PB at a time; a pair is tested in the row of its
   //    smaller site; survivors appended with one atomic per warp
   const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3], cap = P.cap;
   const float* J4 = P.J4 + d.off_mat;
@@ -497,7 +487,7 @@ __global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
           const int mid = (lo + hi) >> 1;
           if (pc[mid] <= t) lo = mid; else hi = mid;
         }
-        const int i = li[lo], j = (int)(uint32_t)cs[t - pc[lo]];
+        const int i = li[lo], j = cj[t - pc[lo]];
         const float2 vi = sa[i], vj = sa[j];
         ij[u] = i | (j << 16);   // n <= 16384
         cv[u] = __fsub_rn(thr, vi.x);
@@ -530,9 +520,7 @@ __global__ void __launch_bounds__(128, 12) k_scan_sparse(DevPtrs P) {
   if (lane == 0 && nev) atomicAdd(P.eval_cnt + (b & 63), (unsigned long long)nev);
 }
 
-size_t scan_sparse_smem(int NP) {
-  return (size_t)next_pow2(NP) * 8 + (size_t)NP * 8 + (size_t)NP * 4 + (size_t)(NP + 1) * 4;
-}
+size_t scan_sparse_smem(int NP) { return (size_t)NP * 8 + (size_t)NP * 12; }
 
 cudaError_t launch_scan_sparse(const DevPtrs& P, cudaStream_t s) {
   const size_t sm = scan_sparse_smem(P.NP);

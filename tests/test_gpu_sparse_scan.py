@@ -1,6 +1,7 @@
-"""The output-sensitive pair scan (live rows, columns sorted by a_j, per-row feasible prefix)
-against the dense register-tile scan (QIS_DENSE_SCAN=1): both test exactly the same pairs
-that can pass, so every search must come out identical, and equal to the oracle."""
+"""The output-sensitive pair scan (live rows, columns ordered by a bucket of a_j, each live
+row's bucket prefix) against the dense register-tile scan (QIS_DENSE_SCAN=1): both test every
+pair that can pass with the same arithmetic, so every search must come out identical, and
+equal to the oracle."""
 import numpy as np
 import pytest
 
@@ -47,3 +48,16 @@ def test_sparse_equals_dense(prec, ens, flips, monkeypatch):
     for r in range(2):
         ref = O.qi_search(J, h, K, iters, phis[0][r], flips=fl)
         assert np.array_equal(sparse[0][r]["bits"], ref["bits"][: ref["count"]])
+
+
+@pytest.mark.parametrize("flips", ["single_pair", "exchange"])
+def test_sparse_equals_dense_several_staging_passes(flips, monkeypatch):
+    """n = 1500: a block stages its sites in three passes of 640."""
+    ns, K, R, iters = [1500, 700], 60, 4, 12
+    _, _, sparse = run("split_bf16", "gaussian", flips, ns, K, R, iters, 610)
+    monkeypatch.setenv("QIS_DENSE_SCAN", "1")
+    _, _, dense = run("split_bf16", "gaussian", flips, ns, K, R, iters, 610)
+    for k in range(len(ns)):
+        for r in range(R):
+            for key in ("count", "bits", "E", "stamp", "used"):
+                assert np.array_equal(sparse[k][r][key], dense[k][r][key]), (k, r, key)
