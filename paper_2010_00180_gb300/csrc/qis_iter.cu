@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   extern __shared__ unsigned long long subkey[];     // [kSubMax] (u32 keys reuse the front)
   __shared__ int hist[256], hist2[256];
   __shared__ int sites[kSubSites];
-  __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near;
+  __shared__ int s_nsites, s_n2, s_bin, s_bin2, s_near, s_ns;
   __shared__ float s_thr;
   __shared__ double s_T, s_cap;
   const int cnt = P.lst_count[b];
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   }
   for (int w = threadIdx.x; w < d.W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   if (threadIdx.x == 0) {
-    P.surv_cnt[b] = 0;
+    s_ns = 0;   // survivors: the singles listed below (one block per search: counted in shared memory)
     s_nsites = 0;
     s_n2 = 0;
     s_near = 0;
@@ -699,10 +699,12 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
       ok = as[i].x <= s_thr;
     }
     if (ok) {
-      const int slot = atomicAdd(P.surv_cnt + b, 1);
+      const int slot = atomicAdd(&s_ns, 1);
       if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, -1);
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) P.surv_cnt[b] = s_ns;
 }
 
 cudaError_t launch_bound(const DevPtrs& P, cudaStream_t s) {

@@ -327,7 +327,7 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 // One block per search: stage {a_j, s_j} and rm_j; list the live rows and B; count, scan and
 // scatter the columns by bucket; each live row's list length from its bucket; offsets by a
 // block scan; then the flat list of (row, column) pairs, one thread each, their coupling loads
-// issued four at a time, survivors appended with one atomic per warp. The per-search work is
+// issued four at a time, survivors appended with one shared atomic per warp. The per-search work is
 // the live rows times their lists (about a thousand pairs a search for n = 600, K = 120,
 // against n(n-1)/2 = 179700), a chain of short dependent steps: the loads it cannot avoid are
 // grouped so that each step waits once.
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   int* li = reinterpret_cast<int*>(sa + NP);                  // [NP] live rows
   int* pc = li + NP;                                          // [NP] rm of each live row, then list offsets
   int* cj = pc + NP;                                          // [NP] columns in bucket order
-  __shared__ int s_nl, s_w[4], bs[kSparseNB + 1], bcur[kSparseNB];
+  __shared__ int s_nl, s_ns, s_w[4], bs[kSparseNB + 1], bcur[kSparseNB];
   __shared__ double wB[4];
   const float2* g = P.as32 + (long long)b * NP;
   const float* rm = P.rm4 + d.off_vec;
@@ -367,7 +367,10 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
       r[u] = rm[i];
     }
   }
-  if (tid == 0) s_nl = 0;
+  if (tid == 0) {
+    s_nl = 0;
+    s_ns = P.surv_cnt[b];   // the singles k_bound listed; this block alone appends to the search
+  }
   for (int k = tid; k < kSparseNB; k += 128) bcur[k] = 0;
   __syncthreads();
   double bl = -INFINITY;
@@ -468,7 +471,8 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   }
   __syncthreads();
   // 3. the listed pairs, one thread each, PB at a time; a pair is tested in the row of its
-  //    smaller site; survivors appended with one atomic per warp
+  //    smaller site; survivors appended with one shared-memory atomic per warp (one block per
+  //    search: the count goes back to global memory once, at the end)
   const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3], cap = P.cap;
   const float* J4 = P.J4 + d.off_mat;
   unsigned long long* surv = P.surv + (long long)b * cap;
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
       if (m) {
         const int leader = __ffs(m) - 1;
         int base = 0;
-        if (lane == leader) base = atomicAdd(P.surv_cnt + b, __popc(m));
+        if (lane == leader) base = atomicAdd(&s_ns, __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
         const int slot = base + __popc(m & ((1u << lane) - 1u));
         if (hit && slot < cap) surv[slot] = surv_entry(ij[u] & 0xffff, ij[u] >> 16);
@@ -518,6 +522,8 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
   if (lane == 0 && nev) atomicAdd(P.eval_cnt + (b & 63), (unsigned long long)nev);
+  __syncthreads();
+  if (tid == 0) P.surv_cnt[b] = s_ns;
 }
 
 size_t scan_sparse_smem(int NP) { return (size_t)NP * 8 + (size_t)NP * 12; }
