@@ -317,12 +317,13 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 // Sec. III dE form). For a pair i < j, y_ij = fl(a_j + s_i s_j 4J~_ij) >= RD(a_j - rm_i) with
 // rm_i = max_j |4J~_ij| (rounding is monotone), so
 //   - row i can hit only if c_i = fl32(thr - a_i) >= RD(amin - rm_i)  (the live rows), and
-//   - its partners j satisfy RD(a_j - rm_i) <= c_i, hence a_j < t_i = nextup(c_i) + rm_i
-//     (exact in FP64): no partner of any live row lies at or above B = max_i t_i.
+//   - its partners j satisfy RD(a_j - rm_i) <= c_i, hence a_j < nextup(c_i) + rm_i <= t_i =
+//     RU(nextup(c_i) + rm_i) (FP32, rounded up): no partner of any live row lies at or above
+//     B = max_i t_i.
 // The columns a_j < B are ordered by a monotone bucket of a_j (kSparseNB equal-width buckets
 // over [amin, B), a counting sort), so the columns with a_j < t_i all lie in the buckets up to
 // bucket(t_i): that bucket prefix is row i's candidate list (a superset of its partners, every
-// member tested exactly). Every pair outside those lists fails y_ij <= c_i, every pair inside
+// member tested exactly). No FP64 arithmetic: GB300's FP64 pipe is narrow. Every pair outside those lists fails y_ij <= c_i, every pair inside
 // is tested with exactly the dense scan's arithmetic, so the survivors are the same set.
 // One block per search: stage {a_j, s_j} and rm_j; list the live rows and B; count, scan and
 // scatter the columns by bucket; each live row's list length from its bucket; offsets by a
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   int* pc = li + NP;                                          // [NP] rm of each live row, then list offsets
   int* cj = pc + NP;                                          // [NP] columns in bucket order
   __shared__ int s_nl, s_ns, s_w[4], bs[kSparseNB + 1], bcur[kSparseNB];
-  __shared__ double wB[4];
+  __shared__ float wB[4];
   const float2* g = P.as32 + (long long)b * NP;
   const float* rm = P.rm4 + d.off_vec;
   // 1. stage {a, s} (the first pass's loads are issued before the first barrier); live rows
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   }
   for (int k = tid; k < kSparseNB; k += 128) bcur[k] = 0;
   __syncthreads();
-  double bl = -INFINITY;
+  float bl = -INFINITY;
   for (int base = 0; base < n; base += SB * 128) {
     if (base > 0) {
 #pragma unroll
@@ -395,24 +396,24 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
           const int q = atomicAdd(&s_nl, 1);
           li[q] = i;
           pc[q] = __float_as_int(r[u]);
-          bl = fmax(bl, (double)nextafterf(c, INFINITY) + (double)r[u]);   // exact; +inf for c = +inf
+          bl = fmaxf(bl, __fadd_ru(nextafterf(c, INFINITY), r[u]));   // +inf for c = +inf
         }
       }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bl = fmax(bl, __shfl_xor_sync(0xffffffffu, bl, o));
+  for (int o = 16; o > 0; o >>= 1) bl = fmaxf(bl, __shfl_xor_sync(0xffffffffu, bl, o));
   if (lane == 0) wB[tid >> 5] = bl;
   __syncthreads();
   const int nl = s_nl;
   if (nl == 0) return;   // block-uniform
-  const double B = fmax(fmax(wB[0], wB[1]), fmax(wB[2], wB[3]));
+  const float B = fmaxf(fmaxf(wB[0], wB[1]), fmaxf(wB[2], wB[3]));
   // 2. bucket of every column a_j < B: equal widths over [amin, B) (one bucket when that range
   //    is not finite); count, exclusive scan (warp 0), scatter
-  const float hi = __double2float_ru(B), span = __fsub_ru(hi, amin);
+  const float span = __fsub_ru(B, amin);
   const float inv = (span > 0.f && span < INFINITY) ? __fdiv_rn((float)kSparseNB, span) : 0.f;
   for (int j = tid; j < n; j += 128)
-    if ((double)sa[j].x < B) atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1);
+    if (sa[j].x < B) atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1);
   __syncthreads();
   if (tid < 32) {
     int x[kSparseNB / 32], s = 0;
@@ -438,14 +439,13 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   }
   __syncthreads();
   for (int j = tid; j < n; j += 128)
-    if ((double)sa[j].x < B) cj[atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1)] = j;
-  // each live row's list: the buckets up to that of t_i = nextup(c_i) + rm_i (rounded up to
-  // FP32, so a_j < t_i gives bucket(a_j) <= bucket(t_i))
+    if (sa[j].x < B) cj[atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1)] = j;
+  // each live row's list: the buckets up to that of t_i (a_j < t_i gives bucket(a_j) <=
+  // bucket(t_i): the bucket is monotone)
   for (int q = tid; q < nl; q += 128) {
     const int i = li[q];
     const float c = __fsub_rn(thr, sa[i].x), rr = __int_as_float(pc[q]);
-    const float t = __double2float_ru((double)nextafterf(c, INFINITY) + (double)rr);
-    pc[q] = bs[sparse_bucket(t, amin, inv) + 1];
+    pc[q] = bs[sparse_bucket(__fadd_ru(nextafterf(c, INFINITY), rr), amin, inv) + 1];
   }
   __syncthreads();
   // exclusive offsets: each thread a run of consecutive rows, then a warp and a block scan
