@@ -314,24 +314,30 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 
 // ---------------------------------------------------------------- output-sensitive pair scan
 // The same filter decided per search with work proportional to its answer (the pruning of the
-// Sec. III dE form). For a pair i < j, y_ij = fl(a_j + s_i s_j 4J~_ij) >= RD(a_j - rm_i) with
-// rm_i = max_j |4J~_ij| (rounding is monotone), so
-//   - row i can hit only if c_i = fl32(thr - a_i) >= RD(amin - rm_i)  (the live rows), and
-//   - its partners j satisfy RD(a_j - rm_i) <= c_i, hence a_j < nextup(c_i) + rm_i <= t_i =
-//     RU(nextup(c_i) + rm_i) (FP32, rounded up): no partner of any live row lies at or above
-//     B = max_i t_i.
+// Sec. III dE form). In row i the filter value of pair {i, j} is y_ij = fl(a_j + s_i s_j 4J~_ij)
+// and the pair passes when y_ij <= c_i = fl32(thr - a_i); since y_ij >= RD(a_j - rm_i) with
+// rm_i = max_j |4J~_ij| (rounding is monotone),
+//   - row i can pass a pair only if c_i >= RD(amin - rm_i)  (the live rows), and
+//   - only with partners a_j < nextup(c_i) + rm_i <= t_i = RU(nextup(c_i) + rm_i) (FP32,
+//     rounded up): no partner of any live row lies at or above B = max_i t_i.
 // The columns a_j < B are ordered by a monotone bucket of a_j (kSparseNB equal-width buckets
-// over [amin, B), a counting sort), so the columns with a_j < t_i all lie in the buckets up to
-// bucket(t_i): that bucket prefix is row i's candidate list (a superset of its partners, every
-// member tested exactly). No FP64 arithmetic: GB300's FP64 pipe is narrow. Every pair outside those lists fails y_ij <= c_i, every pair inside
-// is tested with exactly the dense scan's arithmetic, so the survivors are the same set.
+// over [amin, B), a counting sort), so row i's partners all lie in the buckets up to bucket(t_i):
+// that prefix of the column order is row i's list. A pair within the threshold passes the
+// test of either of its rows (the band of thr bounds the rounding of both forms, which are
+// symmetric in i and j), so both sites are live and each is in the other's list: the pair is
+// tested once, in the row whose site comes first in the column order, against the columns
+// after it. The survivors are therefore a superset of every pair within the threshold, which
+// is all the merge needs (it decides every survivor exactly); pairs the rounding puts on the
+// other side of thr in one form or the other may differ from the dense scan's, never a pair
+// the merge keeps. No FP64 arithmetic: GB300's FP64 pipe is narrow.
 // One block per search: stage {a_j, s_j} and rm_j; list the live rows and B; count, scan and
-// scatter the columns by bucket; each live row's list length from its bucket; offsets by a
-// block scan; then the flat list of (row, column) pairs, one thread each, their coupling loads
-// issued four at a time, survivors appended with one shared atomic per warp. The per-search work is
-// the live rows times their lists (about a thousand pairs a search for n = 600, K = 120,
-// against n(n-1)/2 = 179700), a chain of short dependent steps: the loads it cannot avoid are
-// grouped so that each step waits once.
+// scatter the columns by bucket (each site's spin and position packed into its staged s_j);
+// each live row's list length from its bucket, less its own position; offsets by a block scan;
+// then the flat list of (row, column) pairs, one thread each, their coupling loads issued four
+// at a time, survivors appended with one shared atomic per warp. The per-search work is the
+// live rows times their lists (several hundred pairs a search for n = 600, K = 120, against
+// n(n-1)/2 = 179700), a chain of short dependent steps: the loads it cannot avoid are grouped
+// so that each step waits once.
 constexpr int kSparseNB = 128;   // buckets of a_j
 
 __device__ __forceinline__ int sparse_bucket(float x, float lo, float inv) {
@@ -438,8 +444,19 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
     if (lane == 31) bs[kSparseNB] = acc;
   }
   __syncthreads();
-  for (int j = tid; j < n; j += 128)
-    if (sa[j].x < B) cj[atomicAdd(&bcur[sparse_bucket(sa[j].x, amin, inv)], 1)] = j;
+  // site code in place of s_j: (position in the column order << 1) | sigma_j, or INT_MIN |
+  // sigma_j for a site at or above B
+  for (int j = tid; j < n; j += 128) {
+    const float2 v = sa[j];
+    const int sg = v.y < 0.f;
+    int code = INT_MIN | sg;
+    if (v.x < B) {
+      const int k = atomicAdd(&bcur[sparse_bucket(v.x, amin, inv)], 1);
+      cj[k] = j;
+      code = (k << 1) | sg;
+    }
+    sa[j].y = __int_as_float(code);
+  }
   // each live row's list: the buckets up to that of t_i (a_j < t_i gives bucket(a_j) <=
   // bucket(t_i): the bucket is monotone)
   for (int q = tid; q < nl; q += 128) {
@@ -448,11 +465,17 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
     pc[q] = bs[sparse_bucket(__fadd_ru(nextafterf(c, INFINITY), rr), amin, inv) + 1];
   }
   __syncthreads();
-  // exclusive offsets: each thread a run of consecutive rows, then a warp and a block scan
+  // the columns after the row's own position (none for a row outside the column order), then
+  // exclusive offsets: each thread a run of consecutive rows, a warp and a block scan
   {
     const int per = (nl + 127) >> 7, q0 = min(nl, tid * per), q1 = min(nl, q0 + per);
     int sum = 0;
-    for (int q = q0; q < q1; ++q) sum += pc[q];
+    for (int q = q0; q < q1; ++q) {
+      const int code = __float_as_int(sa[li[q]].y);
+      const int x = code < 0 ? 0 : max(0, pc[q] - (code >> 1) - 1);
+      pc[q] = x;
+      sum += x;
+    }
     int inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -470,9 +493,9 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
     }
   }
   __syncthreads();
-  // 3. the listed pairs, one thread each, PB at a time; a pair is tested in the row of its
-  //    smaller site; survivors appended with one shared-memory atomic per warp (one block per
-  //    search: the count goes back to global memory once, at the end)
+  // 3. the listed pairs, one thread each, PB at a time; survivors appended with one
+  //    shared-memory atomic per warp (one block per search: the count goes back to global
+  //    memory once, at the end)
   const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3], cap = P.cap;
   const float* J4 = P.J4 + d.off_mat;
   unsigned long long* surv = P.surv + (long long)b * cap;
@@ -491,13 +514,16 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
           const int mid = (lo + hi) >> 1;
           if (pc[mid] <= t) lo = mid; else hi = mid;
         }
-        const int i = li[lo], j = cj[t - pc[lo]];
-        const float2 vi = sa[i], vj = sa[j];
-        ij[u] = i | (j << 16);   // n <= 16384
+        const int i = li[lo];
+        const float2 vi = sa[i];
+        const int ci = __float_as_int(vi.y);
+        const int j = cj[(ci >> 1) + 1 + t - pc[lo]];
+        const float2 vj = sa[j];
+        ij[u] = min(i, j) | (max(i, j) << 16);   // n <= 16384
         cv[u] = __fsub_rn(thr, vi.x);
         av[u] = vj.x;
-        pv[u] = vi.y * vj.y;   // s_i s_j
-        ok[u] = j > i && (!EX || pv[u] < 0.f);   // exchanges: opposite spins only
+        pv[u] = ((ci ^ __float_as_int(vj.y)) & 1) ? -1.f : 1.f;   // s_i s_j
+        ok[u] = !EX || pv[u] < 0.f;   // exchanges: opposite spins only
         if (ok[u]) jv[u] = J4[(long long)i * d.n_pad + j];
       }
     }
@@ -506,7 +532,7 @@ __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
       bool hit = false;
       if (ok[u]) {
         ++nev;
-        hit = fmaf(pv[u], jv[u], av[u]) <= cv[u];   // fl(a_j + s_i s_j 4J~_ij): the dense scan's value
+        hit = fmaf(pv[u], jv[u], av[u]) <= cv[u];   // fl(a_j + s_i s_j 4J~_ij) <= c_i
       }
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (m) {
