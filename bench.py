@@ -11,9 +11,10 @@ run I iterations of Alg. 3 on all 7680 searches, merge the R lists of every inst
   e2e    the same metric through the C ABI with host buffers: each step copies J, h and
          the initial states to the device, iterates, and copies back the merged K+1 states
          of every instance with FP64 energies
-  roofline  the candidate-scan kernel: the output-sensitive scan (one block per search)
-         against HBM bandwidth (12 bytes per site and search + 4 bytes per pair tested); the
-         dense tile scan against the SM issue rate (2 ALU operations per pair candidate)
+  roofline  the kernel class with the largest share of the step: the per-search bound, the
+         output-sensitive scan or the merge against HBM bandwidth (their algorithmic bytes per
+         search in the docstrings below), the dense tile scan against the SM issue rate (2 ALU
+         operations per pair candidate), the plain FP64 scan against the FP64 rate
   cpu_baseline  the CPU oracle on a bounded sample of the same workload (host cores)
 
 --impl reference times the oracle (the CPU reference of this tier) on the same metric.
@@ -191,6 +192,7 @@ def run_ours(args, rank, world, device):
     launches0 = ctx.kernel_launches()
     pairs0, singles0 = ctx.candidate_count()
     evald0 = ctx.evaluated_pairs()
+    surv0 = ctx.survivor_count()
     for k in range(5):
         ctx.profile_query(k)                            # drop warm-up timings
     ctx.profile(True)
@@ -217,13 +219,14 @@ def run_ours(args, rank, world, device):
     if flips == "single":   # the metric counts single flips when there are no pairs
         pairs = singles
     evald = ctx.evaluated_pairs() - evald0
-    t = torch.tensor([ms, float(pairs), float(evald)], dtype=torch.float64, device=f"cuda:{device}")
+    surv = ctx.survivor_count() - surv0
+    t = torch.tensor([ms, float(pairs), float(evald), float(surv)], dtype=torch.float64, device=f"cuda:{device}")
     if world > 1:
         tm = t.clone()
         dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
         dist.all_reduce(tm[1:], op=dist.ReduceOp.SUM)
         t = tm
-    ms_max, pairs_all, evald = float(t[0]), float(t[1]), float(t[2])
+    ms_max, pairs_all, evald, surv = float(t[0]), float(t[1]), float(t[2]), float(t[3])
 
     # time to ground state (Eq. (tts) of Sec. IV): p1 = fraction of instances whose merged
     # best energy reaches the best-known one, for a sweep of iteration counts of the same
@@ -264,7 +267,7 @@ def run_ours(args, rank, world, device):
     ctx.close()
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
-                digits=digits, workload=args.workload, pair_scan=pair_scan)
+                digits=digits, workload=args.workload, pair_scan=pair_scan, survivors=surv)
 
 
 def _timed_run(ctx, stream, iters):
@@ -412,8 +415,8 @@ def run_warmstart(args, device=0):
     print(json.dumps(line))
 
 
-def scan_traffic(workload, kernel):
-    """DRAM bytes per launch of a scan kernel from its last ncu capture, or None when the
+def kernel_traffic(workload, kernel):
+    """DRAM bytes per launch of a kernel from its last ncu capture, or None when the
     kernel source has changed since that capture or the capture was of another workload."""
     import hashlib
     try:
@@ -441,10 +444,37 @@ def roofline_bound(res, pk, src):
     achieved = bytes_per_launch / dur / 1e9
     peak = float(pk.get("hbm_gbs", 6800.0))
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_bound",
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_bound"), "kernel": "k_bound",
             "launch_us": round(dur * 1e6, 2), "bytes_per_launch": bytes_per_launch,
             "per_unit": "8 bytes per site ({a_i, s_i}) + 8 bytes per word of each of the K+1 kept states, per search",
             "peak_source": src}
+
+
+def roofline_merge(res, pk, src):
+    """Per-search merge against the measured HBM bandwidth: per search it reads the old list's
+    keys and order and writes the new ones (24 bytes per kept slot), reads the parent's bits
+    (8 bytes a word) and, per survivor, its entry and the exact-key operands aq_i, aq_j and
+    Jq_ij (32 bytes; a single flip is counted like a pair)."""
+    ms, nl = res["prof"]["merge"]
+    if nl == 0 or ms <= 0:
+        return None
+    n, K1 = res["n"], res["K"] + 1
+    words = (n + 63) // 64
+    searches = res["n_inst"] * res["R"]
+    surv = res.get("survivors", 0.0) / nl
+    bytes_per_launch = float(searches * (24 * K1 + 8 * words) + 32 * surv)
+    dur = ms / nl / 1e3
+    achieved = bytes_per_launch / dur / 1e9
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_merge"), "kernel": "k_merge",
+            "launch_us": round(dur * 1e6, 2), "bytes_per_launch": bytes_per_launch,
+            "survivors_per_launch": surv,
+            "per_unit": "24 bytes per kept slot (old and new key and order) + 8 bytes per word of the parent "
+                        "+ 32 bytes per survivor (entry, aq_i, aq_j, Jq_ij), per search",
+            "peak_source": src,
+            "note": "one block per search: exact keys, duplicate test, sort and rank merge, a chain of dependent "
+                    "steps; the new states' bits are not counted"}
 
 
 def roofline(res, pk):
@@ -481,7 +511,7 @@ def roofline(res, pk):
         achieved = bytes_per_launch / dur / 1e9
         peak = float(pk.get("hbm_gbs", 6800.0))
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload"), "k_scan_sparse"),
+                "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_scan_sparse"),
                 "kernel": "k_scan_sparse", "launch_us": round(dur * 1e6, 2),
                 "bytes_per_launch": bytes_per_launch, "searches_per_launch": round(searches, 1),
                 "tested_pairs_per_launch": tested,
@@ -495,7 +525,7 @@ def roofline(res, pk):
     peak = 152 * 128 * clk * 1e6 / 1e12
     ev = 2.0 * res["evald"] / max(1, nl) / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-            "frac": round(achieved / peak, 4), "traffic": scan_traffic(res.get("workload"), "k_scan_pairs"),
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_scan_pairs"),
             "kernel": "k_scan_pairs",
             "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops_per_launch,
             "per_unit": "2 operations per pair candidate decided (signed FMA + compare)",
@@ -574,17 +604,27 @@ def main():
     if rank != 0:
         return
     pk, src = peaks()
-    rl = roofline(res, pk) if flips != "single" else roofline_bound(res, pk, src)
+    # the roofline of the kernel class with the largest share of the step (per-search bound,
+    # pair scan or merge); the others beside it
+    cands = {"bound": roofline_bound(res, pk, src), "merge": roofline_merge(res, pk, src)}
+    if flips != "single":
+        cands["scan"] = roofline(res, pk)
+    cands = {k: v for k, v in cands.items() if v is not None}
+    dom = max(cands, key=lambda k: res["prof"][k][0])
+    rl = dict(cands[dom], dominant_share=round(res["prof"][dom][0] / res["ms"], 4))
+    others = {v["kernel"]: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac", "launch_us")}
+              for k, v in cands.items() if k != dom}
     value = res["pairs"] / (res["ms"] / 1e3)
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 filter / int64 exact keys" if prec != "fp64" else "f64", "data": "synthetic",
-            "config": config, "roofline": rl, "peak_source": src,
+            "config": config, "roofline": rl, "rooflines_other": others, "peak_source": src,
             "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["launches"], "clocks": res["clocks"],
             "tts": res["tts"], "forms": res["forms"],
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["prof"].items()},
             "evaluated_pairs_per_s": res["evald"] / (res["ms"] / 1e3),
+            "survivors_per_s": res["survivors"] / (res["ms"] / 1e3),
             "metric_note": "value = candidates decided exactly per second (every pair of the flip set of every "
                            "parent: n(n-1)/2 by default); evaluated_pairs_per_s = those tested one by one in "
                            "the scan"}

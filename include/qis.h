@@ -269,6 +269,12 @@ int qis_set_incremental_fields(qis_ctx* ctx, int on);
  * once). Synchronises the stream. */
 int qis_evaluated_pairs(qis_ctx* ctx, uint64_t* pairs);
 
+/* Survivors of the candidate filters (singles and pairs passing the FP32 test with its band)
+ * that the merge read, summed over every search and iteration since the context was created:
+ * the candidates whose energies the merge computed exactly (Alg. 2's evaluation of the kept
+ * candidates). Synchronises the stream. */
+int qis_survivor_count(qis_ctx* ctx, uint64_t* count);
+
 /* The library's CUDA stream (a cudaStream_t), so callers can order their own work and
  * CUDA events with respect to the library's kernels. */
 int qis_get_stream(qis_ctx* ctx, void** stream);

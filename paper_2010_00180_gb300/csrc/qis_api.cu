@@ -426,6 +426,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.nprod, B);
     ALLOC(P.npair, B);
     ALLOC(P.eval_cnt, 64);
+    ALLOC(P.surv_tot, 64);
     ALLOC(P.mrg_ref, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_src, (size_t)ctx->max_inst * K1);
     ALLOC(P.mrg_count, ctx->max_inst);
@@ -1308,6 +1309,18 @@ int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles) {
   if (rc) return rc;
   if (pairs) *pairs = ctx->cand_acc[0] + c[0];
   if (singles) *singles = ctx->cand_acc[1] + c[1];
+  return 0;
+}
+
+int qis_survivor_count(qis_ctx* ctx, uint64_t* count) {
+  if (!ctx || !count) return fail(ctx, QIS_ERR_INVALID_ARG, "NULL argument");
+  FLUSH_INIT(ctx);
+  CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long v[64];
+  CK(cudaMemcpy(v, ctx->P.surv_tot, sizeof(v), cudaMemcpyDeviceToHost));
+  uint64_t t = 0;
+  for (int k = 0; k < 64; ++k) t += v[k];
+  *count = t;
   return 0;
 }
 

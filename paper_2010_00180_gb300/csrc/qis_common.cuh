@@ -103,6 +103,7 @@ struct DevPtrs {
   int* nprod;             // [b] productive iterations (a parent was expanded) of search b
   unsigned long long* npair;  // [b] pair candidates of the expanded parents of search b
   unsigned long long* eval_cnt;  // [64] pair terms the FP32 scan evaluated (live rows x chunk width)
+  unsigned long long* surv_tot;  // [64] survivors the merge read (sum of the per-search counts)
   // final merge (Alg. 4) per instance
   int* mrg_ref;           // [inst][K1] search*K1 + slot
   uint64_t* mrg_src;      // [inst][K1]

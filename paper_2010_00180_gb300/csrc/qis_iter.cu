@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   const int fl = P.flips;
   const bool ex = fl == QIS_FLIPS_EXCHANGE;
   int nu = 0;
-  for (int w = 0; w < d.W; ++w) nu += __popcll(pb[w]);   // bits above n are zero
+  if (ex)
+    for (int w = 0; w < d.W; ++w) nu += __popcll(pb[w]);   // bits above n are zero
   const long long C = fl == QIS_FLIPS_SINGLE ? (long long)n
                       : ex ? (long long)nu * (n - nu) : (long long)n * (n + 1) / 2;
   if (C > k && k <= kSubMax) {
@@ -505,8 +506,9 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
       t0 = k;
     } else if (ex) {
       const int nd = n - nu;   // nu, nd >= 1: C > k >= 1
-      int m0 = 1;
+      int m0 = max(1, (int)sqrtf((float)want));   // smallest m0 with m0^2 >= want
       while (m0 * m0 < want) ++m0;
+      while (m0 > 1 && (m0 - 1) * (m0 - 1) >= want) --m0;
       int mu = min(nu, m0);
       int md = min(nd, (want + mu - 1) / mu);
       mu = min(nu, (want + md - 1) / md);
@@ -518,9 +520,12 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
       t0 = mu;
       t1 = md;
     } else {
-      int m = 1;
-      while (m < n && m + m * (m - 1) / 2 < want) ++m;
-      t0 = min(m, kSubSites);
+      // smallest m with m + m(m-1)/2 = m(m+1)/2 >= want (closed form, then a step either
+      // way), at most n
+      int m = max(1, (int)((sqrtf(8.f * (float)want + 1.f) - 1.f) * 0.5f));
+      while (m * (m + 1) / 2 < want) ++m;
+      while (m > 1 && (m - 1) * m / 2 >= want) --m;
+      t0 = min(min(m, n), kSubSites);
     }
     const int lim0 = ex ? kSubSites - t1 : kSubSites;   // site slots of the first class
     const float span = fmaxf(amax - amin, 1e-30f);

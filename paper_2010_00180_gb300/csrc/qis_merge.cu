@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
     if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
     return;
   }
+  if (threadIdx.x == 0 && S) atomicAdd(P.surv_tot + (b & 63), (unsigned long long)S);
   // kept candidates (key, entry): in shared memory for up to kMergeSmemCand of them (the usual
   // case; a small footprint keeps eight blocks per SM), else in the search's global scratch
   const int PCs = merge_smem_cand(P.cap, P.merge_cand);

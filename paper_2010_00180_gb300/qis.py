@@ -23,7 +23,7 @@ SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance",
            "qis_clear_instances", "qis_topk_states_all",
            "qis_instance_info", "qis_init_states", "qis_reset", "qis_iterate", "qis_search_list",
            "qis_set_search_list", "qis_save", "qis_load", "qis_instance_n",
-           "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs",
+           "qis_get_tuning", "qis_set_tuning", "qis_autotune", "qis_evaluated_pairs", "qis_survivor_count",
            "qis_set_incremental_fields",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
@@ -90,6 +90,7 @@ def load():
         "qis_instance_n": (I, [P, I, C.POINTER(I)]),
         "qis_get_tuning": (I, [P, C.POINTER(Tuning)]),
         "qis_evaluated_pairs": (I, [P, C.POINTER(U64)]),
+        "qis_survivor_count": (I, [P, C.POINTER(U64)]),
         "qis_set_tuning": (I, [P, C.POINTER(Tuning)]),
         "qis_autotune": (I, [P, I, C.POINTER(Tuning), C.POINTER(C.c_double)]),
         "qis_load": (I, [P, C.c_char_p]),
@@ -268,6 +269,12 @@ class Context:
         """Pair terms the scan evaluated one by one (the rest were decided by the row bound)."""
         v = C.c_uint64()
         self._check(self.lib.qis_evaluated_pairs(self.h, C.byref(v)))
+        return v.value
+
+    def survivor_count(self) -> int:
+        """Candidates that passed the FP32 filters and were evaluated exactly by the merge."""
+        v = C.c_uint64()
+        self._check(self.lib.qis_survivor_count(self.h, C.byref(v)))
         return v.value
 
     def tuning(self) -> dict:
