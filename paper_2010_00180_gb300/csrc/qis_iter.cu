@@ -23,7 +23,6 @@
 
 namespace qis {
 
-__device__ inline float fl32_up(double x) { return __double2float_ru(x); }
 
 // ---------------------------------------------------------------- parent pick (Alg. 3)
 // One warp per search, four searches per block (more searches resident than with one-warp
@@ -392,7 +391,11 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   // key of T, the last kept energy (its value is formed by thread 0 alone: FP64 arithmetic
   // runs on a narrow pipe)
   const unsigned long long kT = (cnt == P.K1) ? P.lst_key[base + P.K1 - 1] : 0ull;
-  const double Ep = P.par_E[b];
+  // the parent's energy: FP64 in the FP64 mode, the exact integer E 2^q in the split modes
+  // (one register for either)
+  const long long epw = fp64 ? __double_as_longlong(P.par_E[b]) : P.par_q[b];
+  const double Ep = __longlong_as_double(epw);   // FP64 mode
+  const long long Epq = epw;                     // split modes
   const double* a64 = P.a64 + (long long)b * P.NP;
   // kept states one or two flips away from the parent: the only candidates that can be
   // duplicates, each equal to exactly one candidate. The kept states are the list slots
@@ -648,26 +651,24 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
     }
   }
   if (threadIdx.x == 0) {
-    // T from its key (exact integers E 2^q in the split modes)
-    const double T = (cnt != P.K1) ? INFINITY
-                     : fp64        ? dkey_inv(kT)
-                                   : (double)(long long)(kT ^ (1ull << 63)) * d.inv_scale;
-    if (!fp64) U = (double)Uf;
     if (fp64) {
+      const double T = (cnt != P.K1) ? INFINITY : dkey_inv(kT);
       s_T = T;
       s_cap = U;
       P.thrE[b] = T;
       P.capE[b] = U;
     } else {
       // |dE~ - dE| <= delta: a and 4J are fl32 of exact values; the scan adds one FMA
-      // rounding and one subtraction rounding (factor 8 margin in the constant)
-      const double t0 = fmin((T == INFINITY) ? INFINITY : T - Ep, U);   // T - Ep is exact
-      const double big = 3.0 * fmax(fabs((double)amin), fabs((double)amax)) + (double)d.j4max +
-                         (isinf(t0) ? 0.0 : fabs(t0));
-      const double delta = ldexp(big, -21);
-      const double t1 = (T == INFINITY) ? INFINITY : (T - Ep) + delta;
-      const double t2 = U + 2.0 * delta;
-      s_thr = fl32_up(fmin(t1, t2));
+      // rounding and one subtraction rounding (factor 8 margin in the constant). Everything
+      // in FP32 rounded up (an upper bound at each step; GB300's FP64 pipe is narrow):
+      // T - Ep from the exact integer keys, scaled by the power of two 2^-q.
+      const float tE = (cnt != P.K1) ? INFINITY
+                                     : __fmul_ru(__ll2float_ru((long long)(kT ^ (1ull << 63)) - Epq), (float)d.inv_scale);
+      const float t0 = fminf(tE, Uf);
+      const float big = __fadd_ru(__fadd_ru(__fmul_ru(3.f, fmaxf(fabsf(amin), fabsf(amax))), d.j4max),
+                                  isinf(t0) ? 0.f : fabsf(t0));
+      const float delta = __fmul_ru(big, 0x1p-21f);   // exact unless subnormal: rounded up
+      s_thr = fminf(__fadd_ru(tE, delta), __fadd_ru(Uf, 2.f * delta));
       P.thr32[b] = s_thr;
       P.amin32[b] = amin;
     }

@@ -200,12 +200,20 @@ __host__ __device__ inline int merge_smem_cand(int cap, int merge_cand) {
 
 __global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
   const int b = blockIdx.x;
-  if (!P.active[b]) return;
-  const InstDesc d = P.inst[b / P.R];
-  const int W = d.W, K1 = P.K1;
+  const int K1 = P.K1;
   const int lane = threadIdx.x & 31;
   const long long base = (long long)b * K1;
+  // every load that depends only on b is issued before any of them is used (one round trip):
+  // the active flag, the descriptor, the survivor count, the first survivor entry of this
+  // thread (bounded by the capacity, used if below the count), and below the list and the
+  // parent
+  const int act = P.active[b];
+  const InstDesc d = P.inst[b / P.R];
   const int S = P.surv_cnt[b];
+  const unsigned long long* sv = P.surv + (long long)b * P.cap;
+  const unsigned long long sv0 = ((int)threadIdx.x < P.cap) ? sv[threadIdx.x] : 0ull;
+  if (!act) return;
+  const int W = d.W;
   if (S > P.cap) {
     if (threadIdx.x == 0) atomicOr(P.status, kStatCapacity);
     return;
@@ -244,7 +252,7 @@ __global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
   const uint64_t ph = P.par_hash[b];
   const int ndup = P.dup_n[b];
   const uint32_t dc0 = (threadIdx.x < K1) ? P.dup_c[base + threadIdx.x] : kNoCand;
-  for (int w = threadIdx.x; w < W; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
+  for (int w = threadIdx.x; w < P.Wmax; w += blockDim.x) pb[w] = P.par_bits[(long long)b * P.Wmax + w];
   for (int r = threadIdx.x; r < K1; r += blockDim.x) {   // two independent coalesced loads
     oslot[r] = P.lst_ord[base + r];
     okey[r] = P.lst_key[base + r];
@@ -262,11 +270,10 @@ __global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
   // exact energy of survivor t and the threshold test E' < T (strict, Alg. 2); the candidate
   // index c (Sec. III flip order) goes into the entry's low bits. Reads the parent's spins from
   // global memory, so the first block of survivors is evaluated before the first barrier.
-  const unsigned long long* sv = P.surv + (long long)b * P.cap;
   const uint64_t* pbg = P.par_bits + (long long)b * P.Wmax;
   const long long* aqb = fp64 ? nullptr : aq_of(P, b, P.iter_t[b]);
   auto eval = [&](int t, unsigned long long& kk, unsigned long long& ent) -> bool {
-    ent = sv[t];
+    ent = (t == (int)threadIdx.x) ? sv0 : sv[t];
     int i, j;
     surv_sites(ent, i, j);
     ent |= (j < 0) ? (uint32_t)i : pair_index(d.n, i, j);
