@@ -435,8 +435,9 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
         }
       }
     } else {
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {   // a as floats too: only used to bin sites
         const float v = (float)a64[i];
+        as[i] = make_float2(v, 0.f);
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
       }
@@ -533,10 +534,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
     const int lim0 = ex ? kSubSites - t1 : kSubSites;   // site slots of the first class
     const float span = fmaxf(amax - amin, 1e-30f);
     const float scale = 255.99f / span;
-    auto bin_of = [&](int i) {
-      const float a = fp64 ? (float)a64[i] : as[i].x;
-      return min(255, (int)((a - amin) * scale));
-    };
+    auto bin_of = [&](int i) { return min(255, (int)((as[i].x - amin) * scale)); };   // both modes stage a
     for (int t = threadIdx.x; t < 256; t += blockDim.x) {
       hist[t] = 0;
       hist2[t] = 0;
@@ -696,17 +694,24 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
     }
   }
   // single flips: dE_i = a_i (not candidates under exchanges)
-  for (int i = threadIdx.x; i < n && P.flips != QIS_FLIPS_EXCHANGE; i += blockDim.x) {
-    bool ok;
+  // (one loop per mode: no FP64 instruction, even predicated off, in the split modes' loop)
+  if (P.flips != QIS_FLIPS_EXCHANGE) {
     if (fp64) {
-      const double e = __dadd_rn(Ep, a64[i]);
-      ok = (e < s_T) && (e <= s_cap);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double e = __dadd_rn(Ep, a64[i]);
+        if ((e < s_T) && (e <= s_cap)) {
+          const int slot = atomicAdd(&s_ns, 1);
+          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, -1);
+        }
+      }
     } else {
-      ok = as[i].x <= s_thr;
-    }
-    if (ok) {
-      const int slot = atomicAdd(&s_ns, 1);
-      if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, -1);
+      const float th = s_thr;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (as[i].x <= th) {
+          const int slot = atomicAdd(&s_ns, 1);
+          if (slot < P.cap) P.surv[(long long)b * P.cap + slot] = surv_entry(i, -1);
+        }
+      }
     }
   }
   __syncthreads();
