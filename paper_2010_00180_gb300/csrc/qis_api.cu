@@ -866,7 +866,13 @@ int qis_search_list(qis_ctx* ctx, int instance_id, int r, uint64_t* bits, double
   std::vector<uint64_t> st(K1), bb((size_t)K1 * Wm);
   std::vector<uint8_t> u(K1);
   CK(cudaMemcpy(ord.data(), ctx->P.lst_ord + b * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(e.data(), ctx->P.lst_E + b * K1, K1 * sizeof(double), cudaMemcpyDeviceToHost));
+  if (ctx->mode == QIS_FP64) {
+    CK(cudaMemcpy(e.data(), ctx->P.lst_E + b * K1, K1 * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {   // the exact integer E 2^q, scaled by 2^-q as on the device
+    std::vector<long long> q(K1);
+    CK(cudaMemcpy(q.data(), ctx->P.lst_q + b * K1, K1 * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < K1; ++k) e[k] = ldexp((double)q[k], -d.q);
+  }
   CK(cudaMemcpy(st.data(), ctx->P.lst_stamp + b * K1, K1 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(u.data(), ctx->P.lst_used + b * K1, K1, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(bb.data(), ctx->P.lst_bits + b * K1 * Wm, bb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));

@@ -57,7 +57,7 @@ struct DevPtrs {
   const uint64_t* zob;    // Zobrist keys [kMaxN]
   // per-search state, search b
   uint64_t* lst_bits;     // [b][K1][Wmax]
-  double* lst_E;          // [b][K1]
+  double* lst_E;          // [b][K1] FP64 mode (and the initial and imported entries); split modes: lst_q
   long long* lst_q;       // [b][K1] exact E * 2^q of each slot (split modes)
   unsigned long long* lst_key;  // [b][K1] order key of the entry of rank r (qkey of E 2^q, or dkey of E)
   uint64_t* lst_stamp;    // [b][K1]

@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) k_final_merge(DevPtrs P) {
     const int cnt = P.lst_count[b];
     for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
       const int slot = P.lst_ord[base + p];
-      nE[p] = P.lst_E[base + slot];
+      // split modes keep the exact integer E 2^q of a state; E = that times 2^-q (exact scaling)
+      nE[p] = (P.mode == QIS_FP64) ? P.lst_E[base + slot] : (double)P.lst_q[base + slot] * d.inv_scale;
       nH[p] = P.lst_hash[base + slot];
       nR[p] = (int)(base + slot);
       nS[p] = ((unsigned long long)r << 32) | (unsigned)p;

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(128) k_pick(DevPtrs P) {
       P.active[b] = 0;
     } else {
       P.lst_used[base + sel] = 1;
-      P.par_E[b] = P.lst_E[base + sel];
+      if (P.mode == QIS_FP64) P.par_E[b] = P.lst_E[base + sel];   // split modes: par_q
       if (P.mode != QIS_FP64) P.par_q[b] = P.lst_q[base + sel];
       P.par_hash[b] = P.lst_hash[base + sel];
       P.par_stamp[b] = P.lst_stamp[base + sel];

@@ -453,9 +453,9 @@ __global__ void __launch_bounds__(kMergeThreads, 8) k_merge(DevPtrs P) {
     if (fp64) {
       P.lst_E[base + slot] = dkey_inv(kp);
     } else {
-      const long long eq = (long long)(kp ^ (1ull << 63));
-      P.lst_q[base + slot] = eq;
-      P.lst_E[base + slot] = (double)eq * d.inv_scale;   // 2^-q: exact
+      // the exact integer E 2^q only: its FP64 value is formed where it is read (the final
+      // merge, the host), not once per new entry on the narrow FP64 pipe
+      P.lst_q[base + slot] = (long long)(kp ^ (1ull << 63));
     }
     P.lst_stamp[base + slot] = ((uint64_t)t_now << 32) | c;
     P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
