@@ -333,28 +333,29 @@ cudaError_t launch_fields_inc(const DevPtrs& P, cudaStream_t s) {
 }
 
 // Candidate index of the kept state x if it is one or two flips from the parent p (the single
-// flip of its differing site, or the pair of its two), else -1. One pass over the W words,
-// loaded in blocks of 8 together.
-__device__ __forceinline__ long long near_code(const uint64_t* x, const uint64_t* p, int W, int n) {
+// flip of its differing site, or the pair of its two), else -1. One pass over the W words: the
+// parent's from shared memory, the state's loaded in batches of ten (one round trip for
+// n <= 640).
+__device__ __forceinline__ long long near_code_sp(const uint64_t* x, const uint64_t* p, int W, int n) {
   int dist = 0, p0 = 0, p1 = 0;
-  for (int w0 = 0; w0 < W; w0 += 8) {
-    uint64_t xw[8];
+  for (int w0 = 0; w0 < W; w0 += 10) {
+    uint64_t xw[10];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) xw[u] = (w0 + u < W) ? (x[w0 + u] ^ p[w0 + u]) : 0ull;
+    for (int u = 0; u < 10; ++u) xw[u] = (w0 + u < W) ? x[w0 + u] : 0ull;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      uint64_t v = xw[u];
+    for (int u = 0; u < 10; ++u) {
+      uint64_t v = (w0 + u < W) ? (xw[u] ^ p[w0 + u]) : 0ull;
       if (v && dist < 2) {
         const int lo = (w0 + u) * 64 + __ffsll((long long)v) - 1;
         if (dist == 0) {
           p0 = lo;
-          v &= v - 1;
-          if (v) p1 = (w0 + u) * 64 + __ffsll((long long)v) - 1;
+          const uint64_t r = v & (v - 1);
+          if (r) p1 = (w0 + u) * 64 + __ffsll((long long)r) - 1;
         } else {
           p1 = lo;
         }
       }
-      dist += __popcll(xw[u]);
+      dist += __popcll(v);
     }
   }
   if (dist == 1) return p0;
@@ -397,13 +398,6 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   const double Ep = __longlong_as_double(epw);   // FP64 mode
   const long long Epq = epw;                     // split modes
   const double* a64 = P.a64 + (long long)b * P.NP;
-  // kept states one or two flips away from the parent: the only candidates that can be
-  // duplicates, each equal to exactly one candidate. The kept states are the list slots
-  // 0 .. cnt-1; slot threadIdx.x is examined here, before the first barrier (the parent's
-  // words from global memory), so its loads overlap the staging below.
-  const long long near0 = ((int)threadIdx.x < cnt)
-                              ? near_code(P.lst_bits + (base + threadIdx.x) * P.Wmax, P.par_bits + (long long)b * P.Wmax, d.W, n)
-                              : -1;
   // {a_i, s_i} of the search, staged once (split modes): every pass below reads shared memory;
   // the range of a_i is taken on the way (a ~ fl32 of the exact value in FP64 mode too: only
   // used to bin sites)
@@ -475,11 +469,13 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   }
   const float amin = fminf(fminf(wmn[0], wmn[1]), fminf(wmn[2], wmn[3]));
   const float amax = fmaxf(fmaxf(wmx[0], wmx[1]), fmaxf(wmx[2], wmx[3]));
-  // their candidate indices go to dup_c for the merge's duplicate test; among the K+1+near
-  // lowest candidates at least K+1 are new states (slots beyond the block size: here)
-  if (near0 >= 0) P.dup_c[base + atomicAdd(&s_near, 1)] = (uint32_t)near0;
-  for (int r = threadIdx.x + blockDim.x; r < cnt; r += blockDim.x) {
-    const long long c = near_code(P.lst_bits + (base + r) * P.Wmax, pb, d.W, n);
+  // kept states one or two flips away from the parent: the only candidates that can be
+  // duplicates, each equal to exactly one candidate (the kept states are the list slots
+  // 0 .. cnt-1; the parent's words are in shared memory by now). Their candidate indices go
+  // to dup_c for the merge's duplicate test; among the K+1+near lowest candidates at least
+  // K+1 are new states.
+  for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+    const long long c = near_code_sp(P.lst_bits + (base + r) * P.Wmax, pb, d.W, n);
     if (c >= 0) P.dup_c[base + atomicAdd(&s_near, 1)] = (uint32_t)c;
   }
   __syncthreads();
