@@ -534,6 +534,20 @@ def roofline(res, pk):
                     "(achieved_evaluated counts only the pairs of evaluated rows)"}
 
 
+def dominant_roofline(res, pk, src):
+    """The roofline of the kernel class with the largest share of the step (per-search bound,
+    pair scan or merge), and the others beside it."""
+    cands = {"bound": roofline_bound(res, pk, src), "merge": roofline_merge(res, pk, src)}
+    if res["flips"] != "single":
+        cands["scan"] = roofline(res, pk)
+    cands = {k: v for k, v in cands.items() if v is not None}
+    dom = max(cands, key=lambda k: res["prof"][k][0])
+    rl = dict(cands[dom], dominant_share=round(res["prof"][dom][0] / res["ms"], 4))
+    others = {v["kernel"]: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac", "launch_us")}
+              for k, v in cands.items() if k != dom}
+    return rl, others
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -604,16 +618,7 @@ def main():
     if rank != 0:
         return
     pk, src = peaks()
-    # the roofline of the kernel class with the largest share of the step (per-search bound,
-    # pair scan or merge); the others beside it
-    cands = {"bound": roofline_bound(res, pk, src), "merge": roofline_merge(res, pk, src)}
-    if flips != "single":
-        cands["scan"] = roofline(res, pk)
-    cands = {k: v for k, v in cands.items() if v is not None}
-    dom = max(cands, key=lambda k: res["prof"][k][0])
-    rl = dict(cands[dom], dominant_share=round(res["prof"][dom][0] / res["ms"], 4))
-    others = {v["kernel"]: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac", "launch_us")}
-              for k, v in cands.items() if k != dom}
+    rl, others = dominant_roofline(res, pk, src)
     value = res["pairs"] / (res["ms"] / 1e3)
     line = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
