@@ -201,8 +201,8 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize(device)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/qis_clocks_{os.getpid()}.csv") as clk:
+    clk_dir = os.environ.get("QIS_CLOCKS_DIR") or "/tmp"   # where the sampled clock log is kept
+    with Clocks(os.path.join(clk_dir, f"qis_clocks_rank{rank}_{os.getpid()}.csv")) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             step()
@@ -344,7 +344,7 @@ def compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_split, device, flips="s
 
 
 def run_warmstart(args, device=0):
-    """Learned warm start vs random initial states (BASELINE config 5): train the network on the
+    """Learned warm start vs random initial states (n = 300 Gaussian instances): train the network on the
     best states the search finds for `n_train` generated n=300 Gaussian instances, then run the
     search from learned and from random initial states on 120 held-out instances for a sweep of
     iteration counts, and report time-to-ground-state for each (reference: the best energy of

@@ -333,7 +333,7 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m);
  * Allocation-free candidate selection (the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory when they need the work done: code running
  * while a stream is being captured into a CUDA graph, real-time loops that must not block in
- * the driver's allocator, plugins whose process owns device memory through another pool).
+ * the CUDA allocator, plugins whose process owns device memory through another pool).
  *
  * For one parent state psi of an n-spin instance it evaluates every single flip and every
  * pair flip with the library's FP64 arithmetic (E' = E(psi) + dE, as in QIS_FP64) and writes
