@@ -59,7 +59,7 @@ def run_pair(ens, n, K, R, I_, precision, seed=0, n_inst=1, per_iter=False, samp
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
-def test_config1_n16_every_iteration(precision):
+def test_gaussian_n16_every_iteration(precision):
     """N=16 Gaussian, seed 0, K=8, R=4, I=K; merged list vs oracle and 2^16 brute force."""
     n, K, R = 16, 8, 4
     ctx, data = run_pair("gaussian", n, K, R, K, precision, seed=0, per_iter=True)
@@ -96,17 +96,17 @@ def test_many_instances_and_merge(precision, ens):
         np.testing.assert_allclose(got["E"], ref["E"], rtol=1e-9)
 
 
-def test_config2_sizes_fp64_sampled():
+def test_gaussian_n100_120x32_fp64_sampled():
     """120 instances, N=100, K=120, R=32, FP64; sampled searches vs the oracle."""
     run_pair("gaussian", 100, K=120, R=32, I_=120, precision="fp64", seed=2, n_inst=120, sample=12)
 
 
-def test_config3_sizes_split_sampled():
+def test_gaussian_n600_120x64_split_sampled():
     """120 instances, N=600, K=120, R=64, split-BF16; sampled searches vs the oracle."""
     run_pair("gaussian", 600, K=120, R=64, I_=120, precision="split_bf16", seed=3, n_inst=120, sample=4)
 
 
-def test_config4_sizes_pm1_sampled():
+def test_pm1_n1024_64x128_sampled():
     """64 instances, N=1024 +-J, K=120, R=128; sampled searches vs the oracle."""
     run_pair("pm1", 1024, K=120, R=128, I_=120, precision="pm1_fp8", seed=4, n_inst=64, sample=3)
 

@@ -128,7 +128,7 @@ def test_candidate_counters_follow_the_flip_set():
         ctx.close()
 
 
-def test_exchange_config3_sizes_sampled():
+def test_exchange_gaussian_n600_120x64_sampled():
     """120 instances, n = 600, K = 120, R = 64, split-BF16, exchanges; sampled searches."""
     n, K, R, iters, n_inst = 600, 120, 64, 120, 120
     ctx = qis.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=n_inst, flips="exchange")

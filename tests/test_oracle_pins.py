@@ -113,7 +113,7 @@ def test_brute_force_matches_enumeration(ens, n):
     assert np.array_equal(bpsi, psi[order[:k]])
 
 
-def test_config1_n16_ground_state_by_brute_force():
+def test_n16_ground_state_by_brute_force():
     """N=16 Gaussian instance, seed 0, K=8 kept (+1 slot), R=4 random initial states, I=K."""
     n, K, R = 16, 8, 4
     J, h = I.instance("gaussian", n, seed=0)
