@@ -37,11 +37,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pair-flip candidates evaluated/s and time-to-ground-state at N=600 on 1 GB300"
-UNIT = "pair candidates/s"
+# every pair of every expanded parent is decided exactly; only a small fraction of them is
+# tested one by one (evaluated_pairs_per_s beside the value)
+UNIT = "logical pair candidates decided/s"
 
 
 def unit_of(flips):
-    return "single-flip candidates/s" if flips == "single" else UNIT
+    return "logical single-flip candidates decided/s" if flips == "single" else UNIT
 
 WORKLOADS = {
     # name: (ensemble, n, instances, K, R, iterations, precision[, flip set])
@@ -77,7 +79,7 @@ def peaks():
 
 # ------------------------------------------------------------------ CPU oracle leg
 def _oracle_job(args):
-    ens, n, K, I_, seed, inst, r, fl = args
+    ens, n, K, I_, seed, inst, r, fl, keep = args
     from oracle import oracle as O
     from paper_2010_00180_gb300 import inputs as I
     J, h = I.instance(ens, n, seed=seed, inst=inst)
@@ -86,25 +88,30 @@ def _oracle_job(args):
     res = O.qi_search(J, h, K, I_, phi, flips=fl)
     m = int(I.unpack_bits(phi, n).sum())
     per = {0: n * (n - 1) // 2, 1: n, 2: m * (n - m)}[fl]   # candidates of the metric per parent
-    return time.perf_counter() - t, res["productive"] * per
+    lst = None
+    if keep:   # this search also runs on the GPU (r < R): its final list for the per-run error
+        c = res["count"]
+        lst = (r, res["bits"][:c].copy(), res["E"][:c].copy())
+    return time.perf_counter() - t, res["productive"] * per, lst
 
 
 def oracle_sample(workload, n_searches, cores, seed):
     """The oracle as it stands on `n_searches` searches of instance 0 (full I iterations each),
     one process per core (spawned before any GPU use)."""
-    ens, n, _, K, _, I_, _, flips = workload_spec(workload)
+    ens, n, _, K, R, I_, _, flips = workload_spec(workload)
     from oracle import oracle as O
     O.build()
-    jobs = [(ens, n, K, I_, seed, 0, r, FLIP_CODES[flips]) for r in range(n_searches)]
+    jobs = [(ens, n, K, I_, seed, 0, r, FLIP_CODES[flips], r < R) for r in range(n_searches)]
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
         out = pool.map(_oracle_job, jobs)
     wall = time.perf_counter() - t0
-    pairs = sum(p for _, p in out)
+    pairs = sum(p for _, p, _ in out)
+    lists = [x for _, _, x in out if x is not None]
     return dict(value=pairs / wall, unit=unit_of(flips), cores=cores, kind="oracle",
                 sample=f"{n_searches} searches x {I_} iterations of instance 0 of {workload} "
-                       f"({pairs:.3e} candidates, {wall:.1f} s wall)", wall_s=wall)
+                       f"({pairs:.3e} candidates, {wall:.1f} s wall)", wall_s=wall, lists=lists)
 
 
 # ------------------------------------------------------------------ clocks
@@ -166,7 +173,18 @@ def make_inputs(workload, seed):
     return data
 
 
-def run_ours(args, rank, world, device):
+def pinned_copy(a):
+    """A copy of the numpy array `a` in page-locked host memory (torch's pinned allocator), so the
+    library's host-to-device copies run at the link's rate."""
+    import torch
+    t = torch.empty(a.shape, dtype={np.float64: torch.float64, np.uint64: torch.int64}[a.dtype.type],
+                    pin_memory=True)
+    out = t.numpy().view(a.dtype)
+    out[...] = a
+    return out, t
+
+
+def run_ours(args, rank, world, device, oracle_lists=None):
     import torch
     import torch.distributed as dist
     from paper_2010_00180_gb300 import build as B, qis as Q
@@ -186,6 +204,8 @@ def run_ours(args, rank, world, device):
         ctx.iterate(I_)
         ctx.merge()
 
+    # the timed steps replay the iteration's CUDA graph (the product path); the per-kernel
+    # split comes from a separate pass of the same steps with every launch bracketed by events
     for _ in range(args.warmup):
         step()
     ctx.synchronize()
@@ -193,9 +213,6 @@ def run_ours(args, rank, world, device):
     pairs0, singles0 = ctx.candidate_count()
     evald0 = ctx.evaluated_pairs()
     surv0 = ctx.survivor_count()
-    for k in range(5):
-        ctx.profile_query(k)                            # drop warm-up timings
-    ctx.profile(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(device)
@@ -210,8 +227,6 @@ def run_ours(args, rank, world, device):
         ctx.synchronize()
         torch.cuda.synchronize(device)
     ms = ev0.elapsed_time(ev1)
-    ctx.profile(False)
-    prof = {name: ctx.profile_query(k) for k, name in enumerate(Q.KERNEL_CLASSES)}
     launches = ctx.kernel_launches() - launches0
     pairs, singles = ctx.candidate_count()
     pairs -= pairs0
@@ -220,6 +235,23 @@ def run_ours(args, rank, world, device):
         pairs = singles
     evald = ctx.evaluated_pairs() - evald0
     surv = ctx.survivor_count() - surv0
+    # per-kernel split: the same steps again, each launch between two events on the library
+    # stream (graph replay off while profiling)
+    prof_steps = max(1, min(args.steps, args.profile_steps))
+    for k in range(len(Q.KERNEL_CLASSES)):
+        ctx.profile_query(k)
+    ctx.profile(True)
+    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    for _ in range(prof_steps):
+        step()
+    ep1.record(stream)
+    ctx.synchronize()
+    ctx.profile(False)
+    prof_ms = ep0.elapsed_time(ep1) / prof_steps
+    prof = {name: ctx.profile_query(k) for k, name in enumerate(Q.KERNEL_CLASSES)}
+    # scale the per-class totals to the timed steps (the class shares of the profiled pass)
+    prof = {k: (v[0] * args.steps / prof_steps, v[1] * args.steps // prof_steps) for k, v in prof.items()}
     t = torch.tensor([ms, float(pairs), float(evald), float(surv)], dtype=torch.float64, device=f"cuda:{device}")
     if world > 1:
         tm = t.clone()
@@ -227,6 +259,25 @@ def run_ours(args, rank, world, device):
         dist.all_reduce(tm[1:], op=dist.ReduceOp.SUM)
         t = tm
     ms_max, pairs_all, evald, surv = float(t[0]), float(t[1]), float(t[2]), float(t[3])
+
+    # error against the FP64 oracle on this run's searches: the oracle's final lists of the
+    # sampled searches of instance 0 (the CPU baseline leg ran them) against the GPU's
+    oracle_err = None
+    if oracle_lists:
+        ctx.reset()
+        ctx.iterate(I_)
+        same, rel = 0, 0.0
+        for r, bits, E in oracle_lists:
+            g = ctx.search_list(0, r)
+            if g["count"] == len(E) and np.array_equal(g["bits"], bits):
+                same += 1
+            m = min(g["count"], len(E))
+            if m:
+                rel = max(rel, float(np.max(np.abs(g["E"][:m] - E[:m]) / np.maximum(np.abs(E[:m]), 1e-300))))
+        oracle_err = {"searches_compared": len(oracle_lists), "identical_kept_lists": same,
+                      "max_rel_energy_err": rel,
+                      "what": f"final kept lists (bits, FP64 energies) of searches r < {len(oracle_lists)} of "
+                              f"instance 0 after {I_} iterations, GPU vs the FP64 oracle"}
 
     # time to ground state (Eq. (tts) of Sec. IV): p1 = fraction of instances whose merged
     # best energy reaches the best-known one, for a sweep of iteration counts of the same
@@ -243,31 +294,47 @@ def run_ours(args, rank, world, device):
     if not args.no_forms and prec != "fp64":
         forms = compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_max / args.steps, device, flips)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers in page-locked memory: every step creates
+    # the instances from J, h (host to device), sets the initial states, iterates and copies
+    # the merged lists of every instance back; one untimed step first
     e2e = None
     if args.e2e_steps > 0:
-        h2d = sum(J.nbytes + h.nbytes + phi.nbytes for J, h, phi in data)
+        pinned = [(pinned_copy(J), pinned_copy(h), pinned_copy(phi)) for J, h, phi in data]
+        hdata = [(J[0], h[0], phi[0]) for J, h, phi in pinned]
+        h2d = sum(J.nbytes + h.nbytes + phi.nbytes for J, h, phi in hdata)
         d2h = n_inst * (K + 1) * ((n + 63) // 64 * 8 + 8 + 8)
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+
+        def e2e_step():
             ctx.clear_instances()
-            ids = ctx.create_instances([(J, h) for J, h, _ in data])
-            for iid, (_, _, phi) in zip(ids, data):
+            ids = ctx.create_instances([(J, h) for J, h, _ in hdata])
+            for iid, (_, _, phi) in zip(ids, hdata):
                 ctx.init_states(iid, phi)
             ctx.iterate(I_)
             ctx.topk_states_all(K + 1)
-        e2e_s = time.perf_counter() - t0
+
+        e2e_step()
+        if world > 1:
+            dist.barrier()
+        ts = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            e2e_step()
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts)
         e2e = dict(value=pairs / args.steps * args.e2e_steps / e2e_s * world, unit=unit_of(flips),
-                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h))
+                   h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(d2h),
+                   ms_per_step=round(e2e_s / args.e2e_steps * 1e3, 3),
+                   ms_per_step_min_max=[round(min(ts) * 1e3, 3), round(max(ts) * 1e3, 3)],
+                   steps=args.e2e_steps, warmup=1, host_buffers="page-locked (pinned)")
     clocks = clk.summary(device)
     digits = ctx.instance_info(0)[1] if n_inst else 0
     pair_scan = ctx.tuning()["pair_scan"]   # 1 output-sensitive, 2 dense tiles (or the FP64 form)
     ctx.close()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
-                digits=digits, workload=args.workload, pair_scan=pair_scan, survivors=surv)
+                digits=digits, workload=args.workload, pair_scan=pair_scan, survivors=surv, sms=sms,
+                prof_ms_per_step=prof_ms, prof_steps=prof_steps, oracle_err=oracle_err)
 
 
 def _timed_run(ctx, stream, iters):
@@ -491,7 +558,7 @@ def roofline(res, pk):
         dur = ms / nl / 1e3
         ops = 6.0 * pairs_per_launch
         achieved = ops / dur / 1e12
-        peak = 1.25 / 2
+        peak = 1.25 / 2   # nominal FP64 rate of the profiling recipe's table (no measured FP64 peak)
         return {"bound": "fp64", "achieved": round(achieved, 4), "peak": peak, "unit": "T FP64 ops/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_scan64",
                 "launch_us": round(dur * 1e6, 2), "ops_per_launch": ops,
@@ -522,7 +589,7 @@ def roofline(res, pk):
     ops_per_launch = 2.0 * pairs_per_launch       # signed add + compare per pair candidate
     achieved = ops_per_launch / dur / 1e12
     clk = pk.get("sm_max_mhz", 2070.0)
-    peak = 152 * 128 * clk * 1e6 / 1e12
+    peak = res["sms"] * 128 * clk * 1e6 / 1e12   # FP32 lanes of the device's SMs at the max clock
     ev = 2.0 * res["evald"] / max(1, nl) / dur / 1e12
     return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
             "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_scan_pairs"),
@@ -556,7 +623,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="steps of the separate pass that times every kernel launch with events")
     ap.add_argument("--cpu-searches", type=int, default=0,
                     help="oracle sample size in searches (0 = 24 per core: ~10 s of wall time)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -602,16 +671,18 @@ def main():
 
     # CPU baseline first: its worker processes are spawned before any GPU call
     cpu = None
+    oracle_lists = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(args.workload, args.cpu_searches or 24 * cores, cores, args.seed)
         cpu.pop("wall_s", None)
+        oracle_lists = cpu.pop("lists", None)
 
     import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     torch.cuda.set_device(local)
-    res = run_ours(args, rank, world, local)
+    res = run_ours(args, rank, world, local, oracle_lists)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -630,9 +701,15 @@ def main():
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["prof"].items()},
             "evaluated_pairs_per_s": res["evald"] / (res["ms"] / 1e3),
             "survivors_per_s": res["survivors"] / (res["ms"] / 1e3),
-            "metric_note": "value = candidates decided exactly per second (every pair of the flip set of every "
-                           "parent: n(n-1)/2 by default); evaluated_pairs_per_s = those tested one by one in "
-                           "the scan"}
+            "oracle_error": res["oracle_err"],
+            "timing": {"timed_steps": "CUDA-graph replay of the iteration (the product path), CUDA events on the "
+                                      "library stream around all timed steps",
+                       "kernel_split": f"separate pass of {res['prof_steps']} steps with every launch between two "
+                                       "events (graph replay off); class totals scaled to the timed steps",
+                       "profiled_ms_per_step": round(res["prof_ms_per_step"], 3), "sms": res["sms"]},
+            "metric_note": "value = logical pair candidates decided exactly per second (every pair of the flip set "
+                           "of every expanded parent: n(n-1)/2 by default); evaluated_pairs_per_s = those tested "
+                           "one by one in the scan; survivors_per_s = those whose exact energy the merge computed"}
     print(json.dumps(line))
 
 

@@ -44,14 +44,19 @@ extern "C" {
 #define QIS_ERR_CAPACITY (-5)     /* a per-search survivor buffer overflowed (raise survivor_cap) */
 #define QIS_ERR_STATE (-6)        /* call out of order (e.g. iterate before init_states) */
 
-/* Arithmetic of the local fields and candidate energies (precision modes). */
-#define QIS_FP64 0        /* plain form: FP64 fields, energies and comparisons, in the same
-                             evaluation order as the definition in oracle-free terms below */
-#define QIS_SPLIT_BF16 1  /* J fixed-point on the 2^-q grid, split into signed 8-bit digits;
-                             exact integer fields from BF16 digit GEMMs (FP32 accumulate);
-                             FP32 candidate filter with a rigorous error band; exact keys */
-#define QIS_PM1_FP8 2     /* integer couplings |J_ij| <= 15 (e.g. +-J), integer h: one FP8
-                             digit, exact integer fields and energies */
+/* Arithmetic of the local fields and candidate energies (precision modes). The names of the two
+ * exact modes are historical (a BF16 hi/lo split and an FP8 digit were planned); what they do on
+ * this GPU is stated beside each. */
+#define QIS_FP64 0        /* plain form: FP64 fields, energies and comparisons, in one fixed
+                             evaluation order (f_i summed with j ascending, E' = E_p + dE) */
+#define QIS_SPLIT_BF16 1  /* exact fixed point: J and h on the grid 2^-q (Jq = J 2^q, int64);
+                             Jq written in balanced base-4096 digits (12-bit, |d| <= 2048; 11-bit
+                             digits, base 2048, above a padded n of 8192), each an exact FP16
+                             integer; fields from one FP16 tensor-core GEMM per digit with FP32
+                             accumulation, exact for any summation order, combined in int64;
+                             FP32 candidate filter with a rigorous error band; exact int64 keys */
+#define QIS_PM1_FP8 2     /* integer couplings |J_ij| <= 15 (e.g. +-J) and integer h: q = 0 and one
+                             FP16 digit, the same exact integer fields and energies */
 
 typedef struct qis_ctx qis_ctx; /* opaque, library-owned */
 
@@ -114,8 +119,9 @@ int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* co
 /* Remove every instance (ids restart at 0); device buffers stay allocated. */
 int qis_clear_instances(qis_ctx* ctx);
 
-/* Grid exponent q and number of 8-bit digits of an instance, and whether its input had to
- * be rounded onto the grid (QIS_SPLIT_BF16 / QIS_PM1_FP8; q = -1 in QIS_FP64). */
+/* Grid exponent q and number of FP16 digits (12-bit balanced digits, 11-bit above a padded n of
+ * 8192) of an instance's fixed-point couplings, and whether its input had to be rounded onto the
+ * grid (QIS_SPLIT_BF16 / QIS_PM1_FP8; q = -1 and 0 digits in QIS_FP64). */
 int qis_instance_info(qis_ctx* ctx, int instance_id, int* q, int* digits, int* rounded);
 
 /* Number of spins n of an instance (e.g. after qis_load); QIS_ERR_INVALID_ARG for an id

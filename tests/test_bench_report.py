@@ -19,7 +19,7 @@ def res(**kw):
                    "merge": (72.0, 600)},
              n=600, n_inst=120, R=64, K=120, pairs=179700 * 7680 * 600.0, evald=770 * 7680 * 600.0,
              survivors=190 * 7680 * 600.0, prec="split_bf16", flips="single_pair", pair_scan=1,
-             workload="gaussian_n600_120x64", ms=250.0)
+             workload="gaussian_n600_120x64", ms=250.0, sms=152)
     r.update(kw)
     return r
 
