@@ -17,6 +17,7 @@
 // every element a call reads is written earlier in that same call, so nothing needs clearing.
 // Calls whose kernels overlap on the GPU (different streams, no ordering) race on the array.
 #include <mutex>
+#include <string>
 
 #include "qis_common.cuh"
 
@@ -178,21 +179,50 @@ extern "C" int qis_select_candidates_noalloc(int n, const double* J, const doubl
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_ptr[dev]) {
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return QIS_ERR_CUDA;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+      if (e != cudaSuccess || !p) {
+        set_global_error((std::string("qis_select_candidates_noalloc: cudaGetSymbolAddress of the scratch array: ") +
+                          cudaGetErrorString(e)).c_str());
+        return QIS_ERR_CUDA;
+      }
       g_na_ptr[dev] = static_cast<NoAllocScratch*>(p);
     }
     if (!g_na_attr[dev]) {
       const int sm_c = kNaChunk * 12, sm_f = next_pow2(kNaBlocks * kNaMaxK) * 12;
-      if (cudaFuncSetAttribute(k_na_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_c) != cudaSuccess ||
-          cudaFuncSetAttribute(k_na_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_f) != cudaSuccess)
+      cudaError_t e = cudaFuncSetAttribute(k_na_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_c);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k_na_final, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_f);
+      if (e != cudaSuccess) {
+        set_global_error((std::string("qis_select_candidates_noalloc: shared-memory attribute: ") +
+                          cudaGetErrorString(e)).c_str());
         return QIS_ERR_CUDA;
+      }
       g_na_attr[dev] = true;
     }
     S = g_na_ptr[dev];
   }
+  // Each launch's own status: cudaLaunchKernel returns the error of that launch (it does not
+  // consume an error the caller's earlier work left in the runtime's last-error state).
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_na_fields<<<1, 256, 0, s>>>(n, J, h, bits, S);
-  k_na_candidates<<<kNaBlocks, 256, kNaChunk * 12, s>>>(n, J, bits, k, S);
-  k_na_final<<<1, 256, next_pow2(kNaBlocks * k) * 12, s>>>(k, S, E_out, c_out, Ep_out);
-  return cudaGetLastError() == cudaSuccess ? QIS_OK : QIS_ERR_CUDA;
+  const auto launched = [](cudaError_t e, const char* kernel) {
+    if (e == cudaSuccess) return QIS_OK;
+    set_global_error((std::string("qis_select_candidates_noalloc: launch of ") + kernel + ": " +
+                      cudaGetErrorString(e)).c_str());
+    return QIS_ERR_CUDA;
+  };
+  {
+    void* args[] = {&n, &J, &h, &bits, &S};
+    const int rc = launched(cudaLaunchKernel((const void*)k_na_fields, dim3(1), dim3(256), args, 0, s), "k_na_fields");
+    if (rc) return rc;
+  }
+  {
+    void* args[] = {&n, &J, &bits, &k, &S};
+    const int rc = launched(cudaLaunchKernel((const void*)k_na_candidates, dim3(kNaBlocks), dim3(256), args,
+                                             (size_t)kNaChunk * 12, s), "k_na_candidates");
+    if (rc) return rc;
+  }
+  {
+    void* args[] = {&k, &S, &E_out, &c_out, &Ep_out};
+    return launched(cudaLaunchKernel((const void*)k_na_final, dim3(1), dim3(256), args,
+                                     (size_t)next_pow2(kNaBlocks * k) * 12, s), "k_na_final");
+  }
 }

@@ -31,13 +31,20 @@ def regular_path(J, h, phi, k):
     return E, c, E0
 
 
-def test_noalloc_selection_equals_regular_path_on_two_calls():
+# (n, k, seed): two ordinary calls in a row, then the documented limits (n = 512 fills 2052 of
+# a block's 4096 candidate slots, k = 128 the final merge's 8192), a tiny n where k is every
+# candidate (n(n+1)/2 = 15) and most blocks hold only padding, and n a multiple of 64 (the
+# last word of the state full)
+CASES = [(300, 100, 11), (150, 64, 12), (512, 128, 13), (5, 15, 14), (128, 50, 15)]
+
+
+def test_noalloc_selection_equals_regular_path_on_consecutive_calls():
     torch = pytest.importorskip("torch")
     build.build()
     qis.load()
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream(dev)
-    for call, (n, k, seed) in enumerate([(300, 100, 11), (150, 64, 12)]):
+    for call, (n, k, seed) in enumerate(CASES):
         J, h = I.instance("gaussian", n, seed=seed)
         phi = I.random_states(n, 1, seed=seed + 1)[0]
         dJ = torch.tensor(J, dtype=torch.float64, device=dev)
