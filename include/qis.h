@@ -139,7 +139,7 @@ int qis_instance_n(qis_ctx* ctx, int instance_id, int* n);
 int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits);
 
 /* Reset every search of every instance to its stored initial state (device-side, no host
- * copy). */
+ * copy). Also clears the device error flags (timeout, survivor overflow) of earlier iterations. */
 int qis_reset(qis_ctx* ctx);
 
 /* Run n_iters iterations of Alg. 3 on every search of every instance (lockstep).
@@ -208,6 +208,16 @@ int qis_energies(qis_ctx* ctx, int instance_id, int count, const uint64_t* bits,
 
 /* Block until all device work of the context is done; reports deferred device errors. */
 int qis_synchronize(qis_ctx* ctx);
+
+/* Bound of every device-side wait of the context's kernels (the mbarrier waits of the tensor-core
+ * field GEMM and of the dense pair scan's staging ring), in ns of %globaltimer (2 s by default;
+ * 1e3 <= limit_ns <= 6e10). A wait that runs out sets the context's timeout flag, reported as
+ * QIS_ERR_DEVICE_TIMEOUT by the next synchronising call; the kernel then waits (at most 2 s) for
+ * the copies and tensor-core operations it already issued, frees its tensor memory and returns,
+ * so the context stays usable: qis_reset clears the flag and restarts the searches.
+ * probe = 1 makes every later field GEMM first wait on a barrier that nothing ever completes, so
+ * that path can be exercised without any fault (failure-detection tests); 0 for normal work. */
+int qis_set_wait_limit(qis_ctx* ctx, uint64_t limit_ns, int probe);
 
 /* Launch statistics: number of kernels this context has launched so far. */
 int qis_kernel_launches(qis_ctx* ctx, uint64_t* count);

@@ -135,9 +135,15 @@ uint64_t state_key(uint64_t seed, int id) {
 int check_status(qis_ctx* ctx) {
   int st = 0;
   CK(cudaMemcpy(&st, ctx->P.status, sizeof(int), cudaMemcpyDeviceToHost));
+  // a timeout first: the kernels after a timed-out one run on fields it did not write, so any
+  // other flag they raise is a consequence
+  if (st & kStatTimeout)
+    return fail(ctx, QIS_ERR_DEVICE_TIMEOUT,
+                "a bounded device-side wait gave up; the searches are undefined until qis_reset");
   if (st & kStatCapacity)
-    return fail(ctx, QIS_ERR_CAPACITY, "a search produced more survivors than survivor_cap; raise survivor_cap");
-  if (st & kStatTimeout) return fail(ctx, QIS_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up");
+    return fail(ctx, QIS_ERR_CAPACITY,
+                "a search produced more survivors than survivor_cap (raise survivor_cap); the searches are "
+                "undefined until qis_reset");
   if (st) return fail(ctx, QIS_ERR_STATE, "device reported an inconsistent search state");
   return 0;
 }
@@ -351,6 +357,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     P.B = 0;
     P.NP = ctx->NP;
     P.flips = ctx->cfg.flips;
+    P.wait_ns = 2000000000ull;
+    P.wait_probe = 0;
     P.J64 = ctx->J64;
     P.Jq = ctx->Jq;
     P.J4 = ctx->J4;
@@ -693,6 +701,7 @@ int qis_clear_instances(qis_ctx* ctx) {
     if (ctx->P.B > 0) CK(cudaMemset(ctx->P.nprod, 0, sizeof(int) * (size_t)ctx->P.B));
     if (ctx->P.B > 0) CK(cudaMemset(ctx->P.npair, 0, sizeof(unsigned long long) * (size_t)ctx->P.B));
   }
+  CK(cudaMemset(ctx->P.status, 0, sizeof(int)));   // device flags of the removed searches
   ctx->inst.clear();
   ctx->inst_ready.clear();
   ctx->init_pending.clear();
@@ -769,6 +778,18 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   CK(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int qis_set_wait_limit(qis_ctx* ctx, uint64_t limit_ns, int probe) {
+  if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
+  if (limit_ns < 1000 || limit_ns > 60000000000ull)
+    return fail(ctx, QIS_ERR_INVALID_ARG, "limit_ns must be in [1e3, 6e10]");
+  if (probe != 0 && probe != 1) return fail(ctx, QIS_ERR_INVALID_ARG, "probe must be 0 or 1");
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->P.wait_ns = limit_ns;
+  ctx->P.wait_probe = probe;
+  drop_graph(ctx);   // the captured iteration holds the old values
   return 0;
 }
 
@@ -1109,10 +1130,27 @@ int qis_save(qis_ctx* ctx, const char* path) {
   return 0;
 }
 
+namespace {
+int load_checkpoint(qis_ctx* ctx, const char* path);
+}
+
 int qis_load(qis_ctx* ctx, const char* path) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
   if (!path) return fail(ctx, QIS_ERR_INVALID_ARG, "path is NULL");
   if (!ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "qis_load needs a context without instances");
+  const int rc = load_checkpoint(ctx, path);
+  if (rc && !ctx->inst.empty()) {
+    // a file that fails part-way leaves no partly restored context: the instances created
+    // before the failing record are removed, so the caller can retry with another file
+    const std::string msg = ctx->err;
+    qis_clear_instances(ctx);
+    ctx->err = msg;
+  }
+  return rc;
+}
+
+namespace {
+int load_checkpoint(qis_ctx* ctx, const char* path) {
   Reader rd;
   {
     FILE* f = fopen(path, "rb");
@@ -1191,6 +1229,7 @@ int qis_load(qis_ctx* ctx, const char* path) {
   ctx->merged_fresh = false;
   return 0;
 }
+}  // namespace
 
 int qis_topk_states(qis_ctx* ctx, int instance_id, int k, uint64_t* bits_out, double* E_out, uint64_t* src_out,
                     int* n_out) {

@@ -100,6 +100,9 @@ struct DevPtrs {
   double* init_E;         // [b] energy of the initial state (set with it)
   long long* init_q;      // [b] the same, exact E 2^q (split modes)
   int* status;            // [0] error bits
+  unsigned long long wait_ns;  // bound of every device-side wait (%globaltimer ns; 2 s by default)
+  int wait_probe;         // 1: the field GEMM's MMA thread first waits on a barrier that nothing
+                          // completes (tests the timeout path); 0 otherwise
   int* nprod;             // [b] productive iterations (a parent was expanded) of search b
   unsigned long long* npair;  // [b] pair candidates of the expanded parents of search b
   unsigned long long* eval_cnt;  // [64] pair terms the FP32 scan evaluated (live rows x chunk width)

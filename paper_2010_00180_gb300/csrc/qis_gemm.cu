@@ -20,8 +20,10 @@
 //   warps 2-5     : epilogue, each on its TMEM lane quarter: stage the tile's parent spins and
 //                   active flags in shared memory, tcgen05.ld the accumulators, exact int64
 //                   combination of the digits, a_i = -2 s_i f_i; release the buffer.
-// Every wait is bounded (2 s of %globaltimer); on timeout the CTA raises kStatTimeout, drains
-// what it issued (again bounded), frees its TMEM and returns.
+// Every wait is bounded (P.wait_ns of %globaltimer, 2 s by default); on timeout the CTA raises
+// kStatTimeout, drains what it issued (those waits bounded by a fixed 2 s: the copies and MMAs
+// in flight complete), frees its TMEM and returns. P.wait_probe makes the MMA thread first wait
+// on a barrier that nothing completes, so that path can be tested without any fault.
 #include <cuda_fp16.h>
 
 #include "qis_common.cuh"
@@ -59,10 +61,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
   return ok != 0;
 }
-// Bounded wait: false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t t0) {
+// Bounded wait: false once `limit` ns have passed since t0.
+constexpr uint64_t kDrainNs = 2000000000ull;   // bound of the waits for work already issued (2 s)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t t0, uint64_t limit) {
   while (!mbar_try(bar, parity)) {
-    if (gtimer() - t0 > 2000000000ull) return false;
+    if (gtimer() - t0 > limit) return false;
   }
   return true;
 }
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], done;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], done, never;
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
   __shared__ uint64_t s_pw[256][2];   // parent spin words of the tile's rows, per search of the tile
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
       mbar_init(&tempty[b], 4);   // one arrival per epilogue warp
     }
     mbar_init(&done, 1);
+    mbar_init(&never, 1);   // no thread ever arrives here (the timeout probe)
     s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
       const int kc_total = d.n_pad / kKC;
       for (int kc = 0; kc < kc_total; ++kc, ++it) {
         const int s = it % S;
-        if (it >= S && !mbar_wait(&empty[s], ((it / S) + 1) & 1, t0)) {
+        if (it >= S && !mbar_wait(&empty[s], ((it / S) + 1) & 1, t0, P.wait_ns)) {
           atomicOr(&s_err, 1);
           break;
         }
@@ -186,18 +190,19 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
     // drain: after an error the last (at most S) issued stages may still be in flight; each
     // stage's full barrier is in the phase armed last, so the parity waits are exact
     if (*(volatile int*)&s_err) {
-      for (int k = max(0, it - S); k < it; ++k) mbar_wait(&full[k % S], (k / S) & 1, gtimer());
+      for (int k = max(0, it - S); k < it; ++k) mbar_wait(&full[k % S], (k / S) & 1, gtimer(), kDrainNs);
     }
   } else if (threadIdx.x == 32) {
     // ---------------- MMA issuer: tile lt accumulates into TMEM buffer lt % nbuf
     const uint32_t idesc = idesc_f16(NT);
     int it = 0, lt = 0;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (P.wait_probe && !mbar_wait(&never, 0, t0, P.wait_ns)) atomicOr(&s_err, 8);   // always runs out
+    for (int tile = blockIdx.x; tile < n_tiles && !*(volatile int*)&s_err; tile += gridDim.x) {
       const int inst = tile / tpi, m0 = ((tile % tpi) / n_nt) * 128;
       const InstDesc d = P.inst[inst];
       if (m0 >= d.n_pad || skip(tile)) continue;
       const int buf = lt % nbuf, use = lt / nbuf;
-      if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1, t0)) {
+      if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1, t0, P.wait_ns)) {
         atomicOr(&s_err, 2);
         break;
       }
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
       bool ok = true;
       for (int kc = 0; kc < kc_total; ++kc, ++it) {
         const int s = it % S;
-        if (!mbar_wait(&full[s], (it / S) & 1, t0)) {
+        if (!mbar_wait(&full[s], (it / S) & 1, t0, P.wait_ns)) {
           atomicOr(&s_err, 2);
           ok = false;
           break;
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
       ++lt;
     }
     mma_commit(&done);           // every MMA issued so far completes -> done
-    mbar_wait(&done, 0, gtimer());
+    mbar_wait(&done, 0, gtimer(), kDrainNs);
   } else if (warp >= 2) {
     // ---------------- epilogue warps 2-5: TMEM lane quarter (warp % 4), exact int64 fields
     const int quarter = warp & 3, etid = threadIdx.x - 64;
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(192, 1) k_fields_tc(const __half* __restrict__
         s_pw[t][0] = valid ? P.par_bits[b * G.Wmax + w0] : 0ull;
         s_pw[t][1] = (valid && w0 + 1 < G.Wmax) ? P.par_bits[b * G.Wmax + w0 + 1] : 0ull;
       }
-      const bool ok = mbar_wait(&tfull[buf], use & 1, t0);
+      const bool ok = mbar_wait(&tfull[buf], use & 1, t0, P.wait_ns);
       if (epi_vote(!ok || *(volatile int*)&s_err != 0)) {   // also orders the staging above
         if (!ok) atomicOr(&s_err, 4);
         break;

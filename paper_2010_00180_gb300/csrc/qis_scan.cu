@@ -73,7 +73,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 constexpr int kRing = 2;                      // staging ring depth (power of two)
 constexpr int kPer = 8;                       // searches per ring slot (two liveness ballots)
-constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait: 2 s
+constexpr uint64_t kDrainNs = 2000000000ull;   // bound of the waits for copies already issued: 2 s
 
 // Staging ring of one block: slot u % kRing holds searches kPer u .. kPer u + kPer - 1. full[q]
 // completes a phase when the slot's bulk copies have landed; rel[q] counts the warps' releases.
@@ -168,7 +168,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
     // bounded wait for the slot; an error anywhere in the block ends every warp's loop
     bool ready = mbar_try(&sm.full[q], par);
     while (!ready) {
-      if (*(volatile int*)&sm.err || gtimer() - t0 > kWaitNs) break;
+      if (*(volatile int*)&sm.err || gtimer() - t0 > P.wait_ns) break;
       ready = mbar_try(&sm.full[q], par);
     }
     if (!__all_sync(0xffffffffu, ready)) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ void scan_task(const DevPtrs& P, const InstDesc& d, i
       if (sm.issued[q] == 0) continue;
       const uint32_t par = (uint32_t)(sm.issued[q] - 1) & 1u;
       const uint64_t t1 = gtimer();
-      while (!mbar_try(&sm.full[q], par) && gtimer() - t1 < kWaitNs) {
+      while (!mbar_try(&sm.full[q], par) && gtimer() - t1 < kDrainNs) {
       }
     }
   }

@@ -27,6 +27,7 @@ SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance",
            "qis_set_incremental_fields",
            "qis_topk_states", "qis_merge", "qis_energies", "qis_synchronize", "qis_kernel_launches",
            "qis_candidate_count", "qis_get_stream", "qis_profile_enable", "qis_profile_query",
+           "qis_set_wait_limit",
            "qis_select_candidates_noalloc",
            "qis_mlp_create", "qis_mlp_destroy", "qis_mlp_last_error", "qis_mlp_num_params", "qis_mlp_get_params",
            "qis_mlp_set_params", "qis_mlp_features", "qis_mlp_add_example", "qis_mlp_clear_examples",
@@ -118,6 +119,7 @@ def load():
         "qis_mlp_train": (I, [P, I, C.c_float, C.POINTER(C.c_double)]),
         "qis_init_states_learned": (I, [P, I, P]),
         "qis_set_incremental_fields": (I, [P, I]),
+        "qis_set_wait_limit": (I, [P, U64, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -371,6 +373,11 @@ class Context:
         ms, n = C.c_double(), C.c_uint64()
         self._check(self.lib.qis_profile_query(self.h, k, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def set_wait_limit(self, limit_ns: int, probe: bool = False):
+        """Bound of the kernels' device-side waits (qis_set_wait_limit); probe makes the field
+        GEMM wait on a barrier nothing completes, so the timeout path runs (tests)."""
+        self._check(self.lib.qis_set_wait_limit(self.h, int(limit_ns), int(probe)))
 
     def init_states_learned(self, iid: int, mlp: "MLP"):
         """Initial states of instance iid proposed by the network (qis_init_states_learned)."""

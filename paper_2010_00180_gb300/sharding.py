@@ -19,6 +19,7 @@ instance wherever it runs, so the result is the single-process result exactly.
 from __future__ import annotations
 
 from dataclasses import dataclass
+from datetime import timedelta
 
 import numpy as np
 
@@ -66,6 +67,36 @@ def split_instances(shards: list[list[Shard]]) -> set[int]:
         for s in mine:
             seen[s.instance] = seen.get(s.instance, 0) + 1
     return {i for i, c in seen.items() if c > 1}
+
+
+class PeerLost(RuntimeError):
+    """A process of the run did not reach a step (it raised, exited or never joined)."""
+
+    def __init__(self, step: int, missing: list[int]):
+        super().__init__(f"step {step}: rank(s) {missing} did not arrive")
+        self.step = step
+        self.missing = missing
+
+
+def check_peers(store, step: int, rank: int, world: int, timeout_s: float = 10.0) -> None:
+    """Host-side liveness check between steps, before the next launch or collective: every
+    process announces `step` in the key-value store (torch.distributed.TCPStore or any store
+    with set/wait/check), then waits at most `timeout_s` for every other process's announcement.
+    Raises PeerLost naming the processes that never announced (a process that left between
+    steps), so the survivors stop instead of blocking in a collective that cannot complete."""
+    keys = [f"qis/alive/{step}/{k}" for k in range(world)]
+    store.set(keys[rank], "1")
+    try:
+        store.wait(keys, timedelta(seconds=timeout_s))
+    except Exception:   # timeout, or the store's server process itself is gone
+        missing = []
+        for k, key in enumerate(keys):
+            try:
+                if not store.check([key]):
+                    missing.append(k)
+            except Exception:
+                missing.append(k)
+        raise PeerLost(step, missing or [k for k in range(world) if k != rank]) from None
 
 
 def gather_lists(local: dict, shards: list[list[Shard]], rank: int, group=None) -> dict:

@@ -98,6 +98,32 @@ def test_load_rejects_bad_files(tmp_path):
     b.close()
 
 
+def test_load_failing_part_way_leaves_no_instances(tmp_path):
+    """A checkpoint whose second instance does not fit the context (n = 80 > max_n = 60) fails
+    after the first instance was created: the load removes it again, so a retry with a good
+    file succeeds in the same context and continues the saved searches exactly."""
+    big, good = str(tmp_path / "two.bin"), str(tmp_path / "one.bin")
+    a = make_ctx("gaussian", "split_bf16", [40, 80])
+    a.iterate(3)
+    a.save(big)
+    a.close()
+    a = make_ctx("gaussian", "split_bf16", [40])
+    a.iterate(3)
+    a.save(good)
+    a.iterate(4)
+    want = snapshot(a, 1, 4)
+    a.close()
+    b = qis.Context(K=20, R=4, precision="split_bf16", max_n=60, max_instances=2)
+    with pytest.raises(qis.QISError) as e:
+        b.load(big)
+    assert e.value.name == "INVALID_ARG" and "max_n" in str(e.value)
+    assert b.lib.qis_instance_n(b.h, 0, None) != 0          # no instance left behind
+    b.load(good)
+    b.iterate(4)
+    same_lists(want, snapshot(b, 1, 4))
+    b.close()
+
+
 def test_set_search_list_roundtrip_and_checks():
     a = make_ctx("gaussian", "split_bf16", [90], R=2)
     a.iterate(5)

@@ -109,3 +109,60 @@ def test_gather_to_owner_gives_single_process_merge(n_inst, R):
             assert tuple(ref["bits"][qpos].tolist()) == tx
             assert ref["E"][qpos] == e
             assert int(ref["src"][qpos]) == (r << 32) | pos
+
+
+def _leaver(rank, world, port, steps_of_rank, q):
+    """A gloo process group over a host TCPStore; each step is the liveness check and then a
+    collective. Rank `rank` runs steps 0 .. steps_of_rank[rank] - 1 and then leaves (a process
+    that exits between steps, with nothing in flight); a rank that does not leave reports the
+    PeerLost it gets at the liveness check, before it would enter a collective that cannot
+    complete."""
+    done = 0
+    try:
+        sys.path.insert(0, ROOT)
+        import datetime
+        import torch
+        import torch.distributed as dist
+        from paper_2010_00180_gb300 import sharding as S
+        store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=datetime.timedelta(seconds=30),
+                              wait_for_workers=False)
+        dist.init_process_group("gloo", store=store, rank=rank, world_size=world,
+                                timeout=datetime.timedelta(seconds=30))
+        for step in range(steps_of_rank[rank]):
+            S.check_peers(store, step, rank, world, timeout_s=3.0)
+            x = torch.ones(1)
+            dist.all_reduce(x)                  # the step's exchange
+            assert x.item() == world
+            done += 1
+        q.put((rank, done, None))
+        if rank == 0:                           # the store's server stays up until the others are done
+            import time
+            time.sleep(5.0)
+    except Exception as e:
+        q.put((rank, done, e.missing if hasattr(e, "missing") else repr(e)))
+
+
+def test_a_rank_that_leaves_between_steps_is_reported_not_waited_for():
+    """World size 2 on CPU with gloo: rank 1 takes part in steps 0 and 1 (check and all_reduce)
+    and exits; rank 0 reaches step 2, where the host liveness check raises PeerLost naming rank 1
+    within its 3 s timeout instead of blocking in the all_reduce."""
+    import multiprocessing as mp
+    import time
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    steps = {0: 5, 1: 2}
+    t0 = time.time()
+    ps = [ctx.Process(target=_leaver, args=(k, world, port, steps, q)) for k in range(world)]
+    for p in ps:
+        p.start()
+    out = {}
+    for _ in range(world):
+        rank, done, err = q.get(timeout=120)
+        out[rank] = (done, err)
+    for p in ps:
+        p.join(timeout=60)
+    assert out[1] == (2, None)                 # left after its two steps, no error of its own
+    assert out[0] == (2, [1])                  # rank 0 stopped at step 2, naming rank 1
+    assert time.time() - t0 < 60
