@@ -135,22 +135,26 @@ def _upper_pairs(n: int):
     return iu, ju
 
 
-def instance(ensemble: str, n: int, seed: int, inst: int = 0, grid_bits: int = GRID_BITS):
+def instance(ensemble: str, n: int, seed: int, inst: int = 0, grid_bits: int | None = GRID_BITS):
     """One Ising instance: (J, h) with J symmetric (n x n, zero diagonal) and h (n,), FP64.
 
     Draw number k of the coupling stream is the k-th pair (i, j), i < j, in lexicographic order.
+    grid_bits=None keeps the real-valued draws as they come (full FP64 values, not on a grid).
     """
+    def rnd(x):
+        return x if grid_bits is None else to_grid(x, grid_bits)
+
     kj = stream_key(seed, inst, TAG_J)
     kh = stream_key(seed, inst, TAG_H)
     iu, ju = _upper_pairs(n)
     cnt = np.arange(iu.size, dtype=np.uint64)
     hc = np.arange(n, dtype=np.uint64)
     if ensemble == "gaussian":
-        vals = to_grid(gaussian(kj, cnt), grid_bits)
-        h = to_grid(gaussian(kh, hc), grid_bits)
+        vals = rnd(gaussian(kj, cnt))
+        h = rnd(gaussian(kh, hc))
     elif ensemble == "uniform":
-        vals = to_grid(uniform01(kj, cnt), grid_bits) - 0.5
-        h = to_grid(uniform01(kh, hc), grid_bits) - 0.5
+        vals = rnd(uniform01(kj, cnt)) - 0.5
+        h = rnd(uniform01(kh, hc)) - 0.5
     elif ensemble == "pm1":
         vals = np.where((splitmix64(kj, cnt) >> np.uint64(63)) == 1, -1.0, 1.0)
         h = np.floor(uniform01(kh, hc) * 3.0) - 1.0

@@ -101,16 +101,6 @@ def test_gaussian_n100_120x32_fp64_sampled():
     run_pair("gaussian", 100, K=120, R=32, I_=120, precision="fp64", seed=2, n_inst=120, sample=12)
 
 
-def test_gaussian_n600_120x64_split_sampled():
-    """120 instances, N=600, K=120, R=64, split-BF16; sampled searches vs the oracle."""
-    run_pair("gaussian", 600, K=120, R=64, I_=120, precision="split_bf16", seed=3, n_inst=120, sample=4)
-
-
-def test_pm1_n1024_64x128_sampled():
-    """64 instances, N=1024 +-J, K=120, R=128; sampled searches vs the oracle."""
-    run_pair("pm1", 1024, K=120, R=128, I_=120, precision="pm1_fp8", seed=4, n_inst=64, sample=3)
-
-
 def test_mixed_sizes_one_batch():
     """One context holding instances of different n (the mixed batch of N in {200,350,500,700}),
     scaled down in K and I."""
