@@ -3,10 +3,12 @@
  * Ueda, Otsuka and Yunoki, "Quantum-inspired search method for low-energy states of
  * classical Ising Hamiltonians" (arXiv 2010.00180).
  *
- * TEST INFRASTRUCTURE ONLY. Plain, slow, single-threaded FP64 code that follows the
- * paper's Algorithms 1-4 step by step. Only the test suite, the smoke check and the
- * CPU-baseline leg of the benchmark load it; the library's product path never does.
- * It shares no code, header or table with the CUDA path.
+ * TEST INFRASTRUCTURE ONLY. Plain, slow, single-threaded FP64 code that restates what the
+ * paper's Algorithms 1-4 compute, in their order, from the definitions of Sec. III: the flip
+ * sets, the incremental energy, and the kept states of Alg. 2 as an ordered set with its
+ * admission rule. Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark load it; the library's product path never does. It shares no code, header or
+ * table with the CUDA path.
  *
  * Conventions (Sec. III, Eq. (4)):
  *   state psi = sum_i 2^i sigma_i, stored as W = ceil(N/64) little-endian uint64 words;
@@ -58,15 +60,6 @@
 static int nwords(int n) { return (n + 63) / 64; }
 static int get_sigma(const uint64_t* b, int i) { return (int)((b[i >> 6] >> (i & 63)) & 1u); }
 static double spin(const uint64_t* b, int i) { return get_sigma(b, i) ? -1.0 : 1.0; }
-
-/* Compare two states as the integers psi of Eq. (4): most significant word first. */
-static int cmp_state(const uint64_t* a, const uint64_t* b, int W) {
-  for (int w = W - 1; w >= 0; --w) {
-    if (a[w] < b[w]) return -1;
-    if (a[w] > b[w]) return 1;
-  }
-  return 0;
-}
 
 /* ---------------------------------------------------------------- Eq. (1) */
 double orc_energy(int n, const double* J, const double* h, const uint64_t* bits) {
@@ -134,179 +127,202 @@ void orc_candidates(int n, const double* J, const double* h, const uint64_t* bit
   orc_candidates_flips(n, J, h, bits, 0, out);
 }
 
-/* ------------------------------------------------------------ state lists */
-/* The four lists of Alg. 2: psi (energy order), psi' (ascending integer order), E, l.
- * Placeholders (I_M in psi/psi', R_M in E) are flagged `empty`; an empty psi' entry
- * compares above every state, like the maximum integer I_M. */
+/* ------------------------------------------------------------ kept states */
+/* What Alg. 2 maintains, stated as a data structure: the kept states of a search, at most
+ * K+1 of them, in ascending order of the key (E, arrival). Its rules follow from Sec. III:
+ *   - a state is kept at most once (a generated state already kept is skipped);
+ *   - a new state arrives after every state already kept, so among equal energies it ranks
+ *     last: it is placed after every kept state with E <= E';
+ *   - only the K+1 lowest keys are kept: when all K+1 places are taken, a new state enters
+ *     only if its key precedes the last one, i.e. E' < E_{K+1} strictly (its arrival is later),
+ *     and the last state leaves.
+ * Unfilled places are the listing's placeholders (I_M, R_M): they are simply absent here.
+ * Membership is a hash set of the kept states (open addressing with linear probing, FNV-1a 64
+ * over the state's words); a removed state is taken out by shifting later members of its
+ * probe run back, so no tombstones accumulate. */
 typedef struct {
-  int n, W, K1;
-  uint64_t* psi;     /* K1 x W, energy order */
+  int n, W, K1, count;
+  uint64_t* psi;     /* K1 x W, key order; entries 0 .. count-1 are kept states */
   double* E;         /* K1 */
   uint8_t* l;        /* K1: used as a parent */
-  uint8_t* empty;    /* K1 */
   uint64_t* stamp;   /* K1 (bookkeeping) */
   uint64_t* src;     /* K1 (bookkeeping for Alg. 4: (search << 32) | position) */
-  uint64_t* psis;    /* K1 x W, psi' in ascending order */
-  uint8_t* psis_empty;
-} qlist;
+  uint64_t* hkey;    /* hcap x W: the member states of the hash set */
+  uint8_t* hused;    /* hcap: slot occupied */
+  int hcap;          /* power of two >= 4 K1 */
+} kept_set;
 
-static void list_free(qlist* L) {
-  free(L->psi); free(L->E); free(L->l); free(L->empty); free(L->stamp); free(L->src);
-  free(L->psis); free(L->psis_empty);
+static uint64_t state_hash(const uint64_t* x, int W) {
+  uint64_t h = 0xcbf29ce484222325ull;   /* FNV-1a, 64 bits, over the bytes of the words */
+  for (int w = 0; w < W; ++w)
+    for (int b = 0; b < 8; ++b) {
+      h ^= (x[w] >> (8 * b)) & 0xffu;
+      h *= 0x100000001b3ull;
+    }
+  return h;
 }
 
-static int list_init(qlist* L, int n, int K) {
-  memset(L, 0, sizeof(*L));
-  L->n = n; L->W = nwords(n); L->K1 = K + 1;
-  L->psi = calloc((size_t)L->K1 * L->W, 8);
-  L->E = calloc(L->K1, sizeof(double));
-  L->l = calloc(L->K1, 1);
-  L->empty = calloc(L->K1, 1);
-  L->stamp = calloc(L->K1, 8);
-  L->src = calloc(L->K1, 8);
-  L->psis = calloc((size_t)L->K1 * L->W, 8);
-  L->psis_empty = calloc(L->K1, 1);
-  if (!L->psi || !L->E || !L->l || !L->empty || !L->stamp || !L->src || !L->psis || !L->psis_empty) {
-    list_free(L);
-    return ORC_ENOMEM;
+/* Slot of x in the hash set, or the empty slot where its probe run ends. */
+static int hs_find(const kept_set* S, const uint64_t* x, int* present) {
+  int pos = (int)(state_hash(x, S->W) & (uint64_t)(S->hcap - 1));
+  while (S->hused[pos]) {
+    if (memcmp(S->hkey + (size_t)pos * S->W, x, (size_t)S->W * 8) == 0) {
+      *present = 1;
+      return pos;
+    }
+    pos = (pos + 1) & (S->hcap - 1);
   }
-  for (int k = 0; k < L->K1; ++k) {
-    L->E[k] = DBL_MAX;         /* R_M */
-    L->empty[k] = 1;           /* I_M */
-    L->psis_empty[k] = 1;
-    L->stamp[k] = UINT64_MAX;
-    L->src[k] = UINT64_MAX;
+  *present = 0;
+  return pos;
+}
+
+static int hs_contains(const kept_set* S, const uint64_t* x) {
+  int present;
+  hs_find(S, x, &present);
+  return present;
+}
+
+static void hs_insert(kept_set* S, const uint64_t* x) {
+  int present;
+  const int pos = hs_find(S, x, &present);
+  if (present) return;
+  memcpy(S->hkey + (size_t)pos * S->W, x, (size_t)S->W * 8);
+  S->hused[pos] = 1;
+}
+
+/* Remove x; later members of the probe run move back into the gap when their home slot does
+ * not lie cyclically in (gap, their slot]. */
+static void hs_remove(kept_set* S, const uint64_t* x) {
+  int present;
+  int gap = hs_find(S, x, &present);
+  if (!present) return;
+  const int m = S->hcap - 1;
+  S->hused[gap] = 0;
+  for (int j = (gap + 1) & m; S->hused[j]; j = (j + 1) & m) {
+    const int home = (int)(state_hash(S->hkey + (size_t)j * S->W, S->W) & (uint64_t)m);
+    const int stays = (gap <= j) ? (gap < home && home <= j) : (gap < home || home <= j);
+    if (stays) continue;
+    memcpy(S->hkey + (size_t)gap * S->W, S->hkey + (size_t)j * S->W, (size_t)S->W * 8);
+    S->hused[gap] = 1;
+    S->hused[j] = 0;
+    gap = j;
+  }
+}
+
+static void kept_free(kept_set* S) {
+  free(S->psi); free(S->E); free(S->l); free(S->stamp); free(S->src); free(S->hkey); free(S->hused);
+}
+
+static int kept_init(kept_set* S, int n, int K) {
+  memset(S, 0, sizeof(*S));
+  S->n = n; S->W = nwords(n); S->K1 = K + 1; S->count = 0;
+  S->hcap = 4;
+  while (S->hcap < 4 * S->K1) S->hcap <<= 1;
+  S->psi = calloc((size_t)S->K1 * S->W, 8);
+  S->E = calloc(S->K1, sizeof(double));
+  S->l = calloc(S->K1, 1);
+  S->stamp = calloc(S->K1, 8);
+  S->src = calloc(S->K1, 8);
+  S->hkey = calloc((size_t)S->hcap * S->W, 8);
+  S->hused = calloc(S->hcap, 1);
+  if (!S->psi || !S->E || !S->l || !S->stamp || !S->src || !S->hkey || !S->hused) {
+    kept_free(S);
+    return ORC_ENOMEM;
   }
   return ORC_OK;
 }
 
-/* Binary_search of Alg. 2 over psi': returns p (0..K1) with psi'_p <= x < psi'_{p+1}
- * in 1-based terms, i.e. the number of entries <= x, and sets *found when psi'_p == x. */
-static int bsearch_state(const qlist* L, const uint64_t* x, int* found) {
-  int lo = 0, hi = L->K1; /* count of entries <= x lies in [lo, hi] */
-  while (lo < hi) {
-    int mid = (lo + hi) / 2;
-    int le = L->psis_empty[mid] ? 0 : (cmp_state(L->psis + (size_t)mid * L->W, x, L->W) <= 0);
-    if (le) lo = mid + 1; else hi = mid;
-  }
-  *found = (lo > 0 && !L->psis_empty[lo - 1] && cmp_state(L->psis + (size_t)(lo - 1) * L->W, x, L->W) == 0);
-  return lo;
+/* Whether a new state of energy e would be kept (the K+1 rule above). */
+static int admissible(const kept_set* S, double e) {
+  return S->count < S->K1 || e < S->E[S->K1 - 1];
 }
 
-/* Binary_search of Alg. 2 over E: number of entries with E_k <= e (insertion after equals). */
-static int bsearch_energy(const qlist* L, double e) {
-  int lo = 0, hi = L->K1;
-  while (lo < hi) {
-    int mid = (lo + hi) / 2;
-    if (L->E[mid] <= e) lo = mid + 1; else hi = mid;
+/* Offer state x (not a member) with energy e and flag l: kept if admissible, after every kept
+ * state with E <= e; the last state leaves when all K+1 places were taken. */
+static void offer(kept_set* S, const uint64_t* x, double e, uint8_t l, uint64_t stamp, uint64_t src) {
+  if (!admissible(S, e)) return;
+  const int W = S->W;
+  if (S->count == S->K1) {
+    hs_remove(S, S->psi + (size_t)(S->K1 - 1) * W);
+    S->count -= 1;
   }
-  return lo;
-}
-
-/* update_list_sub of Alg. 2: if E < E_{K+1}, drop slot K+1 and insert (x, E, l) after every
- * entry of energy <= E; keep psi' sorted (remove the dropped state, insert x at p'). */
-static void update_list_sub(qlist* L, const uint64_t* x, double e, uint8_t l, int pprime,
-                            uint64_t stamp, uint64_t src) {
-  const int W = L->W, K1 = L->K1;
-  if (!(e < L->E[K1 - 1])) return;
-  /* position of the evicted state psi_{K+1} in psi' */
-  int pe;
-  if (L->empty[K1 - 1]) {
-    pe = K1 - 1; /* an I_M entry: the last one of psi' */
-  } else {
-    int f;
-    pe = bsearch_state(L, L->psi + (size_t)(K1 - 1) * W, &f) - 1;
+  int p = 0;   /* first place whose energy exceeds e (binary search over the kept energies) */
+  int hi = S->count;
+  while (p < hi) {
+    const int mid = (p + hi) / 2;
+    if (S->E[mid] <= e) p = mid + 1; else hi = mid;
   }
-  /* psi': remove index pe, insert x so that it follows the first pprime entries of the old list */
-  int ins = pprime; /* 0-based insertion index in the old list */
-  if (pe < ins) {
-    memmove(L->psis + (size_t)pe * W, L->psis + (size_t)(pe + 1) * W, (size_t)(ins - 1 - pe) * W * 8);
-    memmove(L->psis_empty + pe, L->psis_empty + pe + 1, (size_t)(ins - 1 - pe));
-    ins -= 1;
-  } else {
-    memmove(L->psis + (size_t)(ins + 1) * W, L->psis + (size_t)ins * W, (size_t)(pe - ins) * W * 8);
-    memmove(L->psis_empty + ins + 1, L->psis_empty + ins, (size_t)(pe - ins));
-  }
-  memcpy(L->psis + (size_t)ins * W, x, (size_t)W * 8);
-  L->psis_empty[ins] = 0;
-  /* energy-ordered lists: insert after all entries with E_k <= e, drop the last */
-  int p = bsearch_energy(L, e);
-  int tail = K1 - 1 - p;
-  memmove(L->psi + (size_t)(p + 1) * W, L->psi + (size_t)p * W, (size_t)tail * W * 8);
-  memmove(L->E + p + 1, L->E + p, (size_t)tail * sizeof(double));
-  memmove(L->l + p + 1, L->l + p, (size_t)tail);
-  memmove(L->empty + p + 1, L->empty + p, (size_t)tail);
-  memmove(L->stamp + p + 1, L->stamp + p, (size_t)tail * 8);
-  memmove(L->src + p + 1, L->src + p, (size_t)tail * 8);
-  memcpy(L->psi + (size_t)p * W, x, (size_t)W * 8);
-  L->E[p] = e;
-  L->l[p] = l;
-  L->empty[p] = 0;
-  L->stamp[p] = stamp;
-  L->src[p] = src;
+  const int tail = S->count - p;
+  memmove(S->psi + (size_t)(p + 1) * W, S->psi + (size_t)p * W, (size_t)tail * W * 8);
+  memmove(S->E + p + 1, S->E + p, (size_t)tail * sizeof(double));
+  memmove(S->l + p + 1, S->l + p, (size_t)tail);
+  memmove(S->stamp + p + 1, S->stamp + p, (size_t)tail * 8);
+  memmove(S->src + p + 1, S->src + p, (size_t)tail * 8);
+  memcpy(S->psi + (size_t)p * W, x, (size_t)W * 8);
+  S->E[p] = e;
+  S->l[p] = l;
+  S->stamp[p] = stamp;
+  S->src[p] = src;
+  S->count += 1;
+  hs_insert(S, x);
 }
 
 /* ---------------------------------------------------------------- Alg. 3 */
-/* One QI single search. The list starts as [psi0, placeholders]; each of I iterations
- * takes the first unused entry (in list order) as the parent and pushes all of its
- * single and pair flips through update_list (Alg. 2).
- * update_list computes E' first and performs the duplicate binary search only when
- * E' < E_{K+1}: both tests are side-effect free and the insertion needs both, so the
- * outcome equals the paper's search-first order. */
+/* One QI single search. The kept states start as {psi0} (the other K places unfilled); each of
+ * I iterations takes as the parent the first kept state, in key order, not yet used, marks it
+ * used, and offers every candidate of its flip set, in the candidate order of Sec. III, to the
+ * kept states. A candidate's energy and the K+1 rule are tested before the membership test:
+ * both are free of side effects, so the outcome is that of testing membership first. */
 static int qi_search(const double* J, const double* h, int n, int K, int I, int flips, const uint64_t* psi0,
-                     qlist* L, int* n_productive) {
+                     kept_set* S, int* n_productive) {
   const int W = nwords(n);
-  int rc = list_init(L, n, K);
+  int rc = kept_init(S, n, K);
   if (rc) return rc;
   double* f = malloc((size_t)n * sizeof(double));
   uint64_t* parent = malloc((size_t)W * 8);
   uint64_t* x = malloc((size_t)W * 8);
-  if (!f || !parent || !x) { free(f); free(parent); free(x); list_free(L); return ORC_ENOMEM; }
+  if (!f || !parent || !x) { free(f); free(parent); free(x); kept_free(S); return ORC_ENOMEM; }
 
-  memcpy(L->psi, psi0, (size_t)W * 8);
-  L->E[0] = orc_energy(n, J, h, psi0);
-  L->empty[0] = 0;
-  L->stamp[0] = 0;
-  memcpy(L->psis, psi0, (size_t)W * 8);
-  L->psis_empty[0] = 0;
+  offer(S, psi0, orc_energy(n, J, h, psi0), 0, 0, 0);
 
   int prod = 0;
   for (int it = 1; it <= I; ++it) {
-    int k;
-    for (k = 0; k < L->K1; ++k)
-      if (!L->l[k]) break;
-    if (k == L->K1) continue;              /* every entry used: the iteration does nothing */
-    if (L->empty[k]) {
-      if (flips == 0) { rc = ORC_EPLACEHOLDER; break; }   /* unreachable for K < 2^N */
-      continue;                            /* the sector's reachable states are all used */
+    int k = 0;
+    while (k < S->count && S->l[k]) ++k;
+    if (k == S->K1) continue;              /* every kept state used: the iteration does nothing */
+    if (k == S->count) {
+      /* every kept state used with places still unfilled: the listing would pick a placeholder.
+       * For single and pair flips that cannot happen when K < 2^N (the kept states would be
+       * closed under single flips, i.e. all 2^N states); for exchanges it means the
+       * magnetisation sector holds no further state, and the search has ended. */
+      if (flips == 0) { rc = ORC_EPLACEHOLDER; break; }
+      continue;
     }
-    L->l[k] = 1;
+    S->l[k] = 1;
     ++prod;
-    memcpy(parent, L->psi + (size_t)k * W, (size_t)W * 8);
-    const double Ep = L->E[k];
+    memcpy(parent, S->psi + (size_t)k * W, (size_t)W * 8);
+    const double Ep = S->E[k];
     orc_fields(n, J, h, parent, f);
 
-    int64_t c = 0;
+    int64_t c = 0;   /* candidate index: singles i, then pairs (i, j) in lexicographic order */
     for (int order = 1; order <= 2; ++order) {
       for (int i = 0; i < n; ++i) {
         for (int j = (order == 1 ? -1 : i + 1); j < (order == 1 ? 0 : n); ++j, ++c) {
           if (!in_flip_set(flips, parent, i, j)) continue;
           const double e = Ep + cand_dE(n, J, f, parent, i, j);   /* E' */
-          if (!(e < L->E[L->K1 - 1])) continue;
+          if (!admissible(S, e)) continue;
           memcpy(x, parent, (size_t)W * 8);                        /* Alg. 1: XOR with 2^i (+2^j) */
           x[i >> 6] ^= (uint64_t)1 << (i & 63);
           if (j >= 0) x[j >> 6] ^= (uint64_t)1 << (j & 63);
-          int found;
-          int p = bsearch_state(L, x, &found);
-          if (found) continue;
-          update_list_sub(L, x, e, 0, p, ((uint64_t)it << 32) | (uint64_t)c, 0);
+          if (hs_contains(S, x)) continue;
+          offer(S, x, e, 0, ((uint64_t)it << 32) | (uint64_t)c, 0);
         }
       }
     }
   }
   if (n_productive) *n_productive = prod;
   free(f); free(parent); free(x);
-  if (rc) list_free(L);
+  if (rc) kept_free(S);
   return rc;
 }
 
@@ -316,19 +332,22 @@ static int check_args(int n, int K) {
   return ORC_OK;
 }
 
-static void export_list(const qlist* L, uint64_t* bits, double* E, uint8_t* used, uint64_t* stamp,
+/* The K+1 places in key order; places past the kept states are the listing's placeholders:
+ * bits 0, E = DBL_MAX (R_M), not used, stamp and src UINT64_MAX. */
+static void export_list(const kept_set* S, uint64_t* bits, double* E, uint8_t* used, uint64_t* stamp,
                         uint64_t* src, int* count) {
-  int cnt = 0;
-  for (int k = 0; k < L->K1; ++k) {
-    if (L->empty[k]) break;
-    ++cnt;
+  const int W = S->W, K1 = S->K1, c = S->count;
+  if (bits) {
+    memcpy(bits, S->psi, (size_t)c * W * 8);
+    memset(bits + (size_t)c * W, 0, (size_t)(K1 - c) * W * 8);
   }
-  if (bits) memcpy(bits, L->psi, (size_t)L->K1 * L->W * 8);
-  if (E) memcpy(E, L->E, (size_t)L->K1 * sizeof(double));
-  if (used) memcpy(used, L->l, (size_t)L->K1);
-  if (stamp) memcpy(stamp, L->stamp, (size_t)L->K1 * 8);
-  if (src) memcpy(src, L->src, (size_t)L->K1 * 8);
-  if (count) *count = cnt;
+  for (int k = 0; k < K1; ++k) {
+    if (E) E[k] = k < c ? S->E[k] : DBL_MAX;
+    if (used) used[k] = k < c ? S->l[k] : 0;
+    if (stamp) stamp[k] = k < c ? S->stamp[k] : UINT64_MAX;
+    if (src) src[k] = k < c ? S->src[k] : UINT64_MAX;
+  }
+  if (count) *count = c;
 }
 
 /* Alg. 3. Outputs hold K+1 slots in energy order; slots past *count are placeholders
@@ -339,11 +358,11 @@ int orc_qi_search_flips(int n, const double* J, const double* h, int K, int I, i
   int rc = check_args(n, K);
   if (rc) return rc;
   if (flips < 0 || flips > 2) return ORC_EINVAL;
-  qlist L;
-  rc = qi_search(J, h, n, K, I, flips, psi0, &L, productive_out);
+  kept_set S;
+  rc = qi_search(J, h, n, K, I, flips, psi0, &S, productive_out);
   if (rc) return rc;
-  export_list(&L, bits_out, E_out, used_out, stamp_out, NULL, count_out);
-  list_free(&L);
+  export_list(&S, bits_out, E_out, used_out, stamp_out, NULL, count_out);
+  kept_free(&S);
   return ORC_OK;
 }
 
@@ -355,13 +374,14 @@ int orc_qi_search(int n, const double* J, const double* h, int K, int I, const u
 }
 
 /* ---------------------------------------------------------------- Alg. 4 */
-/* QI multi search with the L initial states phi (L x W) given by the caller. Search 1's
- * list receives the lists of searches 2..L in turn: each entry, taken in energy order,
- * is binary-searched in psi' and, when absent, offered to update_list_sub with its own
- * energy and used flag. (The paper's listing pairs the spin-ordered psi'_{0,j} with the
- * energy-ordered E_{0,j}; the entries are read here as (psi_{0,j}, E_{0,j}, l_{0,j}).)
+/* QI multi search with the L initial states phi (L x W) given by the caller: L independent
+ * searches; the kept states of search 1 then receive those of searches 2..L in turn, each
+ * list read in key order, every state not already kept offered with its own energy, used
+ * flag and stamp under the rules of Alg. 2 above. (The paper's listing pairs the spin-ordered
+ * psi'_{0,j} with the energy-ordered E_{0,j}; the entries are read here as (psi_{0,j},
+ * E_{0,j}, l_{0,j}) of one state.)
  * src of a merged entry = (search index r << 32) | position in search r's final list.
- * Optional per-search outputs (L x (K+1) slots each) may be NULL. */
+ * Optional per-search outputs (L x (K+1) places each) may be NULL. */
 int orc_qi_multi_search_flips(int n, const double* J, const double* h, int K, int I, int flips, int Lc,
                               const uint64_t* phi, uint64_t* bits_out, double* E_out, uint8_t* used_out,
                               uint64_t* src_out, int* count_out,
@@ -371,32 +391,28 @@ int orc_qi_multi_search_flips(int n, const double* J, const double* h, int K, in
   if (rc) return rc;
   if (Lc < 1 || flips < 0 || flips > 2) return ORC_EINVAL;
   const int W = nwords(n), K1 = K + 1;
-  qlist M;
+  const int want_all = all_bits || all_E || all_used || all_stamp || all_count;
+  kept_set M;
   rc = qi_search(J, h, n, K, I, flips, phi, &M, NULL);
   if (rc) return rc;
-  for (int k = 0; k < K1; ++k)
-    if (!M.empty[k]) M.src[k] = (uint64_t)k;
-  if (all_bits || all_E || all_used || all_stamp || all_count)
-    export_list(&M, all_bits, all_E, all_used, all_stamp, NULL, all_count);
+  for (int k = 0; k < M.count; ++k) M.src[k] = (uint64_t)k;
+  if (want_all) export_list(&M, all_bits, all_E, all_used, all_stamp, NULL, all_count);
   for (int r = 1; r < Lc && !rc; ++r) {
-    qlist S;
+    kept_set S;
     rc = qi_search(J, h, n, K, I, flips, phi + (size_t)r * W, &S, NULL);
     if (rc) break;
-    if (all_bits || all_E || all_used || all_stamp || all_count)
+    if (want_all)
       export_list(&S, all_bits ? all_bits + (size_t)r * K1 * W : NULL, all_E ? all_E + (size_t)r * K1 : NULL,
                   all_used ? all_used + (size_t)r * K1 : NULL, all_stamp ? all_stamp + (size_t)r * K1 : NULL,
                   NULL, all_count ? all_count + r : NULL);
-    for (int j = 0; j < K1; ++j) {
-      if (S.empty[j]) break;
-      int found;
+    for (int j = 0; j < S.count; ++j) {
       const uint64_t* x = S.psi + (size_t)j * W;
-      int p = bsearch_state(&M, x, &found);
-      if (!found) update_list_sub(&M, x, S.E[j], S.l[j], p, S.stamp[j], ((uint64_t)r << 32) | (uint64_t)j);
+      if (!hs_contains(&M, x)) offer(&M, x, S.E[j], S.l[j], S.stamp[j], ((uint64_t)r << 32) | (uint64_t)j);
     }
-    list_free(&S);
+    kept_free(&S);
   }
   if (!rc) export_list(&M, bits_out, E_out, used_out, NULL, src_out, count_out);
-  list_free(&M);
+  kept_free(&M);
   return rc;
 }
 
