@@ -235,6 +235,8 @@ def run_ours(args, rank, world, device, oracle_lists=None):
         pairs = singles
     evald = ctx.evaluated_pairs() - evald0
     surv = ctx.survivor_count() - surv0
+    # expanded parents of the timed steps: n singles each (every flip set but exchanges)
+    parents = singles / n if flips != "exchange" else float(n_inst * R * I_ * args.steps)
     # per-kernel split: the same steps again, each launch between two events on the library
     # stream (graph replay off while profiling)
     prof_steps = max(1, min(args.steps, args.profile_steps))
@@ -334,7 +336,7 @@ def run_ours(args, rank, world, device, oracle_lists=None):
     return dict(ms=ms_max, pairs=pairs_all, evald=evald, prof=prof, launches=launches, tts=tts, forms=forms,
                 e2e=e2e, clocks=clocks, n=n, n_inst=n_inst, K=K, R=R, I=I_, prec=prec, flips=flips,
                 digits=digits, workload=args.workload, pair_scan=pair_scan, survivors=surv, sms=sms,
-                prof_ms_per_step=prof_ms, prof_steps=prof_steps, oracle_err=oracle_err)
+                prof_ms_per_step=prof_ms, prof_steps=prof_steps, oracle_err=oracle_err, parents=parents)
 
 
 def _timed_run(ctx, stream, iters):
@@ -601,10 +603,54 @@ def roofline(res, pk):
                     "(achieved_evaluated counts only the pairs of evaluated rows)"}
 
 
+def roofline_search(res, pk, src):
+    """The fused search kernel (one block per search through every iteration of a call) against
+    the measured HBM bandwidth, with its algorithmic bytes: per expanded parent the fields by
+    update (the generator's exact fields and two coupling rows read, the parent's written: 32
+    bytes a site), the row maxima of the pair scan (4 bytes a site), the kept states' words for
+    the near-duplicate test (8 bytes a word of each of the K+1 states); 4 bytes per pair tested
+    (4J~_ij); 32 bytes per survivor (entry, aq_i, aq_j, Jq_ij). The list order, keys, stamps,
+    used flags and {a_i, s_i} live in shared memory and cost no HBM traffic; the new states'
+    words are not counted."""
+    ms, nl = res["prof"].get("search", (0.0, 0))
+    if nl == 0 or ms <= 0:
+        return None
+    n, K1 = res["n"], res["K"] + 1
+    words = (n + 63) // 64
+    parents = res["parents"] / nl                 # expanded parents per launch
+    tested = res["evald"] / nl
+    surv = res.get("survivors", 0.0) / nl
+    per_parent = 32.0 * n + 4.0 * n + 8.0 * words * K1
+    bytes_per_launch = parents * per_parent + 4.0 * tested + 32.0 * surv
+    dur = ms / nl / 1e3
+    achieved = bytes_per_launch / dur / 1e9
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    # SURVEY 8(d)'s ALU speed of light of the candidate decision: 3 instructions per candidate
+    # on the FP32 lanes of every SM at the maximum clock; the output-sensitive scan decides the
+    # logical pairs without evaluating each one
+    clk = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = res["sms"] * 128 * clk * 1e6 / 3.0
+    logical = res["pairs"] / (res["ms"] / 1e3)
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(res.get("workload"), "k_search"),
+            "kernel": "k_search", "launch_us": round(dur * 1e6, 2), "bytes_per_launch": bytes_per_launch,
+            "parents_per_launch": parents, "tested_pairs_per_launch": tested, "survivors_per_launch": surv,
+            "per_unit": "per expanded parent 32 B/site (fields by update) + 4 B/site (row maxima) + 8 B per word "
+                        "of each of the K+1 kept states; 4 B per pair tested; 32 B per survivor",
+            "peak_source": src,
+            "logical_pairs_vs_dense_alu": {"achieved": logical, "peak": alu_peak,
+                                           "frac": round(logical / alu_peak, 4),
+                                           "what": "logical pair candidates decided per second of the whole step "
+                                                   "against SMs x 128 lanes x max clock / 3 instructions"},
+            "note": "one block per search through all iterations: chains of short dependent phases with a few "
+                    "kilobytes per search, neither a stream nor an ALU loop"}
+
+
 def dominant_roofline(res, pk, src):
-    """The roofline of the kernel class with the largest share of the step (per-search bound,
-    pair scan or merge), and the others beside it."""
-    cands = {"bound": roofline_bound(res, pk, src), "merge": roofline_merge(res, pk, src)}
+    """The roofline of the kernel class with the largest share of the step (fused search kernel,
+    per-search bound, pair scan or merge), and the others beside it."""
+    cands = {"bound": roofline_bound(res, pk, src), "merge": roofline_merge(res, pk, src),
+             "search": roofline_search(res, pk, src) if "parents" in res else None}
     if res["flips"] != "single":
         cands["scan"] = roofline(res, pk)
     cands = {k: v for k, v in cands.items() if v is not None}

@@ -239,10 +239,15 @@ int qis_candidate_count(qis_ctx* ctx, uint64_t* pairs, uint64_t* singles);
  *   pair_scan:     which form of the split modes' FP32 pair filter runs: 1 = output-sensitive
  *                  (one block per search: the live rows c_i >= RD(min_j a_j - rm_i), with
  *                  rm_i = max_j |4J~_ij|, and each live row's prefix of the columns sorted by
- *                  a_j; needs a padded size of at most 4096), 2 = dense register tiles (shaped
- *                  by scan_chunk_nc and scan_search_group), 0 = automatic (1 where allowed,
- *                  else 2; the environment variable QIS_DENSE_SCAN=1 makes 2 the default).
- *                  Both give the same survivor set. QIS_FP64 scans every pair in its plain
+ *                  a_j; needs a padded size of at most 4096), run inside the fused search
+ *                  kernel where it can (one block per search takes it through every iteration of
+ *                  a qis_iterate call: padded n <= 1024, K+1 <= 256, fields by update; the
+ *                  environment variable QIS_FUSED=0 turns the fused kernel off), else as its own
+ *                  kernel in every iteration; 3 = output-sensitive, always as its own kernel in
+ *                  every iteration (the per-kernel form); 2 = dense register tiles (shaped by
+ *                  scan_chunk_nc and scan_search_group); 0 = automatic (1 where allowed, else 2;
+ *                  the environment variable QIS_DENSE_SCAN=1 makes 2 the default).
+ *                  Every form gives the same kept lists. QIS_FP64 scans every pair in its plain
  *                  FP64 form whatever this says; qis_get_tuning reports 2 there. */
 typedef struct {
   int scan_chunk_nc;
@@ -255,7 +260,7 @@ typedef struct {
 int qis_get_tuning(qis_ctx* ctx, qis_tuning* out);
 
 /* Set the launch shapes for the current and later instances. QIS_ERR_INVALID_ARG for values
- * out of range, pair_scan 1 where the output-sensitive scan cannot run (QIS_FP64, padded size
+ * out of range, pair_scan 1 or 3 where the output-sensitive scan cannot run (QIS_FP64, padded size
  * above 4096) or a scan task list larger than the context holds (the setting is unchanged). */
 int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t);
 
@@ -299,7 +304,8 @@ int qis_get_stream(qis_ctx* ctx, void** stream);
  * bracketed by two events on the library stream. qis_profile_query synchronises, returns the
  * summed device time (ms) and launch count of one kernel class since the last query, and
  * resets that class. Classes: 0 parent pick, 1 local fields, 2 per-search bound,
- * 3 candidate scan, 4 exact merge. */
+ * 3 candidate scan, 4 exact merge, 5 fused search kernel (bound, scan and merge of every
+ * iteration of a qis_iterate call, and the pick and fields of all but its first). */
 int qis_profile_enable(qis_ctx* ctx, int on);
 int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches);
 

@@ -70,7 +70,9 @@ struct qis_ctx {
   // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
   bool profiling = false;
   bool use_graph = true;                    // QIS_NO_GRAPH=1 launches the kernels one by one
+  bool no_fused = false;                    // QIS_FUSED=0: the per-kernel form of every iteration
   cudaGraphExec_t graph_exec = nullptr;     // one iteration, captured for the current instances
+  int graph_n = 0;                          // fused form: the iteration count the graph was captured for
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
   size_t ev_used[8] = {0};
   std::string err = "no error";
@@ -202,6 +204,32 @@ cudaError_t prof_end(qis_ctx* ctx, int k) {
 // per-search shared-memory arrays), by default or when asked for; the dense tiles otherwise.
 static bool sparse_allowed(const qis_ctx* ctx) { return ctx->mode != QIS_FP64 && ctx->NP <= kSparseMaxNP; }
 static bool sparse_scan(const qis_ctx* ctx) { return sparse_allowed(ctx) && ctx->tune.pair_scan != 2; }
+// The fused search kernel: the output-sensitive scan (pair_scan 0 or 1) with fields by update,
+// a padded n and a list small enough for its shared-memory arrays (QIS_FUSED=0 turns it off).
+static bool fused_search(const qis_ctx* ctx) {
+  return sparse_scan(ctx) && ctx->tune.pair_scan != 3 && ctx->NP <= kSearchMaxNP && ctx->K1 <= kSearchMaxK1 &&
+         ctx->P.inc_on && !ctx->fields_simt && !ctx->no_fused;
+}
+
+// Every iteration of a qis_iterate call in one launch of the fused search kernel: the first
+// iteration's parent pick and fields run first as their own kernels (the tensor-core GEMM
+// computes the fields of every parent without a stored generator, e.g. every initial state),
+// then one block per search runs its n iterations.
+int launch_iterations_fused(qis_ctx* ctx, int n, cudaStream_t s) {
+  ctx->P.dense_ctl = 0;
+  const DevPtrs& P = ctx->P;
+  CK(prof_begin(ctx, 0));
+  LAUNCH(launch_pick(P, s));
+  CK(prof_end(ctx, 0));
+  CK(prof_begin(ctx, 1));
+  LAUNCH(launch_fields_inc(P, s));
+  LAUNCH(launch_fields_tc(P, ctx->D16, P.S16, ctx->max_inst, ctx->digits_used, P.gemm_nt, s));
+  CK(prof_end(ctx, 1));
+  CK(prof_begin(ctx, 5));
+  LAUNCH(launch_search(P, n, s));
+  CK(prof_end(ctx, 5));
+  return 0;
+}
 
 int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
   ctx->P.dense_ctl = !sparse_scan(ctx);   // the output-sensitive scan reads no control words
@@ -238,6 +266,7 @@ int launch_iteration(qis_ctx* ctx, cudaStream_t s) {
 void drop_graph(qis_ctx* ctx) {
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   ctx->graph_exec = nullptr;
+  ctx->graph_n = 0;
 }
 
 int build_work(qis_ctx* ctx) {
@@ -316,6 +345,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     if (ds && ds[0] == '1') ctx->tune.pair_scan = 2;   // the register-tile pair scan by default
     const char* g = getenv("QIS_NO_GRAPH");
     ctx->use_graph = !(g && g[0] == '1');
+    const char* fz = getenv("QIS_FUSED");
+    ctx->no_fused = fz && fz[0] == '0';
   }
   auto bail = [&](int rc) {
     g_create_error = ctx->err;
@@ -818,8 +849,35 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
   }
   cudaStream_t s = ctx->stream;
   const DevPtrs& P = ctx->P;
-  if (!ctx->profiling && ctx->use_graph) {
+  if (fused_search(ctx) && n_iters > 0) {
+    // the kernels of the whole call, captured once per iteration count and replayed
+    if (!ctx->profiling && ctx->use_graph) {
+      if (ctx->graph_exec && ctx->graph_n != n_iters) drop_graph(ctx);
+      if (!ctx->graph_exec) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = launch_iterations_fused(ctx, n_iters, s);
+        cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (rc) {
+          if (g) cudaGraphDestroy(g);
+          return rc;
+        }
+        CK(ec);
+        ec = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(ec);
+        ctx->graph_n = n_iters;
+        ctx->launches -= 4;   // counted at each replay below
+      }
+      CK(cudaGraphLaunch(ctx->graph_exec, s));
+      ctx->launches += 4;
+    } else {
+      const int rc = launch_iterations_fused(ctx, n_iters, s);
+      if (rc) return rc;
+    }
+  } else if (!ctx->profiling && ctx->use_graph) {
     // one iteration = five kernels, captured once into a CUDA graph and replayed
+    if (ctx->graph_exec && ctx->graph_n != 0) drop_graph(ctx);   // a graph of the fused form
     if (!ctx->graph_exec) {
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1417,8 +1475,8 @@ int qis_set_tuning(qis_ctx* ctx, const qis_tuning* t) {
   const int nt = t->gemm_tile_searches;
   if (nt != 0 && (nt % 16 != 0 || nt < 16 || nt > 256 || ctx->digits_used * nt > 512))
     return fail(ctx, QIS_ERR_INVALID_ARG, "gemm_tile_searches must be a multiple of 16 in [16, 256] with digits * it <= 512");
-  if (t->pair_scan < 0 || t->pair_scan > 2) return fail(ctx, QIS_ERR_INVALID_ARG, "pair_scan must be 0, 1 or 2");
-  if (t->pair_scan == 1 && !sparse_allowed(ctx))
+  if (t->pair_scan < 0 || t->pair_scan > 3) return fail(ctx, QIS_ERR_INVALID_ARG, "pair_scan must be 0, 1, 2 or 3");
+  if ((t->pair_scan == 1 || t->pair_scan == 3) && !sparse_allowed(ctx))
     return fail(ctx, QIS_ERR_INVALID_ARG, "the output-sensitive scan needs a split mode and a padded size <= 4096");
   CK(cudaSetDevice(ctx->cfg.device));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1538,7 +1596,7 @@ int qis_profile_enable(qis_ctx* ctx, int on) {
 
 int qis_profile_query(qis_ctx* ctx, int kernel_class, double* total_ms, uint64_t* launches) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
-  if (kernel_class < 0 || kernel_class >= 5) return fail(ctx, QIS_ERR_INVALID_ARG, "kernel class must be in [0, 5)");
+  if (kernel_class < 0 || kernel_class >= 6) return fail(ctx, QIS_ERR_INVALID_ARG, "kernel class must be in [0, 6)");
   CK(cudaStreamSynchronize(ctx->stream));
   double sum = 0.0;
   auto& v = ctx->ev[kernel_class];

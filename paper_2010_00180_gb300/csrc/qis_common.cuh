@@ -297,6 +297,12 @@ cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cu
 cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s);
 cudaError_t launch_scan_sparse(const DevPtrs& P, cudaStream_t s);
 constexpr int kSparseMaxNP = 4096;   // the sparse pair scan's largest padded n (shared-memory lists)
+// The fused search kernel (every iteration of a search in one block): its largest padded n and
+// list length (per-search arrays in shared memory).
+constexpr int kSearchMaxNP = 1024;
+constexpr int kSearchMaxK1 = 256;
+cudaError_t launch_search(const DevPtrs& P, int n_iters, cudaStream_t s);
+size_t search_smem(const DevPtrs& P);
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s);
 cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16, int max_inst, int digits_max,

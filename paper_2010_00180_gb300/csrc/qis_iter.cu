@@ -19,7 +19,7 @@
 // (at most `count` candidates duplicate a kept state). U is taken as the (K+1+count)-th
 // smallest energy among the single and pair flips of a few sites with the lowest a_i, a
 // subset of the candidates, so it never lies below the true order statistic.
-#include "qis_common.cuh"
+#include "qis_block.cuh"
 
 namespace qis {
 
@@ -192,70 +192,6 @@ cudaError_t launch_fields_fp64(const DevPtrs& P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- helpers
-// Block-wide minimum and maximum of one value per thread (every thread gets both).
-__device__ void block_min_max(float& lo, float& hi) {
-  __shared__ float s_lo[32], s_hi[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    s_lo[w] = lo;
-    s_hi[w] = hi;
-  }
-  __syncthreads();
-  lo = s_lo[0];
-  hi = s_hi[0];
-  for (int k = 1; k < nw; ++k) {
-    lo = fminf(lo, s_lo[k]);
-    hi = fmaxf(hi, s_hi[k]);
-  }
-  __syncthreads();
-}
-
-// An upper bound of the rank-th smallest (0-based) of cnt values in shared memory, tight to one
-// of 256 equal-width bins of the range of the finite ones: the largest value whose bin is at
-// most the bin holding that element (binning is monotone, so at least rank + 1 values lie in
-// those bins). +inf values (excluded candidates) go to the last bin, so the bound is +inf when
-// fewer than rank + 1 values are finite. Two passes over the values instead of the four of a
-// radix select. Every thread of the block calls it.
-// lo, hi: this thread's minimum and maximum of the finite values (the caller tracks them while
-// writing the values; the block-wide range is reduced here).
-__device__ float value_select_upper(const float* v, int cnt, int rank, int* hist, float lo, float hi) {
-  __shared__ int s_b;
-  for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
-  block_min_max(lo, hi);
-  const float scale = 255.99f / fmaxf(hi - lo, 1e-30f);
-  for (int t0 = 0; t0 < cnt; t0 += blockDim.x) {
-    const int t = t0 + threadIdx.x;
-    const bool in = t < cnt;
-    const unsigned act = __ballot_sync(0xffffffffu, in);
-    if (in) {
-      const float x = v[t];
-      const int bin = (x <= hi) ? min(255, (int)((x - lo) * scale)) : 255;   // +inf (excluded): last bin
-      const unsigned peers = __match_any_sync(act, bin);
-      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], __popc(peers));
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int b, within;
-    find_bin(hist, rank, b, within);
-    if (threadIdx.x == 0) s_b = b;
-  }
-  __syncthreads();
-  const int bsel = s_b;
-  float mx = -INFINITY, dummy = INFINITY;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    const float x = v[t];
-    if (((x <= hi) ? min(255, (int)((x - lo) * scale)) : 255) <= bsel) mx = fmaxf(mx, x);
-  }
-  block_min_max(dummy, mx);
-  return mx;
-}
-
 // ---------------------------------------------------------------- fields by update (split modes)
 // A kept state x entered the list at iteration tg (its stamp) as a flip of site i, or of sites
 // i and j, of that iteration's parent g, whose exact fields are in the aq ring. With s_g the
@@ -332,40 +268,7 @@ cudaError_t launch_fields_inc(const DevPtrs& P, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Candidate index of the kept state x if it is one or two flips from the parent p (the single
-// flip of its differing site, or the pair of its two), else -1. One pass over the W words: the
-// parent's from shared memory, the state's loaded in batches of ten (one round trip for
-// n <= 640).
-__device__ __forceinline__ long long near_code_sp(const uint64_t* x, const uint64_t* p, int W, int n) {
-  int dist = 0, p0 = 0, p1 = 0;
-  for (int w0 = 0; w0 < W; w0 += 10) {
-    uint64_t xw[10];
-#pragma unroll
-    for (int u = 0; u < 10; ++u) xw[u] = (w0 + u < W) ? x[w0 + u] : 0ull;
-#pragma unroll
-    for (int u = 0; u < 10; ++u) {
-      uint64_t v = (w0 + u < W) ? (xw[u] ^ p[w0 + u]) : 0ull;
-      if (v && dist < 2) {
-        const int lo = (w0 + u) * 64 + __ffsll((long long)v) - 1;
-        if (dist == 0) {
-          p0 = lo;
-          const uint64_t r = v & (v - 1);
-          if (r) p1 = (w0 + u) * 64 + __ffsll((long long)r) - 1;
-        } else {
-          p1 = lo;
-        }
-      }
-      dist += __popcll(v);
-    }
-  }
-  if (dist == 1) return p0;
-  if (dist == 2) return pair_index(n, p0, p1);
-  return -1;
-}
-
 // ---------------------------------------------------------------- per-search bound
-constexpr int kSubSites = 64;   // at most this many low-a sites in the subset (2080 candidates)
-constexpr int kSubMax = kSubSites * (kSubSites + 1) / 2;
 
 __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   const int b = blockIdx.x;

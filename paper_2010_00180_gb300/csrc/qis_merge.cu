@@ -16,178 +16,9 @@
 //  3. New list = first K+1 of (old list, new candidates) by (E, stamp): old entries precede
 //     new ones of equal energy (they arrived earlier), new ones are ordered by candidate
 //     index c (the order of the Alg. 3 loop). Slots of evicted entries are reused.
-#include "qis_common.cuh"
+#include "qis_block.cuh"
 
 namespace qis {
-
-constexpr uint32_t kNoCand = 0xffffffffu;   // empty slot of the duplicate table
-__device__ inline uint32_t chash(uint32_t c) { return (c * 2654435761u) >> 7; }
-
-
-
-// exclusive prefix sum of one int per thread over the block (blockDim multiple of 32)
-__device__ int block_exclusive_sum(int v, int* wsum /* [33] */, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int w = (lane < nw) ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < nw) wsum[lane] = w;   // inclusive warp totals
-  }
-  __syncthreads();
-  const int before = (warp > 0 ? wsum[warp - 1] : 0) + x - v;
-  *total = wsum[nw - 1];
-  __syncthreads();
-  return before;
-}
-
-// (key, c) order of candidates: energy key, ties by candidate index c (the Alg. 3 loop order).
-__device__ __forceinline__ bool kc_less(unsigned long long ka, unsigned long long ea, unsigned long long kb,
-                                        unsigned long long eb) {
-  return ka < kb || (ka == kb && (uint32_t)ea < (uint32_t)eb);
-}
-
-// Ascending bitonic sort of n2 (power of two) (key, entry) pairs in shared memory, any size.
-__device__ void bitonic_sort_smem(unsigned long long* key, unsigned long long* ent, int n2) {
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
-        const int u = t ^ j;
-        if (u > t) {
-          const unsigned long long a = key[t], c = key[u], va = ent[t], vc = ent[u];
-          const bool up = (t & k) == 0;
-          if (kc_less(c, vc, a, va) == up) {
-            key[t] = c; key[u] = a;
-            ent[t] = vc; ent[u] = va;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Ascending bitonic sort of the 32 (key, entry) pairs of one warp, one per lane, in shuffles.
-__device__ __forceinline__ void warp_sort32(unsigned long long& key, unsigned long long& ent) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key, j);
-      const unsigned long long eo = __shfl_xor_sync(0xffffffffu, ent, j);
-      const bool want_min = ((lane & j) == 0) == ((lane & k) == 0);
-      const bool take = want_min ? kc_less(ko, eo, key, ent) : kc_less(key, ent, ko, eo);
-      if (take) {
-        key = ko;
-        ent = eo;
-      }
-    }
-  }
-}
-
-// Sort of nv <= blockDim.x pairs: every warp sorts a run of 32 (padding ~0 sorts last), then
-// each element's place = its index in its run + the number of smaller elements in every other
-// run (binary search, 32 entries). Input in (key, ent)[0..nv), output in (okey, oent)[0..nv).
-// Every thread of the block calls it.
-__device__ void sort_runs(const unsigned long long* key, const unsigned long long* ent, int nv,
-                          unsigned long long* okey, unsigned long long* oent) {
-  const int t = threadIdx.x, w = t >> 5;
-  const int nr = (nv + 31) >> 5;
-  unsigned long long k = ~0ull, e = ~0ull;
-  if (t < nv) {
-    k = key[t];
-    e = ent[t];
-  }
-  if (w < nr) warp_sort32(k, e);   // warp-uniform
-  okey[t] = k;                     // runs staged in the output arrays (blockDim.x entries)
-  oent[t] = e;
-  __syncthreads();
-  int pos = t & 31;
-  const bool real = w < nr && k != ~0ull;   // a finite energy's key is never all ones
-  if (real) {
-    for (int v = 0; v < nr; ++v) {
-      if (v == w) continue;
-      const unsigned long long* rk = okey + 32 * v;
-      const unsigned long long* re = oent + 32 * v;
-      int lo = 0, hi = 32;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (kc_less(rk[mid], re[mid], k, e)) lo = mid + 1; else hi = mid;
-      }
-      pos += lo;
-    }
-  }
-  __syncthreads();   // every search done before the runs are overwritten
-  if (real) {
-    okey[pos] = k;
-    oent[pos] = e;
-  }
-  __syncthreads();
-}
-
-// Ascending bitonic sort of 32 single keys of one warp, one per lane, in shuffles.
-__device__ __forceinline__ void warp_sort32_key(unsigned long long& key) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key, j);
-      const bool want_min = ((lane & j) == 0) == ((lane & k) == 0);
-      key = want_min ? min(key, ko) : max(key, ko);
-    }
-  }
-}
-
-// sort_runs for packed keys ((key - kmin) << cb | c: one 64-bit value carries the (key, c)
-// order when the keys span less than 2^(64 - cb)); the packing is done on load. Output in
-// okey[0..nv). Every thread of the block calls it; nv <= blockDim.x.
-__device__ void sort_runs_packed(const unsigned long long* key, const unsigned long long* ent, int nv,
-                                 unsigned long long kmin, int cb, unsigned long long* okey) {
-  const int t = threadIdx.x, w = t >> 5;
-  const int nr = (nv + 31) >> 5;
-  unsigned long long k = ~0ull;
-  if (t < nv) k = ((key[t] - kmin) << cb) | (uint32_t)ent[t];
-  if (w < nr) warp_sort32_key(k);   // warp-uniform
-  okey[t] = k;
-  __syncthreads();
-  int pos = t & 31;
-  const bool real = w < nr && k != ~0ull;   // a packed key is never all ones (c < 2^cb - 1)
-  if (real) {
-    for (int v = 0; v < nr; ++v) {
-      if (v == w) continue;
-      const unsigned long long* rk = okey + 32 * v;
-      int lo = 0, hi = 32;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (rk[mid] < k) lo = mid + 1; else hi = mid;
-      }
-      pos += lo;
-    }
-  }
-  __syncthreads();
-  if (real) okey[pos] = k;
-  __syncthreads();
-}
-
-__device__ inline uint64_t flip_mask(int x, int i, int j) {
-  uint64_t m = 0;
-  if ((i >> 6) == x) m ^= 1ull << (i & 63);
-  if (j >= 0 && (j >> 6) == x) m ^= 1ull << (j & 63);
-  return m;
-}
 
 constexpr int kMergeThreads = 256;
 // kept candidates held in shared memory: min(next_pow2(max(cap, 256)), P.merge_cand), where

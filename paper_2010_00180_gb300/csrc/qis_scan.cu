@@ -27,7 +27,7 @@
 // couplings: the FMA propagates NaN and min ignores it. When a row's minimum passes, the lane
 // marks which of its columns pass from the same values, and appends one survivor entry per
 // passing pair.
-#include "qis_common.cuh"
+#include "qis_block.cuh"
 
 namespace qis {
 
@@ -338,13 +338,6 @@ cudaError_t launch_scan_pairs(const DevPtrs& P, const int4* tasks, int n_tasks, 
 // live rows times their lists (several hundred pairs a search for n = 600, K = 120, against
 // n(n-1)/2 = 179700), a chain of short dependent steps: the loads it cannot avoid are grouped
 // so that each step waits once.
-constexpr int kSparseNB = 128;   // buckets of a_j
-
-__device__ __forceinline__ int sparse_bucket(float x, float lo, float inv) {
-  const float f = __fmul_rn(__fsub_rn(x, lo), inv);   // monotone in x; NaN for inf * 0
-  return f < (float)kSparseNB ? max(0, (int)f) : kSparseNB - 1;
-}
-
 template <bool EX>
 __global__ void __launch_bounds__(128, 16) k_scan_sparse(DevPtrs P) {
   constexpr int SB = 5;   // sites staged per thread and pass (n = 600: one pass)

@@ -1,0 +1,856 @@
+// qis_search.cu -- every iteration of one search in one thread block (the fused, persistent
+// form of the iteration of Alg. 3 in the split precision modes).
+//
+// The R searches of an instance, and the instances, share nothing until the Alg. 4 merge, so
+// one block can take one search through all the iterations of a qis_iterate call without ever
+// waiting for another block. Per iteration t the block runs, back to back:
+//   pick    the first unused kept state in key order becomes the parent (Alg. 3)
+//   fields  its exact integer fields from its generating parent's, held in the aq ring, minus
+//           the flipped sites' coupling columns (the Sec. III energy algebra; a parent whose
+//           generator is no longer in the ring gets them from a full row sum instead);
+//           a_i = -2 s_i f_i
+//   bound   filter threshold (the last kept energy and an order-statistic bound), the kept
+//           states one or two flips from the parent (the only possible duplicates), singles
+//   scan    pair flips dE_ij = a_i + a_j + 4 s_i s_j J_ij decided by the output-sensitive scan
+//   merge   exact integer keys of the survivors, duplicates dropped, first K+1 of the old
+//           list and the new states by (E, stamp)
+// The kept list's order, keys, stamps and used flags, the parent's spins and {a_i, s_i} stay in
+// shared memory across the iterations; the kept states' bits, the aq ring and the survivor
+// buffer are in global memory (written and read by this block only, within the L2 cache).
+// The first iteration's parent is picked, and its fields computed (update, or the tensor-core
+// GEMM for a parent without a stored generator), by the kernels launched before this one.
+// The arithmetic of every phase is that of the per-kernel form (k_bound, k_scan_sparse,
+// k_merge), so the kept lists are identical bit for bit.
+#include "qis_block.cuh"
+
+namespace qis {
+
+constexpr int kSNT = 128;   // threads of a search block
+
+__host__ __device__ inline int search_pcs(int cap, int merge_cand) {
+  const int pc = next_pow2(cap > 256 ? cap : 256);
+  return pc < merge_cand ? pc : merge_cand;
+}
+
+// Byte offsets of the dynamic shared memory of a search block.
+struct SearchLayout {
+  int as, pb, okey0, okey1, ostamp, oslot0, oslot1, dupc, oused, scratch, total;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SearchLayout search_layout(int NP, int Wmax, int K1, int cap, int merge_cand) {
+  SearchLayout L;
+  int o = 0;
+  auto take = [&](int bytes) {
+    o = align_up(o, 16);
+    const int r = o;
+    o += bytes;
+    return r;
+  };
+  L.as = take(NP * 8);
+  L.pb = take(Wmax * 8);
+  L.okey0 = take(K1 * 8);
+  L.okey1 = take(K1 * 8);
+  L.ostamp = take(K1 * 8);
+  L.oslot0 = take(K1 * 4);
+  L.oslot1 = take(K1 * 4);
+  L.dupc = take(K1 * 4);
+  L.oused = take(K1);
+  // scratch: the phases' working arrays, one phase at a time
+  const int bound = kSubMax * 4 + 2 * 256 * 4 + kSubSites * 4;
+  const int scan = 3 * NP * 4 + (2 * kSparseNB + 1) * 4;
+  const int merge = search_pcs(cap, merge_cand) * 16 + 2 * 256 * 8 + next_pow2(2 * K1) * 4 + 256 * 4;
+  int sc = bound > scan ? bound : scan;
+  sc = sc > merge ? sc : merge;
+  L.scratch = take(sc);
+  L.total = align_up(o, 16);
+  return L;
+}
+
+// Packed keys (key - kmin) << cb | c of nv <= 2 * blockDim.x candidates in ascending order:
+// runs of 32 sorted by warps (warp w takes runs w, w + warps, ...), then each key's place = its
+// index in its run + the count of smaller keys in every other run. tmp holds the runs
+// (ceil(nv / 32) * 32 entries), out receives the nv sorted keys.
+static __device__ void sort_packed_runs(const unsigned long long* key, const unsigned long long* ent, int nv,
+                                        unsigned long long kmin, int cb, unsigned long long* tmp,
+                                        unsigned long long* out) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nr = (nv + 31) >> 5;
+  for (int run = threadIdx.x >> 5; run < nr; run += nw) {
+    const int e = run * 32 + lane;
+    unsigned long long k = ~0ull;
+    if (e < nv) k = ((key[e] - kmin) << cb) | (uint32_t)ent[e];
+    warp_sort32_key(k);
+    tmp[e] = k;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
+    const unsigned long long k = tmp[e];
+    if (k == ~0ull) continue;   // padding (a packed key is never all ones)
+    const int run = e >> 5;
+    int pos = e & 31;
+    for (int v = 0; v < nr; ++v) {
+      if (v == run) continue;
+      const unsigned long long* rk = tmp + 32 * v;
+      int lo = 0, hi = 32;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (rk[mid] < k) lo = mid + 1; else hi = mid;
+      }
+      pos += lo;
+    }
+    out[pos] = k;
+  }
+  __syncthreads();
+}
+
+// FL: flip set (QIS_FLIPS_*). One block of kSNT threads per search; n_iters >= 1.
+template <int FL>
+__global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
+  constexpr bool EX = FL == QIS_FLIPS_EXCHANGE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int K1 = P.K1, Wm = P.Wmax, NP = P.NP, cap = P.cap;
+  const long long base = (long long)b * K1;
+  const SearchLayout L = search_layout(NP, Wm, K1, cap, P.merge_cand);
+  float2* as = reinterpret_cast<float2*>(smem + L.as);
+  uint64_t* pb = reinterpret_cast<uint64_t*>(smem + L.pb);
+  unsigned long long* okeyA = reinterpret_cast<unsigned long long*>(smem + L.okey0);
+  unsigned long long* okeyB = reinterpret_cast<unsigned long long*>(smem + L.okey1);
+  uint64_t* ostamp = reinterpret_cast<uint64_t*>(smem + L.ostamp);
+  int* oslotA = reinterpret_cast<int*>(smem + L.oslot0);
+  int* oslotB = reinterpret_cast<int*>(smem + L.oslot1);
+  uint32_t* dupc = reinterpret_cast<uint32_t*>(smem + L.dupc);
+  uint8_t* oused = reinterpret_cast<uint8_t*>(smem + L.oused);
+  unsigned char* scr = smem + L.scratch;
+
+  __shared__ int s_sel, s_near, s_ns, s_nsites, s_n2, s_bin, s_bin2, s_nl, s_nv, s_ocut;
+  __shared__ float s_thr, wf[8];
+  __shared__ int s_w[33];
+  __shared__ unsigned long long s_kmin, s_kmax;
+
+  const int act0 = P.active[b];
+  const InstDesc d = P.inst[b / P.R];
+  const int n = d.n, W = d.W;
+  const int t_first = P.iter_t[b];
+  const int ring_t0 = P.ring_t0[b];
+  int cnt = P.lst_count[b];
+  long long Epq = P.par_q[b];
+  uint64_t ph = P.par_hash[b];
+  for (int r = tid; r < K1; r += kSNT) {
+    okeyA[r] = P.lst_key[base + r];
+    oslotA[r] = P.lst_ord[base + r];
+    ostamp[r] = P.lst_stamp[base + r];
+    oused[r] = P.lst_used[base + r];
+  }
+  for (int w = tid; w < W; w += kSNT) pb[w] = P.par_bits[(long long)b * Wm + w];
+  float mn = INFINITY, mx = -INFINITY;   // this thread's range of a_i (for the bound)
+  if (act0)
+    for (int i = tid; i < n; i += kSNT) {
+      const float2 v = P.as32[(long long)b * NP + i];
+      as[i] = v;
+      mn = fminf(mn, v.x);
+      mx = fmaxf(mx, v.x);
+    }
+  __syncthreads();
+
+  int act = act0, t = t_first, cur = 0;
+  int nprod = 0;
+  unsigned long long npair = 0, nev = 0, nsurv = 0;
+  const float scale_q = (float)d.inv_scale;
+  const long long* Jq = P.Jq + d.off_mat;
+  const float* J4 = P.J4 + d.off_mat;
+  unsigned long long* surv = P.surv + (long long)b * cap;
+
+  for (int iter = 0; iter < n_iters; ++iter) {
+    unsigned long long* okey = cur ? okeyB : okeyA;
+    unsigned long long* okeyN = cur ? okeyA : okeyB;
+    int* oslot = cur ? oslotB : oslotA;
+    int* oslotN = cur ? oslotA : oslotB;
+    if (iter > 0) {
+      t += 1;
+      if (!act) continue;
+      // ------------------------------------------------------------ pick (Alg. 3)
+      if (warp == 0) {
+        int sel = -1;
+        for (int r0 = 0; r0 < cnt && sel < 0; r0 += 32) {
+          const int r = r0 + lane;
+          const bool un = r < cnt && !oused[oslot[r]];
+          const unsigned m = __ballot_sync(0xffffffffu, un);
+          if (m) sel = r0 + __ffs(m) - 1;
+        }
+        if (lane == 0) s_sel = sel;
+      }
+      __syncthreads();
+      const int sel = s_sel;
+      if (sel < 0) {   // every kept state used: the search ends (block-uniform)
+        act = 0;
+        continue;
+      }
+      const int pslot = oslot[sel];
+      Epq = (long long)(okey[sel] ^ (1ull << 63));
+      const uint64_t pst = ostamp[pslot];
+      ph = P.lst_hash[base + pslot];
+      for (int w = tid; w < W; w += kSNT) pb[w] = P.lst_bits[(base + pslot) * Wm + w];
+      __syncthreads();   // the parent's words; every thread has read s_sel and the used flags
+      if (tid == 0) {
+        oused[pslot] = 1;
+        P.lst_used[base + pslot] = 1;
+      }
+      ++nprod;
+      if (FL == QIS_FLIPS_SINGLE_PAIR) npair += (unsigned long long)n * (n - 1) / 2;
+      if (EX) {
+        int down = 0;
+        for (int w = 0; w < W; ++w) down += __popcll(pb[w]);
+        npair += (unsigned long long)down * (unsigned long long)(n - down);
+      }
+      // ------------------------------------------------------------ fields
+      // x = the parent, entered at iteration tg as candidate c of that iteration's parent g
+      const int tg = (int)(pst >> 32);
+      long long* __restrict__ ax = aq_of(P, b, t);
+      if (tg >= 1 && tg > ring_t0 && tg < t && t - tg < P.ring_n) {
+        int i, j;
+        decode_candidate(n, (uint32_t)pst, i, j);
+        const long long gi = sigma_of(pb, i) ? 2 : -2;   // 2 s_g at the flipped sites (s_g = -s_x)
+        const long long gj = (j >= 0) ? (sigma_of(pb, j) ? 2 : -2) : 0;
+        const long long* __restrict__ ag = aq_of(P, b, tg);
+        const long long* __restrict__ Ji = Jq + (long long)i * d.n_pad;   // row i = column i
+        const long long* __restrict__ Jj = Jq + (long long)max(j, 0) * d.n_pad;
+        constexpr int U = 4;   // sites per thread and pass, their loads issued together
+        for (int k0 = 0; k0 < n; k0 += U * kSNT) {
+          long long vg[U], vi[U], vj[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * kSNT + tid;
+            vg[u] = vi[u] = vj[u] = 0;
+            if (k < n) {
+              vg[u] = ag[k];
+              vi[u] = Ji[k];
+              if (j >= 0) vj[u] = Jj[k];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * kSNT + tid;
+            if (k >= n) break;
+            const int sx = sigma_of(pb, k);
+            const int sg = sx ^ (k == i || k == j);
+            const long long fg = sg ? vg[u] / 2 : -(vg[u] / 2);   // aq = -2 s f, s = -1 where sigma = 1
+            const long long fx = fg - gi * vi[u] - gj * vj[u];
+            const long long aq = sx ? 2 * fx : -2 * fx;
+            const float a = __ll2float_rn(aq) * scale_q;
+            ax[k] = aq;
+            as[k] = make_float2(a, sx ? -1.f : 1.f);
+            mn = fminf(mn, a);
+            mx = fmaxf(mx, a);
+          }
+        }
+      } else {
+        // no stored generator: fq_k = hq_k + sum_j s_j Jq_jk from scratch (columns coalesced)
+        for (int k = tid; k < n; k += kSNT) {
+          long long acc = P.hq[d.off_vec + k];
+          for (int jj = 0; jj < n; ++jj) {
+            const long long v = Jq[(long long)jj * d.n_pad + k];
+            acc += sigma_of(pb, jj) ? -v : v;
+          }
+          const int sx = sigma_of(pb, k);
+          const long long aq = sx ? 2 * acc : -2 * acc;
+          const float a = __ll2float_rn(aq) * scale_q;
+          ax[k] = aq;
+          as[k] = make_float2(a, sx ? -1.f : 1.f);
+          mn = fminf(mn, a);
+          mx = fmaxf(mx, a);
+        }
+      }
+    } else if (!act) {
+      continue;
+    }
+    // ---------------------------------------------------------------- bound
+    // range of a over the block; the kept states one or two flips from the parent (their
+    // candidate indices: the only candidates that can be duplicates, each equal to exactly one)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      wf[warp] = mn;
+      wf[4 + warp] = mx;
+    }
+    if (tid == 0) {
+      s_near = 0;
+      s_ns = 0;
+      s_nsites = 0;
+      s_n2 = 0;
+      s_nl = 0;
+    }
+    __syncthreads();   // the fields and the range are complete
+    const float amin = fminf(fminf(wf[0], wf[1]), fminf(wf[2], wf[3]));
+    const float amax = fmaxf(fmaxf(wf[4], wf[5]), fmaxf(wf[6], wf[7]));
+    mn = INFINITY;
+    mx = -INFINITY;
+    for (int r = tid; r < cnt; r += kSNT) {
+      const long long c = near_code_sp(P.lst_bits + (base + r) * Wm, pb, W, n);
+      if (c >= 0) dupc[atomicAdd(&s_near, 1)] = (uint32_t)c;
+    }
+    __syncthreads();
+    const int ndup = s_near;
+    const int k = K1 + ndup;
+    float Uf = INFINITY;
+    int nu = 0;
+    if (EX)
+      for (int w = 0; w < W; ++w) nu += __popcll(pb[w]);
+    const long long Ccand = FL == QIS_FLIPS_SINGLE ? (long long)n : EX ? (long long)nu * (n - nu) : (long long)n * (n + 1) / 2;
+    if (Ccand > k && k <= kSubMax) {
+      float* subv = reinterpret_cast<float*>(scr);                    // [kSubMax]
+      int* hist = reinterpret_cast<int*>(scr + kSubMax * 4);          // [256]
+      int* hist2 = hist + 256;                                         // [256]
+      int* sites = hist2 + 256;                                        // [kSubSites]
+      const int want = min(3 * k, kSubMax);
+      int t0 = 0, t1 = 0;
+      if (FL == QIS_FLIPS_SINGLE) {
+        t0 = k;
+      } else if (EX) {
+        const int nd = n - nu;
+        int m0 = max(1, (int)sqrtf((float)want));
+        while (m0 * m0 < want) ++m0;
+        while (m0 > 1 && (m0 - 1) * (m0 - 1) >= want) --m0;
+        int mu = min(nu, m0);
+        int md = min(nd, (want + mu - 1) / mu);
+        mu = min(nu, (want + md - 1) / md);
+        if (mu + md > kSubSites) {
+          if (mu <= kSubSites / 2) md = kSubSites - mu;
+          else if (md <= kSubSites / 2) mu = kSubSites - md;
+          else mu = md = kSubSites / 2;
+        }
+        t0 = mu;
+        t1 = md;
+      } else {
+        int m = max(1, (int)((sqrtf(8.f * (float)want + 1.f) - 1.f) * 0.5f));
+        while (m * (m + 1) / 2 < want) ++m;
+        while (m > 1 && (m - 1) * m / 2 >= want) --m;
+        t0 = min(min(m, n), kSubSites);
+      }
+      const int lim0 = EX ? kSubSites - t1 : kSubSites;
+      const float scale = 255.99f / fmaxf(amax - amin, 1e-30f);
+      auto bin_of = [&](int i) { return min(255, (int)((as[i].x - amin) * scale)); };
+      for (int x = tid; x < 256; x += kSNT) {
+        hist[x] = 0;
+        hist2[x] = 0;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += kSNT) atomicAdd(&((EX && sigma_of(pb, i)) ? hist2 : hist)[bin_of(i)], 1);
+      __syncthreads();
+      if (warp == 0) {
+        int bin, within;
+        find_bin(hist, t0 - 1, bin, within);
+        if (lane == 0) s_bin = bin;
+        if (EX) {
+          find_bin(hist2, t1 - 1, bin, within);
+          if (lane == 0) s_bin2 = bin;
+        }
+      }
+      __syncthreads();
+      float vlo = INFINITY, vhi = -INFINITY;
+      for (int i = tid; i < n; i += kSNT) {
+        const int c = EX ? sigma_of(pb, i) : 0;
+        if (bin_of(i) > (c ? s_bin2 : s_bin)) continue;
+        const int slot = atomicAdd(c ? &s_n2 : &s_nsites, 1);
+        if (FL == QIS_FLIPS_SINGLE) {
+          if (slot < kSubMax) {
+            const float de = as[i].x;
+            vlo = fminf(vlo, de);
+            vhi = fmaxf(vhi, de);
+            subv[slot] = de;
+          }
+        } else if (slot < (c ? t1 : lim0)) {
+          sites[c ? lim0 + slot : slot] = i;
+        }
+      }
+      __syncthreads();
+      const int mm = min(s_nsites, lim0), m2 = min(s_n2, t1);
+      const int M = FL == QIS_FLIPS_SINGLE ? min(s_nsites, kSubMax) : EX ? mm * m2 : mm + mm * (mm - 1) / 2;
+      auto member = [&](int q, int& i, int& j) {
+        j = -1;
+        if (EX) {
+          i = sites[q / m2];
+          j = sites[lim0 + q % m2];
+        } else if (q < mm) {
+          i = sites[q];
+        } else {
+          const int r = q - mm;
+          const float qq = 2.f * mm - 1.f;
+          int x = (int)((qq - sqrtf(fmaxf(qq * qq - 8.f * (float)r, 0.f))) * 0.5f);
+          x = max(0, min(x, mm - 2));
+          while (x > 0 && x * mm - x * (x + 1) / 2 > r) --x;
+          while (x < mm - 2 && (x + 1) * mm - (x + 1) * (x + 2) / 2 <= r) ++x;
+          const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
+          i = sites[x];
+          j = sites[y];
+        }
+        if (j >= 0 && i > j) {
+          const int tmp = i;
+          i = j;
+          j = tmp;
+        }
+      };
+      if (M >= k && FL != QIS_FLIPS_SINGLE) {
+        for (int q0 = 0; q0 < M; q0 += 4 * kSNT) {
+          int mi[4], mj[4];
+          float j4v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * kSNT + tid;
+            mi[u] = 0;
+            mj[u] = -1;
+            j4v[u] = 0.f;
+            if (q < M) {
+              member(q, mi[u], mj[u]);
+              if (mj[u] >= 0) j4v[u] = J4[(long long)mi[u] * d.n_pad + mj[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * kSNT + tid;
+            if (q >= M) break;
+            const int i = mi[u], j = mj[u];
+            float de = as[i].x;
+            if (j >= 0) {
+              const float2 vj = as[j];
+              de = as[i].x + fmaf((sigma_of(pb, i) ? -j4v[u] : j4v[u]), vj.y, vj.x);
+            }
+            vlo = fminf(vlo, de);
+            vhi = fmaxf(vhi, de);
+            subv[q] = de;
+          }
+        }
+      }
+      if (M >= k) {
+        __syncthreads();
+        Uf = value_select_upper(subv, M, k - 1, hist, vlo, vhi);
+      }
+    }
+    if (tid == 0) {
+      // |dE~ - dE| <= delta: a and 4J are fl32 of exact values; the scan adds one FMA rounding
+      // and one subtraction rounding (factor 8 margin). Everything in FP32 rounded up; T - Ep
+      // from the exact integer keys, scaled by the power of two 2^-q.
+      const unsigned long long kT = okey[K1 - 1];
+      const float tE = (cnt != K1) ? INFINITY
+                                   : __fmul_ru(__ll2float_ru((long long)(kT ^ (1ull << 63)) - Epq), scale_q);
+      const float tt = fminf(tE, Uf);
+      const float big = __fadd_ru(__fadd_ru(__fmul_ru(3.f, fmaxf(fabsf(amin), fabsf(amax))), d.j4max),
+                                  isinf(tt) ? 0.f : fabsf(tt));
+      const float delta = __fmul_ru(big, 0x1p-21f);
+      s_thr = fminf(__fadd_ru(tE, delta), __fadd_ru(Uf, 2.f * delta));
+    }
+    __syncthreads();
+    const float thr = s_thr;
+    // single flips: dE_i = a_i (not candidates under exchanges)
+    if (!EX) {
+      for (int i = tid; i < n; i += kSNT) {
+        if (as[i].x <= thr) {
+          const int slot = atomicAdd(&s_ns, 1);
+          if (slot < cap) surv[slot] = surv_entry(i, -1);
+        }
+      }
+    }
+    // ---------------------------------------------------------------- scan (pairs)
+    if (FL != QIS_FLIPS_SINGLE) {
+      int* li = reinterpret_cast<int*>(scr);   // [NP] live rows
+      int* pc = li + NP;                       // [NP] their rm, then list offsets
+      int* cj = pc + NP;                       // [NP] columns in bucket order
+      int* bs = cj + NP;                       // [kSparseNB + 1]
+      int* bcur = bs + kSparseNB + 1;          // [kSparseNB]
+      const float* rm = P.rm4 + d.off_vec;
+      __syncthreads();   // the bound's scratch is free
+      for (int x = tid; x < kSparseNB; x += kSNT) bcur[x] = 0;
+      float bl = -INFINITY;
+      constexpr int SB = 5;
+      for (int i0 = 0; i0 < n; i0 += SB * kSNT) {
+        float r[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+          const int i = i0 + tid + u * kSNT;
+          r[u] = (i < n) ? rm[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+          const int i = i0 + tid + u * kSNT;
+          if (i < n) {
+            const float c = __fsub_rn(thr, as[i].x);
+            if (c >= __fsub_rd(amin, r[u])) {
+              const int q = atomicAdd(&s_nl, 1);
+              li[q] = i;
+              pc[q] = __float_as_int(r[u]);
+              bl = fmaxf(bl, __fadd_ru(nextafterf(c, INFINITY), r[u]));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bl = fmaxf(bl, __shfl_xor_sync(0xffffffffu, bl, o));
+      if (lane == 0) wf[warp] = bl;
+      __syncthreads();
+      const int nl = s_nl;
+      if (nl > 0) {   // block-uniform
+        const float B = fmaxf(fmaxf(wf[0], wf[1]), fmaxf(wf[2], wf[3]));
+        const float span = __fsub_ru(B, amin);
+        const float inv = (span > 0.f && span < INFINITY) ? __fdiv_rn((float)kSparseNB, span) : 0.f;
+        for (int j = tid; j < n; j += kSNT)
+          if (as[j].x < B) atomicAdd(&bcur[sparse_bucket(as[j].x, amin, inv)], 1);
+        __syncthreads();
+        if (warp == 0) {
+          int x[kSparseNB / 32], s = 0;
+#pragma unroll
+          for (int q = 0; q < kSparseNB / 32; ++q) {
+            x[q] = bcur[lane * (kSparseNB / 32) + q];
+            s += x[q];
+          }
+          int inc = s;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          int acc = inc - s;
+#pragma unroll
+          for (int q = 0; q < kSparseNB / 32; ++q) {
+            bs[lane * (kSparseNB / 32) + q] = acc;
+            bcur[lane * (kSparseNB / 32) + q] = acc;
+            acc += x[q];
+          }
+          if (lane == 31) bs[kSparseNB] = acc;
+        }
+        __syncthreads();
+        // site code in place of s_j: (position in the column order << 1) | sigma_j, or INT_MIN |
+        // sigma_j for a site at or above B
+        for (int j = tid; j < n; j += kSNT) {
+          const float2 v = as[j];
+          const int sg = v.y < 0.f;
+          int code = INT_MIN | sg;
+          if (v.x < B) {
+            const int q = atomicAdd(&bcur[sparse_bucket(v.x, amin, inv)], 1);
+            cj[q] = j;
+            code = (q << 1) | sg;
+          }
+          as[j].y = __int_as_float(code);
+        }
+        for (int q = tid; q < nl; q += kSNT) {
+          const int i = li[q];
+          const float c = __fsub_rn(thr, as[i].x), rr = __int_as_float(pc[q]);
+          pc[q] = bs[sparse_bucket(__fadd_ru(nextafterf(c, INFINITY), rr), amin, inv) + 1];
+        }
+        __syncthreads();
+        {
+          const int per = (nl + kSNT - 1) / kSNT, q0 = min(nl, tid * per), q1 = min(nl, q0 + per);
+          int sum = 0;
+          for (int q = q0; q < q1; ++q) {
+            const int code = __float_as_int(as[li[q]].y);
+            const int x = code < 0 ? 0 : max(0, pc[q] - (code >> 1) - 1);
+            pc[q] = x;
+            sum += x;
+          }
+          int inc = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+          }
+          if (lane == 31) s_w[warp] = inc;
+          __syncthreads();
+          int acc = inc - sum;
+          for (int w = 0; w < warp; ++w) acc += s_w[w];
+          for (int q = q0; q < q1; ++q) {
+            const int x = pc[q];
+            pc[q] = acc;
+            acc += x;
+          }
+        }
+        __syncthreads();
+        const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3];
+        constexpr int PB = 4;
+        for (int u0 = 0; u0 < tot; u0 += PB * kSNT) {
+          float cv[PB], av[PB], pv[PB], jv[PB];
+          int ij[PB];
+          bool ok[PB];
+#pragma unroll
+          for (int u = 0; u < PB; ++u) {
+            const int e = u0 + u * kSNT + tid;
+            ok[u] = false;
+            if (e < tot) {
+              int lo = 0, hi = nl;
+              while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pc[mid] <= e) lo = mid; else hi = mid;
+              }
+              const int i = li[lo];
+              const float2 vi = as[i];
+              const int ci = __float_as_int(vi.y);
+              const int j = cj[(ci >> 1) + 1 + e - pc[lo]];
+              const float2 vj = as[j];
+              ij[u] = min(i, j) | (max(i, j) << 16);
+              cv[u] = __fsub_rn(thr, vi.x);
+              av[u] = vj.x;
+              pv[u] = ((ci ^ __float_as_int(vj.y)) & 1) ? -1.f : 1.f;
+              ok[u] = !EX || pv[u] < 0.f;
+              if (ok[u]) jv[u] = J4[(long long)i * d.n_pad + j];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < PB; ++u) {
+            bool hit = false;
+            if (ok[u]) {
+              ++nev;
+              hit = fmaf(pv[u], jv[u], av[u]) <= cv[u];
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+              const int leader = __ffs(m) - 1;
+              int sb = 0;
+              if (lane == leader) sb = atomicAdd(&s_ns, __popc(m));
+              sb = __shfl_sync(0xffffffffu, sb, leader);
+              const int slot = sb + __popc(m & ((1u << lane) - 1u));
+              if (hit && slot < cap) surv[slot] = surv_entry(ij[u] & 0xffff, ij[u] >> 16);
+            }
+          }
+        }
+      }
+    }
+    // ---------------------------------------------------------------- merge (Alg. 2)
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(scr);
+    const int PCs = search_pcs(cap, P.merge_cand);
+    unsigned long long* se = sk + PCs;
+    unsigned long long* so = se + PCs;              // [256] sorted packed keys
+    unsigned long long* st = so + 256;              // [256] sorted runs
+    const int HT = next_pow2(2 * K1);
+    uint32_t* htab = reinterpret_cast<uint32_t*>(st + 256);   // [HT]
+    int* rhist = reinterpret_cast<int*>(htab + HT);            // [256]
+    __syncthreads();   // every survivor written; the scan's scratch is free
+    const int S = s_ns;
+    if (S > cap) {   // block-uniform: the buffer held only the first cap survivors
+      if (tid == 0) atomicOr(P.status, kStatCapacity);
+      act = 0;
+      continue;
+    }
+    nsurv += (unsigned long long)S;
+    const bool big = S > PCs;
+    if (big) {
+      const long long stride = next_pow2(max(cap, 256));
+      sk = P.mrg_scratch + (long long)b * 2 * stride;
+      se = sk + stride;
+    }
+    for (int x = tid; x < HT; x += kSNT) htab[x] = kNoCand;
+    if (tid == 0) {
+      s_nv = 0;
+      s_ocut = cnt;
+      s_kmin = ~0ull;
+      s_kmax = 0;
+    }
+    __syncthreads();
+    for (int r = tid; r < ndup; r += kSNT) {
+      const uint32_t c = dupc[r];
+      uint32_t pos = chash(c) & (HT - 1);
+      while (atomicCAS(&htab[pos], kNoCand, c) != kNoCand) pos = (pos + 1) & (HT - 1);
+    }
+    __syncthreads();
+    const long long Tq = (cnt == K1) ? (long long)(okey[K1 - 1] ^ (1ull << 63)) : LLONG_MAX;
+    const long long* aqb = aq_of(P, b, t);
+    unsigned long long kmn = ~0ull, kmx = 0;
+    for (int u0 = 0; u0 < S; u0 += kSNT) {
+      const int e = u0 + tid;
+      bool keep = false;
+      unsigned long long kk = 0, ent = 0;
+      if (e < S) {
+        ent = surv[e];
+        int i, j;
+        surv_sites(ent, i, j);
+        ent |= (j < 0) ? (uint32_t)i : pair_index(n, i, j);
+        long long de = aqb[i];
+        if (j >= 0) {
+          const long long jq = Jq[(long long)i * d.n_pad + j];
+          de += aqb[j] + ((sigma_of(pb, i) ^ sigma_of(pb, j)) ? -4 * jq : 4 * jq);
+        }
+        const long long eq = Epq + de;
+        kk = qkey(eq);
+        keep = eq < Tq;   // Alg. 2: strict <
+        if (keep) {
+          const uint32_t c = (uint32_t)ent;
+          for (uint32_t pos = chash(c) & (HT - 1); htab[pos] != kNoCand; pos = (pos + 1) & (HT - 1))
+            if (htab[pos] == c) {
+              keep = false;   // a kept state (the binary search of Alg. 2)
+              break;
+            }
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (bal) {
+        int wb = 0;
+        if (lane == 0) wb = atomicAdd(&s_nv, __popc(bal));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (keep) {
+          const int slot = wb + __popc(bal & ((1u << lane) - 1));
+          sk[slot] = kk;
+          se[slot] = ent;
+          kmn = min(kmn, kk);
+          kmx = max(kmx, kk);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kmn = min(kmn, __shfl_xor_sync(0xffffffffu, kmn, o));
+      kmx = max(kmx, __shfl_xor_sync(0xffffffffu, kmx, o));
+    }
+    if (lane == 0 && kmn <= kmx) {
+      atomicMin(&s_kmin, kmn);
+      atomicMax(&s_kmax, kmx);
+    }
+    __syncthreads();
+    int nv = s_nv;
+    // more kept candidates than the sort takes at once: only the K+1 lowest can enter the list
+    if (nv > 256 && nv > K1) {
+      const unsigned long long x = radix_select<unsigned long long>(sk, nv, K1 - 1, rhist);
+      int kept = 0;
+      for (int u0 = 0; u0 < nv; u0 += kSNT) {
+        const int e = u0 + tid;
+        unsigned long long kk = 0, ee = 0;
+        bool keep = false;
+        if (e < nv) {
+          kk = sk[e];
+          ee = se[e];
+          keep = kk <= x;
+        }
+        int total;
+        const int pos = kept + block_exclusive_sum(keep ? 1 : 0, s_w, &total);
+        if (keep) {
+          sk[pos] = kk;
+          se[pos] = ee;
+        }
+        kept += total;
+        __syncthreads();
+      }
+      nv = kept;
+    }
+    const unsigned long long kmin = s_kmin;
+    const uint32_t n_cand = (uint32_t)n + (uint32_t)((long long)n * (n - 1) / 2);
+    const int cb = 32 - __clz((int)n_cand);
+    const bool packed = nv > 1 && nv <= 256 && ((s_kmax - kmin) >> (64 - cb)) == 0;
+    const unsigned long long* nk = sk;   // new keys in ascending (E, c) order
+    if (packed) {
+      sort_packed_runs(sk, se, nv, kmin, cb, st, so);
+      nk = so;
+    } else if (nv > 1) {
+      const int m2 = next_pow2(nv);
+      for (int x = nv + tid; x < m2; x += kSNT) {
+        sk[x] = ~0ull;
+        se[x] = ~0ull;
+      }
+      __syncthreads();
+      bitonic_sort_smem(sk, se, m2);
+    }
+    __syncthreads();
+    const unsigned long long cmask = (1ull << cb) - 1;
+    auto new_key = [&](int p) { return packed ? (nk[p] >> cb) + kmin : nk[p]; };
+    for (int o = tid; o < cnt; o += kSNT) {
+      const unsigned long long ko = okey[o];
+      int lo = 0, hi = nv;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (new_key(mid) < ko) lo = mid + 1; else hi = mid;
+      }
+      const int rank = o + lo;
+      if (rank < K1) {
+        oslotN[rank] = oslot[o];
+        okeyN[rank] = ko;
+      } else {
+        atomicMin(&s_ocut, o);
+      }
+    }
+    __syncthreads();
+    const int ocut = s_ocut, n_ev = cnt - ocut;
+    for (int p = tid; p < nv; p += kSNT) {
+      const unsigned long long kp = new_key(p);
+      int lo = 0, hi = cnt;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (okey[mid] <= kp) lo = mid + 1; else hi = mid;
+      }
+      const int rank = p + lo;
+      if (rank >= K1) continue;
+      const int slot = (p < n_ev) ? oslot[ocut + p] : cnt + (p - n_ev);
+      uint32_t c;
+      int i, j;
+      if (packed) {
+        c = (uint32_t)(nk[p] & cmask);
+        decode_candidate(n, c, i, j);
+      } else {
+        surv_decode(se[p], c, i, j);
+      }
+      uint64_t* dst = P.lst_bits + (base + slot) * Wm;
+      for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
+      const uint64_t stamp = ((uint64_t)t << 32) | c;
+      P.lst_q[base + slot] = (long long)(kp ^ (1ull << 63));
+      P.lst_stamp[base + slot] = stamp;
+      ostamp[slot] = stamp;
+      P.lst_hash[base + slot] = ph ^ P.zob[i] ^ ((j >= 0) ? P.zob[j] : 0ull);
+      P.lst_used[base + slot] = 0;
+      oused[slot] = 0;
+      oslotN[rank] = slot;
+      okeyN[rank] = kp;
+    }
+    cnt = min(K1, cnt + nv);
+    cur ^= 1;
+    __syncthreads();   // the new order is complete before the next pick reads it
+  }
+  // ------------------------------------------------------------------ write back
+  const unsigned long long* okey = cur ? okeyB : okeyA;
+  const int* oslot = cur ? oslotB : oslotA;
+  for (int r = tid; r < cnt; r += kSNT) {
+    P.lst_key[base + r] = okey[r];
+    P.lst_ord[base + r] = oslot[r];
+  }
+  if (act0) {   // the last parent (what the per-kernel form leaves in these fields)
+    for (int w = tid; w < W; w += kSNT) P.par_bits[(long long)b * Wm + w] = pb[w];
+  }
+  if (tid == 0) {
+    P.lst_count[b] = cnt;
+    P.iter_t[b] = t_first + n_iters - 1;
+    if (act0) {
+      P.active[b] = act;
+      P.par_q[b] = Epq;
+      P.par_hash[b] = ph;
+      P.nprod[b] += nprod;
+      P.npair[b] += npair;
+      if (nsurv) atomicAdd(P.surv_tot + (b & 63), nsurv);
+    }
+  }
+  if (act0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    if (lane == 0 && nev) atomicAdd(P.eval_cnt + (b & 63), nev);
+  }
+}
+
+size_t search_smem(const DevPtrs& P) { return (size_t)search_layout(P.NP, P.Wmax, P.K1, P.cap, P.merge_cand).total; }
+
+cudaError_t launch_search(const DevPtrs& P, int n_iters, cudaStream_t s) {
+  if (n_iters <= 0 || P.B == 0) return cudaSuccess;
+  const size_t sm = search_smem(P);
+  static size_t attr[3] = {0, 0, 0};
+  const int fl = P.flips;
+  if (attr[fl] < sm) {
+    cudaError_t e = fl == QIS_FLIPS_SINGLE ? cudaFuncSetAttribute(k_search<QIS_FLIPS_SINGLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                  : fl == QIS_FLIPS_EXCHANGE ? cudaFuncSetAttribute(k_search<QIS_FLIPS_EXCHANGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                             : cudaFuncSetAttribute(k_search<QIS_FLIPS_SINGLE_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr[fl] = sm;
+  }
+  if (fl == QIS_FLIPS_SINGLE) k_search<QIS_FLIPS_SINGLE><<<P.B, kSNT, sm, s>>>(P, n_iters);
+  else if (fl == QIS_FLIPS_EXCHANGE) k_search<QIS_FLIPS_EXCHANGE><<<P.B, kSNT, sm, s>>>(P, n_iters);
+  else k_search<QIS_FLIPS_SINGLE_PAIR><<<P.B, kSNT, sm, s>>>(P, n_iters);
+  return cudaGetLastError();
+}
+
+}  // namespace qis

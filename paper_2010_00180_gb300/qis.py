@@ -32,7 +32,7 @@ SYMBOLS = ["qis_create", "qis_destroy", "qis_last_error", "qis_create_instance",
            "qis_mlp_create", "qis_mlp_destroy", "qis_mlp_last_error", "qis_mlp_num_params", "qis_mlp_get_params",
            "qis_mlp_set_params", "qis_mlp_features", "qis_mlp_add_example", "qis_mlp_clear_examples",
            "qis_mlp_forward", "qis_mlp_loss_grad", "qis_mlp_train", "qis_init_states_learned"]
-KERNEL_CLASSES = ["pick", "fields", "bound", "scan", "merge"]
+KERNEL_CLASSES = ["pick", "fields", "bound", "scan", "merge", "search"]
 
 
 class QISError(RuntimeError):
@@ -286,7 +286,8 @@ class Context:
 
     def set_tuning(self, scan_chunk_nc: int = 8, scan_search_group: int = 0, gemm_tile_searches: int = 0,
                    pair_scan: int = 0):
-        """pair_scan: 1 output-sensitive, 2 dense register tiles, 0 automatic."""
+        """pair_scan: 1 output-sensitive (in the fused search kernel where it can run), 3 output-sensitive
+        as its own kernel in every iteration, 2 dense register tiles, 0 automatic."""
         t = Tuning(scan_chunk_nc, scan_search_group, gemm_tile_searches, pair_scan)
         self._check(self.lib.qis_set_tuning(self.h, C.byref(t)))
 

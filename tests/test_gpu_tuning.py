@@ -79,7 +79,7 @@ def test_autotune_resets_and_keeps_results():
 def test_invalid_tuning_is_rejected():
     ctx = make("gaussian", "split_bf16", [80], R=8)
     before = ctx.tuning()
-    for bad in [(0, 0, 0), (9, 0, 0), (8, 9, 0), (8, -1, 0), (8, 0, 24), (8, 0, 512), (8, 0, 0, 3), (8, 0, 0, -1)]:
+    for bad in [(0, 0, 0), (9, 0, 0), (8, 9, 0), (8, -1, 0), (8, 0, 24), (8, 0, 512), (8, 0, 0, 4), (8, 0, 0, -1)]:
         with pytest.raises(qis.QISError) as e:
             ctx.set_tuning(*bad)
         assert e.value.name == "INVALID_ARG"
