@@ -34,8 +34,10 @@ __host__ __device__ inline int search_pcs(int cap, int merge_cand) {
 
 // Byte offsets of the dynamic shared memory of a search block.
 struct SearchLayout {
-  int as, pb, okey0, okey1, ostamp, oslot0, oslot1, dupc, oused, scratch, total;
+  int as, pb, okey0, okey1, ostamp, oslot0, oslot1, htab, ssv, oused, scratch, total;
 };
+
+constexpr int kSSV = 512;   // survivors held in shared memory (more go to the global buffer)
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -55,12 +57,13 @@ __host__ __device__ inline SearchLayout search_layout(int NP, int Wmax, int K1, 
   L.ostamp = take(K1 * 8);
   L.oslot0 = take(K1 * 4);
   L.oslot1 = take(K1 * 4);
-  L.dupc = take(K1 * 4);
+  L.htab = take(next_pow2(2 * K1) * 4);
+  L.ssv = take(kSSV * 8);
   L.oused = take(K1);
   // scratch: the phases' working arrays, one phase at a time
-  const int bound = kSubMax * 4 + 2 * 256 * 4 + kSubSites * 4;
+  const int bound = 4 * 256 * 4 + kSubSites * 4;
   const int scan = 3 * NP * 4 + (2 * kSparseNB + 1) * 4;
-  const int merge = search_pcs(cap, merge_cand) * 16 + 2 * 256 * 8 + next_pow2(2 * K1) * 4 + 256 * 4;
+  const int merge = search_pcs(cap, merge_cand) * 16 + 2 * 256 * 8 + 256 * 4;
   int sc = bound > scan ? bound : scan;
   sc = sc > merge ? sc : merge;
   L.scratch = take(sc);
@@ -105,6 +108,76 @@ static __device__ void sort_packed_runs(const unsigned long long* key, const uns
   __syncthreads();
 }
 
+// Orderable unsigned key of a float (ascending floats -> ascending keys) and its inverse.
+__device__ __forceinline__ unsigned fkey(float x) {
+  const unsigned u = __float_as_uint(x + 0.f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Fields of a parent without a stored generator, from scratch: fq_k = hq_k + sum_j s_j Jq_jk
+// (columns coalesced), aq_k = -2 s_k fq_k. Rarely taken (out of line: the hot loop stays small).
+static __device__ __noinline__ void fields_full(const DevPtrs& P, const InstDesc& d, const uint64_t* pb,
+                                                long long* ax, float2* as, float& mn, float& mx) {
+  const long long* Jq = P.Jq + d.off_mat;
+  const float scale_q = (float)d.inv_scale;
+  for (int k = threadIdx.x; k < d.n; k += blockDim.x) {
+    long long acc = P.hq[d.off_vec + k];
+    for (int jj = 0; jj < d.n; ++jj) {
+      const long long v = Jq[(long long)jj * d.n_pad + k];
+      acc += sigma_of(pb, jj) ? -v : v;
+    }
+    const int sx = sigma_of(pb, k);
+    const long long aq = sx ? 2 * acc : -2 * acc;
+    const float a = __ll2float_rn(aq) * scale_q;
+    ax[k] = aq;
+    as[k] = make_float2(a, sx ? -1.f : 1.f);
+    mn = fminf(mn, a);
+    mx = fmaxf(mx, a);
+  }
+}
+
+// More kept candidates than the packed sort takes at once (rare): keep the K+1 lowest keys
+// (ties included), compacted in place; returns their number. Out of line.
+static __device__ __noinline__ int keep_lowest(unsigned long long* sk, unsigned long long* se, int nv, int K1,
+                                               int* rhist, int* wsum) {
+  const unsigned long long x = radix_select<unsigned long long>(sk, nv, K1 - 1, rhist);
+  int kept = 0;
+  for (int u0 = 0; u0 < nv; u0 += blockDim.x) {
+    const int e = u0 + threadIdx.x;
+    unsigned long long kk = 0, ee = 0;
+    bool keep = false;
+    if (e < nv) {
+      kk = sk[e];
+      ee = se[e];
+      keep = kk <= x;
+    }
+    int total;
+    const int pos = kept + block_exclusive_sum(keep ? 1 : 0, wsum, &total);
+    if (keep) {
+      sk[pos] = kk;
+      se[pos] = ee;
+    }
+    kept += total;
+    __syncthreads();
+  }
+  return kept;
+}
+
+// (key, entry) sort of nv candidates in place, any size (rare: keys spanning more than the
+// packed form holds). Out of line.
+static __device__ __noinline__ void sort_pairs_any(unsigned long long* sk, unsigned long long* se, int nv) {
+  const int m2 = next_pow2(nv);
+  for (int x = nv + threadIdx.x; x < m2; x += blockDim.x) {
+    sk[x] = ~0ull;
+    se[x] = ~0ull;
+  }
+  __syncthreads();
+  bitonic_sort_smem(sk, se, m2);
+}
+
 // FL: flip set (QIS_FLIPS_*). One block of kSNT threads per search; n_iters >= 1.
 template <int FL>
 __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
@@ -122,12 +195,14 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
   uint64_t* ostamp = reinterpret_cast<uint64_t*>(smem + L.ostamp);
   int* oslotA = reinterpret_cast<int*>(smem + L.oslot0);
   int* oslotB = reinterpret_cast<int*>(smem + L.oslot1);
-  uint32_t* dupc = reinterpret_cast<uint32_t*>(smem + L.dupc);
+  uint32_t* htab = reinterpret_cast<uint32_t*>(smem + L.htab);
+  unsigned long long* ssv = reinterpret_cast<unsigned long long*>(smem + L.ssv);
+  const int HT = next_pow2(2 * K1);
   uint8_t* oused = reinterpret_cast<uint8_t*>(smem + L.oused);
   unsigned char* scr = smem + L.scratch;
 
   __shared__ int s_sel, s_near, s_ns, s_nsites, s_n2, s_bin, s_bin2, s_nl, s_nv, s_ocut;
-  __shared__ float s_thr, wf[8];
+  __shared__ float wf[8];
   __shared__ int s_w[33];
   __shared__ unsigned long long s_kmin, s_kmax;
 
@@ -163,6 +238,11 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
   const long long* Jq = P.Jq + d.off_mat;
   const float* J4 = P.J4 + d.off_mat;
   unsigned long long* surv = P.surv + (long long)b * cap;
+  // survivor slot s: shared memory below kSSV, the search's global buffer above (up to cap)
+  auto put_surv = [&](int slot, unsigned long long e) {
+    if (slot < kSSV) ssv[slot] = e;
+    else if (slot < cap) surv[slot] = e;
+  };
 
   for (int iter = 0; iter < n_iters; ++iter) {
     unsigned long long* okey = cur ? okeyB : okeyA;
@@ -248,21 +328,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
           }
         }
       } else {
-        // no stored generator: fq_k = hq_k + sum_j s_j Jq_jk from scratch (columns coalesced)
-        for (int k = tid; k < n; k += kSNT) {
-          long long acc = P.hq[d.off_vec + k];
-          for (int jj = 0; jj < n; ++jj) {
-            const long long v = Jq[(long long)jj * d.n_pad + k];
-            acc += sigma_of(pb, jj) ? -v : v;
-          }
-          const int sx = sigma_of(pb, k);
-          const long long aq = sx ? 2 * acc : -2 * acc;
-          const float a = __ll2float_rn(aq) * scale_q;
-          ax[k] = aq;
-          as[k] = make_float2(a, sx ? -1.f : 1.f);
-          mn = fminf(mn, a);
-          mx = fmaxf(mx, a);
-        }
+        fields_full(P, d, pb, ax, as, mn, mx);   // no stored generator
       }
     } else if (!act) {
       continue;
@@ -285,6 +351,15 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       s_nsites = 0;
       s_n2 = 0;
       s_nl = 0;
+      s_nv = 0;
+      s_ocut = cnt;
+      s_kmin = ~0ull;
+      s_kmax = 0;
+    }
+    for (int x = tid; x < HT; x += kSNT) htab[x] = kNoCand;
+    {
+      int* hist = reinterpret_cast<int*>(scr);   // the bound's histograms, cleared for this iteration
+      for (int x = tid; x < 4 * 256; x += kSNT) hist[x] = 0;
     }
     __syncthreads();   // the fields and the range are complete
     const float amin = fminf(fminf(wf[0], wf[1]), fminf(wf[2], wf[3]));
@@ -293,7 +368,11 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
     mx = -INFINITY;
     for (int r = tid; r < cnt; r += kSNT) {
       const long long c = near_code_sp(P.lst_bits + (base + r) * Wm, pb, W, n);
-      if (c >= 0) dupc[atomicAdd(&s_near, 1)] = (uint32_t)c;
+      if (c >= 0) {
+        atomicAdd(&s_near, 1);
+        uint32_t pos = chash((uint32_t)c) & (HT - 1);
+        while (atomicCAS(&htab[pos], kNoCand, (uint32_t)c) != kNoCand) pos = (pos + 1) & (HT - 1);
+      }
     }
     __syncthreads();
     const int ndup = s_near;
@@ -304,10 +383,13 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       for (int w = 0; w < W; ++w) nu += __popcll(pb[w]);
     const long long Ccand = FL == QIS_FLIPS_SINGLE ? (long long)n : EX ? (long long)nu * (n - nu) : (long long)n * (n + 1) / 2;
     if (Ccand > k && k <= kSubMax) {
-      float* subv = reinterpret_cast<float*>(scr);                    // [kSubMax]
-      int* hist = reinterpret_cast<int*>(scr + kSubMax * 4);          // [256]
+      // the bound's histograms (cleared before the fields barrier): site bins, the second spin
+      // class's site bins (exchanges), the subset values' counts and their per-bin maxima
+      int* hist = reinterpret_cast<int*>(scr);                        // [256]
       int* hist2 = hist + 256;                                         // [256]
-      int* sites = hist2 + 256;                                        // [kSubSites]
+      int* vhist = hist2 + 256;                                        // [256]
+      unsigned* vmax = reinterpret_cast<unsigned*>(vhist + 256);       // [256]
+      int* sites = reinterpret_cast<int*>(vmax + 256);                 // [kSubSites]
       const int want = min(3 * k, kSubMax);
       int t0 = 0, t1 = 0;
       if (FL == QIS_FLIPS_SINGLE) {
@@ -336,11 +418,6 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       const int lim0 = EX ? kSubSites - t1 : kSubSites;
       const float scale = 255.99f / fmaxf(amax - amin, 1e-30f);
       auto bin_of = [&](int i) { return min(255, (int)((as[i].x - amin) * scale)); };
-      for (int x = tid; x < 256; x += kSNT) {
-        hist[x] = 0;
-        hist2[x] = 0;
-      }
-      __syncthreads();
       for (int i = tid; i < n; i += kSNT) atomicAdd(&((EX && sigma_of(pb, i)) ? hist2 : hist)[bin_of(i)], 1);
       __syncthreads();
       if (warp == 0) {
@@ -353,18 +430,26 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
         }
       }
       __syncthreads();
-      float vlo = INFINITY, vhi = -INFINITY;
+      // the subset's values are binned as they are formed, over a range that holds them: every
+      // selected site has a below the upper edge of its class's cut bin (one bin of margin for
+      // the rounding of the binning), a pair lies within 4 max|J~| of a_i + a_j (values outside
+      // clamp to the end bins, which keeps the binning monotone)
+      const float cut0 = __fadd_ru(amin, __fdiv_ru((float)(s_bin + 2), scale));
+      const float cut1 = EX ? __fadd_ru(amin, __fdiv_ru((float)(s_bin2 + 2), scale)) : cut0;
+      const float hi_v = FL == QIS_FLIPS_SINGLE ? cut0 : __fadd_ru(__fadd_ru(cut0, cut1), d.j4max);
+      const float lo_b = FL == QIS_FLIPS_SINGLE ? amin : __fsub_rd(__fadd_rd(amin, amin), d.j4max);
+      const float scale_v = 255.99f / fmaxf(hi_v - lo_b, 1e-30f);
+      auto put_value = [&](float v) {
+        const int bin = min(255, max(0, (int)((v - lo_b) * scale_v)));
+        atomicAdd(&vhist[bin], 1);
+        atomicMax(&vmax[bin], fkey(v));
+      };
       for (int i = tid; i < n; i += kSNT) {
         const int c = EX ? sigma_of(pb, i) : 0;
         if (bin_of(i) > (c ? s_bin2 : s_bin)) continue;
         const int slot = atomicAdd(c ? &s_n2 : &s_nsites, 1);
         if (FL == QIS_FLIPS_SINGLE) {
-          if (slot < kSubMax) {
-            const float de = as[i].x;
-            vlo = fminf(vlo, de);
-            vhi = fmaxf(vhi, de);
-            subv[slot] = de;
-          }
+          if (slot < kSubMax) put_value(as[i].x);
         } else if (slot < (c ? t1 : lim0)) {
           sites[c ? lim0 + slot : slot] = i;
         }
@@ -421,21 +506,29 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
               const float2 vj = as[j];
               de = as[i].x + fmaf((sigma_of(pb, i) ? -j4v[u] : j4v[u]), vj.y, vj.x);
             }
-            vlo = fminf(vlo, de);
-            vhi = fmaxf(vhi, de);
-            subv[q] = de;
+            put_value(de);
           }
         }
       }
       if (M >= k) {
+        // U = the largest subset value in the bins up to the one holding the k-th smallest
+        // (binning is monotone, so at least k subset values are <= U): every warp alike
         __syncthreads();
-        Uf = value_select_upper(subv, M, k - 1, hist, vlo, vhi);
+        int bsel, within;
+        find_bin(vhist, k - 1, bsel, within);
+        unsigned mk = 0u;
+        for (int x = lane; x <= bsel; x += 32) mk = max(mk, vmax[x]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+        Uf = fkey_inv(mk);
       }
     }
-    if (tid == 0) {
+    float thr;
+    {
       // |dE~ - dE| <= delta: a and 4J are fl32 of exact values; the scan adds one FMA rounding
       // and one subtraction rounding (factor 8 margin). Everything in FP32 rounded up; T - Ep
-      // from the exact integer keys, scaled by the power of two 2^-q.
+      // from the exact integer keys, scaled by the power of two 2^-q. (Every thread forms the
+      // same value from the same operands.)
       const unsigned long long kT = okey[K1 - 1];
       const float tE = (cnt != K1) ? INFINITY
                                    : __fmul_ru(__ll2float_ru((long long)(kT ^ (1ull << 63)) - Epq), scale_q);
@@ -443,16 +536,14 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       const float big = __fadd_ru(__fadd_ru(__fmul_ru(3.f, fmaxf(fabsf(amin), fabsf(amax))), d.j4max),
                                   isinf(tt) ? 0.f : fabsf(tt));
       const float delta = __fmul_ru(big, 0x1p-21f);
-      s_thr = fminf(__fadd_ru(tE, delta), __fadd_ru(Uf, 2.f * delta));
+      thr = fminf(__fadd_ru(tE, delta), __fadd_ru(Uf, 2.f * delta));
     }
-    __syncthreads();
-    const float thr = s_thr;
     // single flips: dE_i = a_i (not candidates under exchanges)
     if (!EX) {
       for (int i = tid; i < n; i += kSNT) {
         if (as[i].x <= thr) {
           const int slot = atomicAdd(&s_ns, 1);
-          if (slot < cap) surv[slot] = surv_entry(i, -1);
+          put_surv(slot, surv_entry(i, -1));
         }
       }
     }
@@ -612,7 +703,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
               if (lane == leader) sb = atomicAdd(&s_ns, __popc(m));
               sb = __shfl_sync(0xffffffffu, sb, leader);
               const int slot = sb + __popc(m & ((1u << lane) - 1u));
-              if (hit && slot < cap) surv[slot] = surv_entry(ij[u] & 0xffff, ij[u] >> 16);
+              if (hit) put_surv(slot, surv_entry(ij[u] & 0xffff, ij[u] >> 16));
             }
           }
         }
@@ -624,9 +715,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
     unsigned long long* se = sk + PCs;
     unsigned long long* so = se + PCs;              // [256] sorted packed keys
     unsigned long long* st = so + 256;              // [256] sorted runs
-    const int HT = next_pow2(2 * K1);
-    uint32_t* htab = reinterpret_cast<uint32_t*>(st + 256);   // [HT]
-    int* rhist = reinterpret_cast<int*>(htab + HT);            // [256]
+    int* rhist = reinterpret_cast<int*>(st + 256);            // [256]
     __syncthreads();   // every survivor written; the scan's scratch is free
     const int S = s_ns;
     if (S > cap) {   // block-uniform: the buffer held only the first cap survivors
@@ -641,20 +730,6 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       sk = P.mrg_scratch + (long long)b * 2 * stride;
       se = sk + stride;
     }
-    for (int x = tid; x < HT; x += kSNT) htab[x] = kNoCand;
-    if (tid == 0) {
-      s_nv = 0;
-      s_ocut = cnt;
-      s_kmin = ~0ull;
-      s_kmax = 0;
-    }
-    __syncthreads();
-    for (int r = tid; r < ndup; r += kSNT) {
-      const uint32_t c = dupc[r];
-      uint32_t pos = chash(c) & (HT - 1);
-      while (atomicCAS(&htab[pos], kNoCand, c) != kNoCand) pos = (pos + 1) & (HT - 1);
-    }
-    __syncthreads();
     const long long Tq = (cnt == K1) ? (long long)(okey[K1 - 1] ^ (1ull << 63)) : LLONG_MAX;
     const long long* aqb = aq_of(P, b, t);
     unsigned long long kmn = ~0ull, kmx = 0;
@@ -663,7 +738,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       bool keep = false;
       unsigned long long kk = 0, ent = 0;
       if (e < S) {
-        ent = surv[e];
+        ent = (e < kSSV) ? ssv[e] : surv[e];
         int i, j;
         surv_sites(ent, i, j);
         ent |= (j < 0) ? (uint32_t)i : pair_index(n, i, j);
@@ -710,29 +785,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
     __syncthreads();
     int nv = s_nv;
     // more kept candidates than the sort takes at once: only the K+1 lowest can enter the list
-    if (nv > 256 && nv > K1) {
-      const unsigned long long x = radix_select<unsigned long long>(sk, nv, K1 - 1, rhist);
-      int kept = 0;
-      for (int u0 = 0; u0 < nv; u0 += kSNT) {
-        const int e = u0 + tid;
-        unsigned long long kk = 0, ee = 0;
-        bool keep = false;
-        if (e < nv) {
-          kk = sk[e];
-          ee = se[e];
-          keep = kk <= x;
-        }
-        int total;
-        const int pos = kept + block_exclusive_sum(keep ? 1 : 0, s_w, &total);
-        if (keep) {
-          sk[pos] = kk;
-          se[pos] = ee;
-        }
-        kept += total;
-        __syncthreads();
-      }
-      nv = kept;
-    }
+    if (nv > 256 && nv > K1) nv = keep_lowest(sk, se, nv, K1, rhist, s_w);
     const unsigned long long kmin = s_kmin;
     const uint32_t n_cand = (uint32_t)n + (uint32_t)((long long)n * (n - 1) / 2);
     const int cb = 32 - __clz((int)n_cand);
@@ -742,13 +795,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       sort_packed_runs(sk, se, nv, kmin, cb, st, so);
       nk = so;
     } else if (nv > 1) {
-      const int m2 = next_pow2(nv);
-      for (int x = nv + tid; x < m2; x += kSNT) {
-        sk[x] = ~0ull;
-        se[x] = ~0ull;
-      }
-      __syncthreads();
-      bitonic_sort_smem(sk, se, m2);
+      sort_pairs_any(sk, se, nv);
     }
     __syncthreads();
     const unsigned long long cmask = (1ull << cb) - 1;
