@@ -412,43 +412,12 @@ def compare_fp64_form(ctx, data, K, R, n, n_inst, I_, ms_split, device, flips="s
             "note": "same searches and iterations; identical kept sets => identical hit rate, TTS ratio = time ratio"}
 
 
-def run_warmstart(args, device=0):
-    """Learned warm start vs random initial states (n = 300 Gaussian instances): train the network on the
-    best states the search finds for `n_train` generated n=300 Gaussian instances, then run the
-    search from learned and from random initial states on 120 held-out instances for a sweep of
-    iteration counts, and report time-to-ground-state for each (reference: the best energy of
-    all runs, not certified)."""
+def _warmstart_eval(ctx, net, stream, test, n, R, seed, sweep):
+    """TTS of learned and random initial states on the held-out instances `test` (already in
+    ctx), over an iteration sweep; reference = best energy of all runs here (not certified)."""
     import torch
-    from paper_2010_00180_gb300 import build as B, qis as Q
     from paper_2010_00180_gb300 import inputs as I
-    B.build()
-    n, K, R, n_train, n_test = 300, 120, 32, args.ws_train, 120
-    t0 = time.perf_counter()
-    net = Q.MLP(hidden=256, max_sites=n * n_train, batch=4096, max_n=n, device=device, seed=args.seed)
-    chunk = 250
-    for c0 in range(0, n_train, chunk):
-        m = min(chunk, n_train - c0)
-        ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=m, device=device)
-        data = []
-        for k in range(m):
-            J, h = I.instance("gaussian", n, seed=args.seed + 50, inst=c0 + k)
-            ctx.create_instance(J, h)
-            ctx.init_states(k, I.random_states(n, R, seed=args.seed + 51, inst=c0 + k))
-            data.append((J, h))
-        ctx.iterate(K)
-        for k, (J, h) in enumerate(data):
-            net.add_example(J, h, ctx.topk_states(k, 1)["bits"][0])
-        ctx.close()
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    loss = net.train(args.ws_epochs, lr=1e-3)
-    t_train = time.perf_counter() - t0
-    test = [I.instance("gaussian", n, seed=args.seed + 90, inst=k) for k in range(n_test)]
-    ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=n_test, device=device)
-    for J, h in test:
-        ctx.create_instance(J, h)
-    stream = torch.cuda.ExternalStream(ctx.stream_handle(), device=device)
-    sweep = [15, 30, 60, 120, 240]
+    n_test = len(test)
     results = {}
     best = np.full(n_test, np.inf)
     for mode in ("random", "learned"):
@@ -457,14 +426,14 @@ def run_warmstart(args, device=0):
                 if mode == "learned":
                     ctx.init_states_learned(k, net)
                 else:
-                    ctx.init_states(k, I.random_states(n, R, seed=args.seed + 91, inst=k))
+                    ctx.init_states(k, I.random_states(n, R, seed=seed + 91, inst=k))
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             ctx.iterate(iters)
             ctx.merge()
             ev1.record(stream)
             ctx.synchronize()
-            E = np.array([ctx.topk_states(k, 1)["E"][0] for k in range(n_test)])
+            E = np.array([x["E"][0] for x in ctx.topk_states_all(1)])
             results[(mode, iters)] = (ev0.elapsed_time(ev1) / 1e3, E)
             best = np.minimum(best, E)
     rows = []
@@ -474,12 +443,74 @@ def run_warmstart(args, device=0):
         rows.append({"init": mode, "iterations": iters, "seconds": round(t, 5), "p1": round(p1, 4), "tts_s": tts})
     finite = [r for r in rows if math.isfinite(r["tts_s"]) and r["tts_s"] > 0]
     best_tts = {m: min((r["tts_s"] for r in finite if r["init"] == m), default=math.inf) for m in ("random", "learned")}
+    return best_tts, rows
+
+
+def run_warmstart(args, device=0):
+    """Learned warm start vs random initial states (n = 300 Gaussian instances), over several
+    training runs and held-out sets: for each training seed, train the network on the best states
+    the search finds for `n_train` generated n = 300 instances; for each held-out set of 120
+    instances, run the search from learned and from random initial states over an iteration
+    sweep and take the best time-to-ground-state of each (reference: the best energy of all runs
+    on that set, not certified). Reports every pair and the spread of the TTS ratio."""
+    import torch
+    from paper_2010_00180_gb300 import build as B, qis as Q
+    from paper_2010_00180_gb300 import inputs as I
+    B.build()
+    n, K, R, n_train, n_test = 300, 120, 32, args.ws_train, 120
+    train_seeds = [int(x) for x in args.ws_seeds.split(",")]
+    held_sets = [int(x) for x in args.ws_heldout.split(",")]
+    sweep = [15, 30, 60, 120, 240]
+    runs = []
+    for ts in train_seeds:
+        seed = args.seed + 1000 * ts
+        t0 = time.perf_counter()
+        net = Q.MLP(hidden=256, max_sites=n * n_train, batch=4096, max_n=n, device=device, seed=seed)
+        chunk = 250
+        for c0 in range(0, n_train, chunk):
+            m = min(chunk, n_train - c0)
+            ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=m, device=device)
+            data = [I.instance("gaussian", n, seed=seed + 50, inst=c0 + k) for k in range(m)]
+            ctx.create_instances(data)
+            for k in range(m):
+                ctx.init_states(k, I.random_states(n, R, seed=seed + 51, inst=c0 + k))
+            ctx.iterate(K)
+            tops = ctx.topk_states_all(1)
+            for k, (J, h) in enumerate(data):
+                net.add_example(J, h, tops[k]["bits"][0])
+            ctx.close()
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        loss = net.train(args.ws_epochs, lr=1e-3)
+        t_train = time.perf_counter() - t0
+        for hs in held_sets:
+            hseed = args.seed + 90 + 7 * hs
+            test = [I.instance("gaussian", n, seed=hseed, inst=k) for k in range(n_test)]
+            ctx = Q.Context(K=K, R=R, precision="split_bf16", max_n=n, max_instances=n_test, device=device)
+            ctx.create_instances(test)
+            stream = torch.cuda.ExternalStream(ctx.stream_handle(), device=device)
+            best_tts, rows = _warmstart_eval(ctx, net, stream, test, n, R, hseed, sweep)
+            ctx.close()
+            ratio = best_tts["learned"] / best_tts["random"] if math.isfinite(best_tts["random"]) else None
+            runs.append({"train_seed": ts, "heldout_set": hs, "final_train_loss": round(loss, 5),
+                         "data_gen_s": round(t_data, 2), "train_s": round(t_train, 2),
+                         "tts_learned_s": best_tts["learned"], "tts_random_s": best_tts["random"],
+                         "ratio_learned_over_random": ratio, "sweep": rows})
+        net.close()
+    ratios = [r["ratio_learned_over_random"] for r in runs if r["ratio_learned_over_random"] is not None
+              and math.isfinite(r["ratio_learned_over_random"])]
+    summary = {"runs": len(runs), "ratio_median": float(np.median(ratios)) if ratios else None,
+               "ratio_min": min(ratios) if ratios else None, "ratio_max": max(ratios) if ratios else None,
+               "learned_faster_in": sum(1 for x in ratios if x < 1.0),
+               "mean_final_train_loss": float(np.mean([r["final_train_loss"] for r in runs])),
+               "ln2": math.log(2.0)}
     line = {"metric": "time-to-ground-state, learned vs random initial states, N=300", "unit": "s",
-            "value": best_tts["learned"], "higher_is_better": False, "baseline_random_tts_s": best_tts["random"],
+            "value": float(np.median([r["tts_learned_s"] for r in runs])), "higher_is_better": False,
+            "baseline_random_tts_s": float(np.median([r["tts_random_s"] for r in runs])),
             "config": {"workload": "warmstart_gaussian_n300", "n": n, "K": K, "R": R, "train_instances": n_train,
-                       "test_instances": n_test, "epochs": args.ws_epochs, "final_train_loss": round(loss, 5),
-                       "data_gen_s": round(t_data, 2), "train_s": round(t_train, 2)},
-            "sweep": rows, "reference": "best energy of all runs in this sweep (not certified)",
+                       "test_instances": n_test, "epochs": args.ws_epochs, "train_seeds": train_seeds,
+                       "heldout_sets": held_sets, "sweep_iterations": sweep},
+            "summary": summary, "runs": runs, "reference": "best energy of all runs on each held-out set (not certified)",
             "data": "synthetic"}
     print(json.dumps(line))
 
@@ -680,6 +711,8 @@ def main():
     ap.add_argument("--warmstart", action="store_true", help="learned vs random warm start (n=300) instead")
     ap.add_argument("--ws-train", type=int, default=2000, help="training instances of the warm-start run")
     ap.add_argument("--ws-epochs", type=int, default=20)
+    ap.add_argument("--ws-seeds", default="0,1,2", help="training seeds of the warm-start comparison")
+    ap.add_argument("--ws-heldout", default="0,1", help="held-out instance sets of the warm-start comparison")
     args = ap.parse_args()
 
     if args.warmstart:

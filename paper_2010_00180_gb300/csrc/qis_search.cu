@@ -25,7 +25,9 @@
 
 namespace qis {
 
-constexpr int kSNT = 128;   // threads of a search block
+constexpr int kSNT = 128;          // threads of a search block
+constexpr int kSW = kSNT / 32;      // its warps
+constexpr int kSMinBlocks = 8;      // resident blocks per SM the register budget is set for
 
 __host__ __device__ inline int search_pcs(int cap, int merge_cand) {
   const int pc = next_pow2(cap > 256 ? cap : 256);
@@ -180,7 +182,7 @@ static __device__ __noinline__ void sort_pairs_any(unsigned long long* sk, unsig
 
 // FL: flip set (QIS_FLIPS_*). One block of kSNT threads per search; n_iters >= 1.
 template <int FL>
-__global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
+__global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_iters) {
   constexpr bool EX = FL == QIS_FLIPS_EXCHANGE;
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
   unsigned char* scr = smem + L.scratch;
 
   __shared__ int s_sel, s_near, s_ns, s_nsites, s_n2, s_bin, s_bin2, s_nl, s_nv, s_ocut;
-  __shared__ float wf[8];
+  __shared__ float wf[2 * kSW];
   __shared__ int s_w[33];
   __shared__ unsigned long long s_kmin, s_kmax;
 
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
     }
     if (lane == 0) {
       wf[warp] = mn;
-      wf[4 + warp] = mx;
+      wf[kSW + warp] = mx;
     }
     if (tid == 0) {
       s_near = 0;
@@ -362,8 +364,12 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       for (int x = tid; x < 4 * 256; x += kSNT) hist[x] = 0;
     }
     __syncthreads();   // the fields and the range are complete
-    const float amin = fminf(fminf(wf[0], wf[1]), fminf(wf[2], wf[3]));
-    const float amax = fmaxf(fmaxf(wf[4], wf[5]), fmaxf(wf[6], wf[7]));
+    float amin = wf[0], amax = wf[kSW];
+#pragma unroll
+    for (int w = 1; w < kSW; ++w) {
+      amin = fminf(amin, wf[w]);
+      amax = fmaxf(amax, wf[kSW + w]);
+    }
     mn = INFINITY;
     mx = -INFINITY;
     for (int r = tid; r < cnt; r += kSNT) {
@@ -586,7 +592,9 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
       __syncthreads();
       const int nl = s_nl;
       if (nl > 0) {   // block-uniform
-        const float B = fmaxf(fmaxf(wf[0], wf[1]), fmaxf(wf[2], wf[3]));
+        float B = wf[0];
+#pragma unroll
+        for (int w = 1; w < kSW; ++w) B = fmaxf(B, wf[w]);
         const float span = __fsub_ru(B, amin);
         const float inv = (span > 0.f && span < INFINITY) ? __fdiv_rn((float)kSparseNB, span) : 0.f;
         for (int j = tid; j < n; j += kSNT)
@@ -660,7 +668,9 @@ __global__ void __launch_bounds__(kSNT, 8) k_search(DevPtrs P, int n_iters) {
           }
         }
         __syncthreads();
-        const int tot = s_w[0] + s_w[1] + s_w[2] + s_w[3];
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kSW; ++w) tot += s_w[w];
         constexpr int PB = 4;
         for (int u0 = 0; u0 < tot; u0 += PB * kSNT) {
           float cv[PB], av[PB], pv[PB], jv[PB];

@@ -111,3 +111,32 @@ def test_learned_initial_states_are_lower_than_random():
         ctx.close()
     print(f"mean initial energy: learned {np.mean(e_learned):.2f}, random {np.mean(e_random):.2f}")
     assert np.mean(e_learned) < np.mean(e_random)
+
+
+def test_adam_steps_match_numpy():
+    """Two training steps on a one-batch training set against Adam written out in numpy (beta
+    0.9 / 0.999, eps 1e-8, bias-corrected moments, the FP32 master weights updated), each step's
+    gradient taken from the library's own backward pass at the weights of that step."""
+    n, lr = 200, 1e-3
+    net = qis.MLP(hidden=32, max_sites=1024, batch=1024, max_n=n, seed=9)
+    J, h = I.instance("gaussian", n, seed=810)
+    bits = I.random_states(n, 1, seed=811)[0]
+    net.add_example(J, h, bits)
+    X = net.features(J, h)
+    y = (I.unpack_bits(bits, n)[0] == 0).astype(np.float32)   # y_i = 1 <=> s_i = +1 (sigma_i = 0)
+    p = net.get_params().astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    for t in (1, 2):
+        _, g = net.loss_grad(X, y)
+        g = g.astype(np.float64)
+        net.train(1, lr=lr)                         # one batch: one Adam step
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        p = p - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+        got = net.get_params().astype(np.float64)
+        # FP32 arithmetic in the kernel and atomics in the gradient sums: each update agrees to a
+        # small fraction of the step size lr
+        np.testing.assert_allclose(got, p, rtol=0, atol=2e-3 * lr + 1e-7, err_msg=f"step {t}")
+        p = got                                     # continue from the library's weights
