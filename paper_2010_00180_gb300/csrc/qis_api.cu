@@ -47,6 +47,7 @@ struct qis_ctx {
   uint64_t* zob = nullptr;
   double* stats = nullptr;
   double* jstage = nullptr;
+  LayoutItem* items_d = nullptr;   // [max_inst] staging places of a creation batch
   uint64_t* all_bits = nullptr;   // [max_inst][K1][Wmax] every instance's merged states
   double* all_E = nullptr;        // [max_inst][K1]   // [max_n * max_n] one instance's J as copied from the host
   int4* work = nullptr;    // FP64 scan: 64 x 64 tiles x groups of searches
@@ -73,6 +74,7 @@ struct qis_ctx {
   bool no_fused = false;                    // QIS_FUSED=0: the per-kernel form of every iteration
   cudaGraphExec_t graph_exec = nullptr;     // one iteration, captured for the current instances
   int graph_n = 0;                          // fused form: the iteration count the graph was captured for
+  int last_n = 0;                           // fused form: the iteration count of the previous call
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
   size_t ev_used[8] = {0};
   std::string err = "no error";
@@ -267,6 +269,7 @@ void drop_graph(qis_ctx* ctx) {
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   ctx->graph_exec = nullptr;
   ctx->graph_n = 0;
+  ctx->last_n = 0;
 }
 
 int build_work(qis_ctx* ctx) {
@@ -274,7 +277,7 @@ int build_work(qis_ctx* ctx) {
   ctx->P.gemm_nt = ctx->tune.gemm_tile_searches > 0 ? ctx->tune.gemm_tile_searches
                                                       : gemm_tile_n(ctx->R, ctx->digits_used);
   std::vector<int4> w;
-  for (int id = 0; id < (int)ctx->inst.size(); ++id) {
+  for (int id = 0; id < (int)ctx->inst.size() && ctx->mode == QIS_FP64; ++id) {   // the FP64 scan's tiles
     const int nb = (ctx->inst[id].n + kTile - 1) / kTile;
     for (int bi = 0; bi < nb; ++bi)
       for (int bj = bi; bj < nb; ++bj)
@@ -288,14 +291,15 @@ int build_work(qis_ctx* ctx) {
   // warp tasks of the FP32 pair scan, widest chunks first (better tail balance)
   std::vector<int4> t;
   const int RG = ctx->tune.scan_search_group > 0 ? ctx->tune.scan_search_group : ctx->R;
-  for (int id = 0; id < (int)ctx->inst.size(); ++id)
+  const bool dense = ctx->mode != QIS_FP64 && !sparse_scan(ctx);   // only the dense FP32 scan reads them
+  for (int id = 0; id < (int)ctx->inst.size() && dense; ++id)
     scan_tasks_for(id, ctx->inst[id].n, ctx->tune.scan_chunk_nc, ctx->R, RG, t);
   std::stable_sort(t.begin(), t.end(), [](const int4& a, const int4& b) { return (a.w & 0xff) > (b.w & 0xff); });
   if (t.size() > ctx->tasks_cap)
     return fail(ctx, QIS_ERR_INVALID_ARG, "too many scan tasks for this tuning (wider chunks or larger search groups)");
   ctx->n_tasks = (int)t.size();
+  // (copies from pageable memory: the host vectors are free once the calls return)
   if (!t.empty()) CK(cudaMemcpyAsync(ctx->tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
   ctx->work_dirty = false;
   return 0;
 }
@@ -370,6 +374,7 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     }
     ALLOC(ctx->zob, kMaxN);
     ALLOC(ctx->stats, (size_t)ctx->max_inst * (NP + 8));   // validation statistics of every instance
+    ALLOC(ctx->items_d, (size_t)ctx->max_inst);
     if (ctx->mode == QIS_FP64) ALLOC(ctx->jstage, (size_t)cfg->max_n * cfg->max_n);   // the split modes stage in Jq
     ALLOC(ctx->all_bits, (size_t)ctx->max_inst * K1 * W);
     ALLOC(ctx->all_E, (size_t)ctx->max_inst * K1);
@@ -609,12 +614,14 @@ int describe_instance(qis_ctx* ctx, int id, int n, const double* st, InstDesc& d
 int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds) {
   cudaStream_t s = ctx->stream;
   CK(cudaMemcpyAsync(ctx->inst_d + first, ds.data(), sizeof(InstDesc) * ds.size(), cudaMemcpyHostToDevice, s));
+  if (ctx->mode != QIS_FP64 && !ds.empty()) {
+    // fixed-point planes, digits and row maxima of the whole batch: two launches
+    int max_pad = 0;
+    for (const InstDesc& d : ds) max_pad = std::max(max_pad, d.n_pad);
+    LAUNCH(launch_prepare_batch(ctx->P, first, (int)ds.size(), max_pad, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
+  }
   for (size_t k = 0; k < ds.size(); ++k) {
     const InstDesc& d = ds[k];
-    if (ctx->mode != QIS_FP64) {
-      LAUNCH(launch_quantize(ctx->P, d, first + (int)k, ctx->D16, ctx->Jq, ctx->J4, ctx->hq, s));
-      LAUNCH(launch_rowmax4(ctx->P, d, s));
-    }
     ctx->inst.push_back(d);
     if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
     ctx->inst_ready.push_back(0);
@@ -689,11 +696,22 @@ int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* co
       const int rc = copy_instance(ctx, n[k], J[k], stage);
       if (rc) return rc;
     }
+    // padded layout and validation of the whole batch: two launches
+    std::vector<LayoutItem> items(count);
+    int max_pad = 0;
     for (int k = 0; k < count; ++k) {
-      const double* stage = reinterpret_cast<const double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
-      const int rc = lay_out_instance(ctx, first + k, k, n[k], stage);
-      if (rc) return rc;
+      LayoutItem& L = items[k];
+      L.src = reinterpret_cast<const double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
+      L.off_mat = (long long)(first + k) * ctx->NP * ctx->NP;
+      L.off_vec = (long long)(first + k) * ctx->NP;
+      L.n = n[k];
+      L.n_pad = pad_of(n[k]);
+      L.stats = ctx->stats + (size_t)k * (ctx->NP + 8);
+      max_pad = std::max(max_pad, L.n_pad);
     }
+    CK(cudaMemsetAsync(ctx->stats, 0, sizeof(double) * (size_t)count * (ctx->NP + 8), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->items_d, items.data(), sizeof(LayoutItem) * count, cudaMemcpyHostToDevice, ctx->stream));
+    LAUNCH(launch_layout_batch(ctx->P, ctx->items_d, count, max_pad, ctx->J64, ctx->stream));
   } else {
     for (int k = 0; k < count; ++k) {
       int rc = copy_instance(ctx, n[k], J[k], ctx->jstage);
@@ -851,7 +869,11 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
   const DevPtrs& P = ctx->P;
   if (fused_search(ctx) && n_iters > 0) {
     // the kernels of the whole call, captured once per iteration count and replayed
-    if (!ctx->profiling && ctx->use_graph) {
+    // a call with the iteration count of the previous one replays a captured graph; the first
+    // call with a new count (or after the instances changed) launches directly
+    const bool replay = !ctx->profiling && ctx->use_graph && (ctx->graph_n == n_iters || ctx->last_n == n_iters);
+    ctx->last_n = n_iters;
+    if (replay) {
       if (ctx->graph_exec && ctx->graph_n != n_iters) drop_graph(ctx);
       if (!ctx->graph_exec) {
         cudaGraph_t g = nullptr;

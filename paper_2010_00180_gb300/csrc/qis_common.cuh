@@ -294,6 +294,17 @@ int mlp_max_n(const qis_mlp* m);
 
 // Kernel launchers (defined in the .cu files); each returns the cudaError_t of the launch.
 cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cudaStream_t s);
+// Where one instance of a creation batch was staged and where its layout and statistics go.
+struct LayoutItem {
+  const double* src;   // n x n FP64, contiguous, as copied from the host
+  long long off_mat, off_vec;
+  int n, n_pad;
+  double* stats;       // its validation statistics (NP + 8 doubles)
+};
+cudaError_t launch_layout_batch(const DevPtrs& P, const LayoutItem* items, int count, int max_n_pad, double* J64,
+                                cudaStream_t s);
+cudaError_t launch_prepare_batch(const DevPtrs& P, int first, int count, int max_n_pad, __half* D16, long long* Jq,
+                                 float* J4, long long* hq, cudaStream_t s);
 cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s);
 cudaError_t launch_scan_sparse(const DevPtrs& P, cudaStream_t s);
 constexpr int kSparseMaxNP = 4096;   // the sparse pair scan's largest padded n (shared-memory lists)

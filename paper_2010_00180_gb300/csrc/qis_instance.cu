@@ -32,14 +32,12 @@ __device__ inline int frac_bits(double x) {
 // bitwise symmetry, fraction bits and max |J_ij| (as the bit patterns of non-negative
 // doubles, which order as integers), and the row sum of |J_ij|, j > i, reduced in a fixed
 // shuffle order (deterministic). Sum of |h| is formed on the host.
-__global__ void __launch_bounds__(256) k_validate(const double* J64, const double* h64, int n, int n_pad, double* stats) {
+__device__ __forceinline__ void validate_row(const double* J64, const double* h64, int n, int n_pad, double* stats, int i) {
   int* bad = reinterpret_cast<int*>(stats);
   int* maxfrac = reinterpret_cast<int*>(stats + 1);
   unsigned long long* maxJ = reinterpret_cast<unsigned long long*>(stats + 2);
   unsigned long long* maxh = reinterpret_cast<unsigned long long*>(stats + 3);
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (i >= n) return;   // warp-uniform
   const double* row = J64 + (long long)i * n_pad;
   double rs = 0.0;
   int fb = 0, b = 0;
@@ -77,6 +75,20 @@ __global__ void __launch_bounds__(256) k_validate(const double* J64, const doubl
   }
 }
 
+__global__ void __launch_bounds__(256) k_validate(const double* J64, const double* h64, int n, int n_pad, double* stats) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= n) return;   // warp-uniform
+  validate_row(J64, h64, n, n_pad, stats, i);
+}
+
+// A batch of instances at once: blockIdx.y is the instance of the batch (its layout item).
+__global__ void __launch_bounds__(256) k_validate_batch(const LayoutItem* items, const double* J64, const double* h64) {
+  const LayoutItem L = items[blockIdx.y];
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= L.n) return;   // warp-uniform
+  validate_row(J64 + L.off_mat, h64 + L.off_vec, L.n, L.n_pad, L.stats, i);
+}
+
 cudaError_t launch_validate(const DevPtrs& P, int inst, int n, long long off_mat, long long off_vec,
                             double* stats, cudaStream_t s) {
   (void)inst;
@@ -95,6 +107,27 @@ __global__ void k_restride(const double* src, int n, int n_pad, double* dst) {
     const int i = (int)(e / n_pad), j = (int)(e % n_pad);
     dst[e] = (i < n && j < n) ? src[(long long)i * n + j] : 0.0;
   }
+}
+
+__global__ void k_restride_batch(const LayoutItem* items, double* J64) {
+  const LayoutItem L = items[blockIdx.y];
+  const long long total = (long long)L.n_pad * L.n_pad;
+  double* dst = J64 + L.off_mat;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / L.n_pad), j = (int)(e % L.n_pad);
+    dst[e] = (i < L.n && j < L.n) ? L.src[(long long)i * L.n + j] : 0.0;
+  }
+}
+
+// Layout and validation of `count` staged instances (items on the device), two launches.
+cudaError_t launch_layout_batch(const DevPtrs& P, const LayoutItem* items, int count, int max_n_pad, double* J64,
+                                cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const long long total = (long long)max_n_pad * max_n_pad;
+  const int bx = (int)std::min<long long>((total + 255) / 256, 2048);
+  k_restride_batch<<<dim3(bx, count), 256, 0, s>>>(items, J64);
+  k_validate_batch<<<dim3((max_n_pad + 7) / 8, count), 256, 0, s>>>(items, P.J64, P.h64);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_restride(const double* src, int n, int n_pad, double* dst, cudaStream_t s) {
@@ -126,6 +159,57 @@ __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pa
     }
   }
   if (e < n_pad) hq[e] = (e < n) ? __double2ll_rn(ldexp(h64[e], q)) : 0;
+}
+
+// Instances first .. first+count-1 at once (blockIdx.y), descriptors read on the device.
+__global__ void k_quantize_batch(DevPtrs P, int first, __half* D16, long long* Jq, float* J4, long long* hq) {
+  const int inst = first + blockIdx.y;
+  const InstDesc d = P.inst[inst];
+  const long long tot = (long long)d.n_pad * d.n_pad;
+  const double* J64 = P.J64 + d.off_mat;
+  __half* D = D16 + (long long)inst * P.NP * P.NP;
+  const long long base = 1ll << d.dbits;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d.n_pad), j = (int)(e % d.n_pad);
+    long long v = 0;
+    if (i < d.n && j < d.n) v = __double2ll_rn(ldexp(J64[e], d.q));
+    Jq[d.off_mat + e] = v;
+    J4[d.off_mat + e] = (float)(4.0 * ldexp((double)v, -d.q));
+    long long x = v;
+    for (int dg = 0; dg < d.digits; ++dg) {
+      long long r = x & (base - 1);           // x mod base
+      if (r >= base / 2) r -= base;           // balanced digit in [-base/2, base/2)
+      D[dg * P.pool_mat + d16_offset(i, j, P.NP)] = __float2half_rn((float)r);
+      x = (x - r) >> d.dbits;                 // exact
+    }
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.n_pad; e += gridDim.x * blockDim.x)
+    hq[d.off_vec + e] = (e < d.n) ? __double2ll_rn(ldexp(P.h64[d.off_vec + e], d.q)) : 0;
+}
+
+__global__ void __launch_bounds__(256) k_rowmax4_batch(DevPtrs P, int first) {
+  const InstDesc d = P.inst[first + blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= d.n_pad) return;   // warp-uniform
+  const float* J4 = P.J4 + d.off_mat;
+  float m = 0.f;
+  if (i < d.n)
+    for (int j = lane; j < d.n; j += 32) m = fmaxf(m, fabsf(J4[(long long)i * d.n_pad + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) P.rm4[d.off_vec + i] = m;
+}
+
+// Fixed-point planes, digits and row maxima of instances first .. first+count-1, two launches.
+cudaError_t launch_prepare_batch(const DevPtrs& P, int first, int count, int max_n_pad, __half* D16, long long* Jq,
+                                 float* J4, long long* hq, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const long long tot = (long long)max_n_pad * max_n_pad;
+  const int bx = (int)std::min<long long>((tot + 255) / 256, 2048);
+  k_quantize_batch<<<dim3(bx, count), 256, 0, s>>>(P, first, D16, Jq, J4, hq);
+  k_rowmax4_batch<<<dim3((max_n_pad + 7) / 8, count), 256, 0, s>>>(P, first);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
