@@ -100,8 +100,10 @@ const char* qis_last_error(const qis_ctx* ctx);
 
 /* Add one Ising instance H0 (Eq. (1)).
  *   n: number of spins, 2 <= n <= cfg.max_n.
- *   J: n*n FP64 row-major, symmetric (bitwise J_ij == J_ji), zero diagonal, finite.
- *   h: n FP64 finite.
+ *   J: n*n FP64 row-major, symmetric (bitwise J_ij == J_ji), zero diagonal, finite; host
+ *      memory (not retained). In the split modes a page-locked J (cudaHostAlloc /
+ *      cudaHostRegister) is read by the device directly, without a staging copy.
+ *   h: n FP64 finite, host memory.
  * Instances get consecutive ids from 0. In QIS_SPLIT_BF16 the values are represented on
  * the grid 2^-q with the smallest q that holds them exactly, capped so that every energy
  * sum stays below 2^52 * 2^-q; if the cap binds, J and h are rounded to that grid and

@@ -520,13 +520,23 @@ int check_instance_args(qis_ctx* ctx, int id, int n, const double* J, const doub
   return 0;
 }
 
-// Copy J and h of instance id to the device and validate them into stats slot `slot`
-// (asynchronous on the library stream).
 // Copy J of instance id to the device (asynchronous on the library stream) as one contiguous
 // block (a pitched copy from pageable memory goes row by row), into `stage`.
 int copy_instance(qis_ctx* ctx, int n, const double* J, double* stage) {
   CK(cudaMemcpyAsync(stage, J, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, ctx->stream));
   return 0;
+}
+
+// The device address of page-locked host memory at p (registered or allocated by CUDA, so the
+// GPU reads it over the host link), or NULL for any other memory.
+const double* pinned_view(const double* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // not a sticky error: clear it and stage the copy
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return reinterpret_cast<const double*>(a.devicePointer);
+  return nullptr;
 }
 
 // h of instances first .. first+count-1, zero padded to NP, in one copy (their regions are
@@ -651,7 +661,10 @@ int flush_init(qis_ctx* ctx) {
     }
     int e = a;
     while (e < ni && ctx->init_pending[e]) ctx->init_pending[e++] = 0;
-    LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream));
+    // split modes: the initial energies of the range in groups of states per block first
+    const bool grouped = ctx->mode != QIS_FP64;
+    if (grouped) LAUNCH(launch_init_energy(ctx->P, a, e - a, ctx->stream));
+    LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream, grouped));
     a = e;
   }
   return 0;
@@ -691,17 +704,23 @@ int qis_create_instances(qis_ctx* ctx, int count, const int* n, const double* co
     if (rc) return rc;
   }
   if (ctx->mode != QIS_FP64) {
+    // a page-locked J is read by the layout kernel itself (one pass over the host memory);
+    // any other J is staged with a copy first
+    std::vector<const double*> src(count);
     for (int k = 0; k < count; ++k) {
+      src[k] = pinned_view(J[k]);
+      if (src[k]) continue;
       double* stage = reinterpret_cast<double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
       const int rc = copy_instance(ctx, n[k], J[k], stage);
       if (rc) return rc;
+      src[k] = stage;
     }
     // padded layout and validation of the whole batch: two launches
     std::vector<LayoutItem> items(count);
     int max_pad = 0;
     for (int k = 0; k < count; ++k) {
       LayoutItem& L = items[k];
-      L.src = reinterpret_cast<const double*>(ctx->Jq + (long long)(first + k) * ctx->NP * ctx->NP);
+      L.src = src[k];
       L.off_mat = (long long)(first + k) * ctx->NP * ctx->NP;
       L.off_vec = (long long)(first + k) * ctx->NP;
       L.n = n[k];

@@ -338,6 +338,7 @@ size_t final_merge_smem(int K1);
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s);
 cudaError_t launch_topk_all(const DevPtrs& P, int k, uint64_t* out, double* E, cudaStream_t s);
+cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, cudaStream_t s);
 cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, int k, uint64_t* bits_out,
                                  cudaStream_t s);
 

@@ -242,45 +242,22 @@ cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s) 
 
 // ---------------------------------------------------------------- search initialisation
 // Alg. 3 initial list: [psi0, K placeholders], E(psi0) from Eq. (1), nothing used.
-// Split modes: E0 = (sum_{i<j} Jq_ij s_i s_j + sum_i hq_i s_i) 2^-q in exact int64.
-// FP64 mode: one thread adds the pair terms i-major, j ascending, then the field terms.
-// cached: the initial state's energy was computed by an earlier launch for the same initial
-// states (qis_reset) and is taken from init_E / init_q instead of being summed again.
+// cached: E(psi0) is taken from init_E / init_q, written by k_init_energy (split modes: exact
+// int64 E 2^q, several states per block) or by an earlier launch for the same initial states
+// (qis_reset). Otherwise (FP64 mode) one thread adds the pair terms i-major, j ascending, then
+// the field terms.
 __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cached) {
   const int b = b0 + blockIdx.x;
   const InstDesc d = P.inst[b / P.R];
   const int n = d.n, np = d.n_pad, W = d.W;
   __shared__ uint64_t bits[kMaxN / 64];
-  __shared__ long long red[256];
+  __shared__ long long red[1];
   for (int w = threadIdx.x; w < W; w += blockDim.x) bits[w] = P.init_bits[(long long)b * P.Wmax + w];
   __syncthreads();
   double E0 = 0.0;
   if (cached) {
     E0 = P.init_E[b];
     if (threadIdx.x == 0) red[0] = P.init_q[b];
-  } else if (P.mode != QIS_FP64) {
-    // exact E 2^q: a warp per row i, its lanes over the columns j > i (coalesced)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long acc = 0;
-    for (int i = warp; i < n; i += 8) {
-      const long long* row = P.Jq + d.off_mat + (long long)i * np;
-      const int si = sigma_of(bits, i);
-      long long r = 0;
-#pragma unroll 4
-      for (int j = i + 1 + lane; j < n; j += 32) r += (si ^ sigma_of(bits, j)) ? -row[j] : row[j];
-      if (lane == 0) {
-        const long long hv = P.hq[d.off_vec + i];
-        r += si ? -hv : hv;
-      }
-      acc += r;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    E0 = ldexp((double)red[0], -d.q);
   } else if (threadIdx.x == 0) {
     double Pp = 0.0, F = 0.0;
     const double* J = P.J64 + d.off_mat;
@@ -293,24 +270,32 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
     }
     for (int i = 0; i < n; ++i) F = __dadd_rn(F, P.h64[d.off_vec + i] * (sigma_of(bits, i) ? -1.0 : 1.0));
     E0 = __dadd_rn(Pp, F);
+    red[0] = 0;
   }
+  // Zobrist hash of psi0: XOR over the threads' sites, then over the warps
+  __shared__ uint64_t s_h[8];
+  uint64_t hsh = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (sigma_of(bits, i)) hsh ^= P.zob[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hsh ^= __shfl_xor_sync(0xffffffffu, hsh, o);
+  if ((threadIdx.x & 31) == 0) s_h[threadIdx.x >> 5] = hsh;
+  const long long base = (long long)b * P.K1;
+  for (int w = threadIdx.x; w < W; w += blockDim.x) P.lst_bits[base * P.Wmax + w] = bits[w];
+  for (int k = threadIdx.x; k < P.K1; k += blockDim.x) {
+    P.lst_used[base + k] = 0;
+    P.lst_ord[base + k] = (k == 0) ? 0 : -1;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) hsh ^= s_h[w];
     P.init_E[b] = E0;
     P.init_q[b] = (P.mode != QIS_FP64) ? red[0] : 0;
-    uint64_t hsh = 0;
-    for (int i = 0; i < n; ++i)
-      if (sigma_of(bits, i)) hsh ^= P.zob[i];
-    const long long base = (long long)b * P.K1;
-    for (int w = 0; w < W; ++w) P.lst_bits[base * P.Wmax + w] = bits[w];
     P.lst_E[base] = E0;
     if (P.mode != QIS_FP64) P.lst_q[base] = red[0];
     P.lst_key[base] = (P.mode != QIS_FP64) ? qkey(red[0]) : dkey(E0);
     P.lst_stamp[base] = 0;
     P.lst_hash[base] = hsh;
-    for (int k = 0; k < P.K1; ++k) {
-      P.lst_used[base + k] = 0;
-      P.lst_ord[base + k] = (k == 0) ? 0 : -1;
-    }
     P.lst_count[b] = 1;
     P.active[b] = 1;
     P.iter_t[b] = 0;
@@ -325,72 +310,112 @@ cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s,
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- FP64 rescoring
-// E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i from scratch in FP64 (one block per state;
-// thread t owns rows t, t+256, ...; fixed reduction tree, so the result is reproducible).
-// One block per state: the state's bits staged in shared memory; warp w takes rows w, w+8, ...
-// and its lanes the columns j > i of a row (coalesced, several loads in flight), s_i times the
-// partial row sum accumulated per lane; block reduction at the end.
+// ---------------------------------------------------------------- rescoring from scratch
+// E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i (Eq. 1) of up to kRG states of one instance per
+// block of 256 threads. With x_ij = 1 where s_i != s_j (s = -1 where the bit is set),
+// s_i s_j = 1 - 2 x_ij and s_i = 1 - 2 sigma_i, so
+//   E = (sum_{i<j} J_ij + sum_i h_i) - 2 (sum_{i<j, x_ij = 1} J_ij + sum_{sigma_i = 1} h_i):
+// one pass over the upper triangle serves every state of the block. mask[j] holds the block's
+// spins of site j as bits; a coupling loaded once is added to the accumulator of every state
+// whose two spins differ. Warp w takes rows w, w + 8, ..., its lanes the columns j > i
+// (coalesced). T = long long: the exact fixed-point couplings Jq, hq of an instance on its grid
+// 2^-q (every summation order gives the same integer); T = double: the FP64 couplings, summed in
+// an order fixed by the block shape and not by the state's place in the group.
+constexpr int kRG = 16;
+
 template <typename T>
-__device__ __forceinline__ T block_sum256(T v, T* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+__device__ void rescore_group(const T* __restrict__ Jm, const T* __restrict__ hv, int n, int n_pad,
+                              const uint16_t* __restrict__ mask, T* red /* [9][kRG + 1] */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T q = 0, p[kRG];
+#pragma unroll
+  for (int g = 0; g < kRG; ++g) p[g] = 0;
+  for (int i = warp; i < n; i += 8) {
+    const T* __restrict__ row = Jm + (long long)i * n_pad;
+    const unsigned mi = mask[i];
+#pragma unroll 2
+    for (int j = i + 1 + lane; j < n; j += 32) {
+      const T v = row[j];
+      const unsigned x = mi ^ mask[j];
+      q += v;
+#pragma unroll
+      for (int g = 0; g < kRG; ++g)
+        if ((x >> g) & 1u) p[g] += v;
+    }
   }
-  return red[0];
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const T v = hv[i];
+    const unsigned m = mask[i];
+    q += v;
+#pragma unroll
+    for (int g = 0; g < kRG; ++g)
+      if ((m >> g) & 1u) p[g] += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+#pragma unroll
+    for (int g = 0; g < kRG; ++g) p[g] += __shfl_xor_sync(0xffffffffu, p[g], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int g = 0; g < kRG; ++g) red[warp * (kRG + 1) + g] = p[g];
+    red[warp * (kRG + 1) + kRG] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x <= kRG) {
+    T t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w * (kRG + 1) + threadIdx.x];
+    red[8 * (kRG + 1) + threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRG) red[threadIdx.x] = red[8 * (kRG + 1) + kRG] - 2 * red[8 * (kRG + 1) + threadIdx.x];
+  __syncthreads();   // red[g] = the energy of state g (times 2^q for the exact form)
 }
 
-__global__ void __launch_bounds__(256) k_rescore(const double* J64, const double* h64, int n, int n_pad,
-                                                 const uint64_t* states, int Wn, double* E_out) {
-  __shared__ uint64_t sb[kMaxN / 64];
-  __shared__ double red[256];
-  for (int w = threadIdx.x; w < Wn; w += blockDim.x) sb[w] = states[(long long)blockIdx.x * Wn + w];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc = 0.0;
-  for (int i = warp; i < n; i += 8) {
-    const double* row = J64 + (long long)i * n_pad;
-    double r = (lane == 0) ? h64[i] : 0.0;
-#pragma unroll 4
-    for (int j = i + 1 + lane; j < n; j += 32) r += sigma_of(sb, j) ? -row[j] : row[j];
-    acc += sigma_of(sb, i) ? -r : r;
+// The spin masks of cnt <= kRG states (their words at src[g], Wn words each) into mask[0..n).
+__device__ void group_masks(const uint64_t* const* src, int cnt, int n, uint16_t* mask) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    unsigned m = 0;
+    for (int g = 0; g < cnt; ++g) m |= (unsigned)((src[g][j >> 6] >> (j & 63)) & 1ull) << g;
+    mask[j] = (uint16_t)m;
   }
-  const double E = block_sum256(acc, red);
-  if (threadIdx.x == 0) E_out[blockIdx.x] = E;
 }
 
-// The same energy from the exact fixed-point couplings (split modes, instances on their grid
-// 2^-q): E 2^q = sum_{i<j} s_i s_j Jq_ij + sum_i s_i hq_i in int64, exact, so E = (E 2^q) 2^-q
-// is the value every FP64 summation order of these grid numbers gives (their partial sums are
-// exact), at integer instead of FP64 throughput.
-__global__ void __launch_bounds__(256) k_rescore_q(const long long* Jq, const long long* hq, int n, int n_pad,
-                                                   double inv_scale, const uint64_t* states, int Wn, double* E_out) {
-  __shared__ uint64_t sb[kMaxN / 64];
-  __shared__ long long red[256];
-  for (int w = threadIdx.x; w < Wn; w += blockDim.x) sb[w] = states[(long long)blockIdx.x * Wn + w];
+// Energies of `count` states (Wn words each, consecutive) of one instance: block g0 / kRG takes
+// states g0 .. g0 + kRG - 1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rescore(const T* Jm, const T* hv, int n, int n_pad, double scale,
+                                                 const uint64_t* states, int Wn, int count, double* E_out) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  T* red = reinterpret_cast<T*>(rsm);
+  uint16_t* mask = reinterpret_cast<uint16_t*>(red + 9 * (kRG + 1));
+  __shared__ const uint64_t* src[kRG];
+  const int g0 = blockIdx.x * kRG, cnt = min(kRG, count - g0);
+  if (threadIdx.x < kRG) src[threadIdx.x] = states + (long long)(g0 + min((int)threadIdx.x, cnt - 1)) * Wn;
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long acc = 0;
-  for (int i = warp; i < n; i += 8) {
-    const long long* row = Jq + (long long)i * n_pad;
-    long long r = (lane == 0) ? hq[i] : 0;
-#pragma unroll 4
-    for (int j = i + 1 + lane; j < n; j += 32) r += sigma_of(sb, j) ? -row[j] : row[j];
-    acc += sigma_of(sb, i) ? -r : r;
-  }
-  const long long Eq = block_sum256(acc, red);
-  if (threadIdx.x == 0) E_out[blockIdx.x] = (double)Eq * inv_scale;
+  group_masks(src, cnt, n, mask);
+  __syncthreads();
+  rescore_group<T>(Jm, hv, n, n_pad, mask, red);
+  if (threadIdx.x < cnt) E_out[g0 + threadIdx.x] = (double)red[threadIdx.x] * scale;
 }
+
+size_t rescore_smem(int n, int bytes_T) { return (size_t)9 * (kRG + 1) * bytes_T + (size_t)n * 2; }
 
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  if (P.mode != QIS_FP64 && !d.rounded)
-    k_rescore_q<<<count, 256, 0, s>>>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, d.inv_scale, bits, Wn, E_out);
-  else
-    k_rescore<<<count, 256, 0, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, bits, Wn, E_out);
+  const int grid = (count + kRG - 1) / kRG;
+  const size_t sm = rescore_smem(d.n, 8);
+  if (P.mode != QIS_FP64 && !d.rounded) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_rescore<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_rescore<long long><<<grid, 256, sm, s>>>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, d.inv_scale, bits, Wn,
+                                               count, E_out);
+  } else {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_rescore<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_rescore<double><<<grid, 256, sm, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, 1.0, bits, Wn, count,
+                                            E_out);
+  }
   return cudaGetLastError();
 }
 
@@ -411,55 +436,79 @@ cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, 
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- every instance's merged list
-// Block (inst, r) for r < min(k, count of inst): state r of the merged list, its bits into
-// out[inst][r][Wmax] and its energy rescored as above (exact integers for instances on their
-// grid in the split modes, FP64 otherwise) into E[inst][r].
-__global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, uint64_t* out, double* E) {
-  const int inst = blockIdx.x / k, r = blockIdx.x % k;
-  if (r >= P.mrg_count[inst]) return;
+// ---------------------------------------------------------------- initial energies
+// E(psi0) 2^q of the initial states of instances inst0, inst0 + 1, ... in the split modes
+// (exact int64, Eq. 1), kRG states of one instance per block, into init_q / init_E; the search
+// initialisation then takes them as cached values.
+__global__ void __launch_bounds__(256) k_init_energy(DevPtrs P, int inst0, int ng) {
+  const int inst = inst0 + blockIdx.x / ng, g0 = (blockIdx.x % ng) * kRG;
+  const int cnt = min(kRG, P.R - g0);
   const InstDesc d = P.inst[inst];
-  const int ref = P.mrg_ref[inst * P.K1 + r];
-  const int b = ref / P.K1, slot = ref % P.K1;
-  __shared__ uint64_t sb[kMaxN / 64];
-  __shared__ double redd[256];
-  __shared__ long long redq[256];
-  const long long o = ((long long)inst * k + r) * P.Wmax;
-  for (int w = threadIdx.x; w < P.Wmax; w += blockDim.x) {
-    const uint64_t v = (w < d.W) ? P.lst_bits[((long long)b * P.K1 + slot) * P.Wmax + w] : 0ull;
-    sb[w] = v;
-    out[o + w] = v;
+  extern __shared__ __align__(16) unsigned char rsm[];
+  long long* red = reinterpret_cast<long long*>(rsm);
+  uint16_t* mask = reinterpret_cast<uint16_t*>(red + 9 * (kRG + 1));
+  __shared__ const uint64_t* src[kRG];
+  const long long b0 = (long long)d.first_search + g0;
+  if (threadIdx.x < kRG) src[threadIdx.x] = P.init_bits + (b0 + min((int)threadIdx.x, cnt - 1)) * P.Wmax;
+  __syncthreads();
+  group_masks(src, cnt, d.n, mask);
+  __syncthreads();
+  rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, red);
+  if (threadIdx.x < cnt) {
+    P.init_q[b0 + threadIdx.x] = red[threadIdx.x];
+    P.init_E[b0 + threadIdx.x] = ldexp((double)red[threadIdx.x], -d.q);
+  }
+}
+
+cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, cudaStream_t s) {
+  if (n_inst <= 0) return cudaSuccess;
+  const int ng = (P.R + kRG - 1) / kRG;
+  const size_t sm = rescore_smem(P.NP, 8);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_init_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_init_energy<<<n_inst * ng, 256, sm, s>>>(P, inst0, ng);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- every instance's merged list
+// Block (inst, group) for the states group * kRG ... of the first min(k, count of inst) of the
+// merged list: their bits into out[inst][r][Wmax] and their energies, rescored as above, into
+// E[inst][r].
+__global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, uint64_t* out, double* E) {
+  const int ng = (k + kRG - 1) / kRG;
+  const int inst = blockIdx.x / ng, g0 = (blockIdx.x % ng) * kRG;
+  const int cnt = min(kRG, min(k, P.mrg_count[inst]) - g0);
+  if (cnt <= 0) return;
+  const InstDesc d = P.inst[inst];
+  extern __shared__ __align__(16) unsigned char rsm[];
+  long long* redq = reinterpret_cast<long long*>(rsm);
+  double* redd = reinterpret_cast<double*>(rsm);
+  uint16_t* mask = reinterpret_cast<uint16_t*>(redq + 9 * (kRG + 1));
+  __shared__ const uint64_t* src[kRG];
+  if (threadIdx.x < kRG) {
+    const int ref = P.mrg_ref[inst * P.K1 + g0 + min((int)threadIdx.x, cnt - 1)];
+    src[threadIdx.x] = P.lst_bits + (long long)ref * P.Wmax;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = d.n;
+  for (int x = threadIdx.x; x < cnt * P.Wmax; x += blockDim.x) {
+    const int g = x / P.Wmax, w = x - g * P.Wmax;
+    out[((long long)inst * k + g0 + g) * P.Wmax + w] = (w < d.W) ? src[g][w] : 0ull;
+  }
+  group_masks(src, cnt, d.n, mask);
+  __syncthreads();
   if (P.mode != QIS_FP64 && !d.rounded) {
-    long long acc = 0;
-    for (int i = warp; i < n; i += 8) {
-      const long long* row = P.Jq + d.off_mat + (long long)i * d.n_pad;
-      long long rr = (lane == 0) ? P.hq[d.off_vec + i] : 0;
-#pragma unroll 4
-      for (int j = i + 1 + lane; j < n; j += 32) rr += sigma_of(sb, j) ? -row[j] : row[j];
-      acc += sigma_of(sb, i) ? -rr : rr;
-    }
-    const long long Eq = block_sum256(acc, redq);
-    if (threadIdx.x == 0) E[(long long)inst * k + r] = (double)Eq * d.inv_scale;
+    rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, redq);
+    if (threadIdx.x < cnt) E[(long long)inst * k + g0 + threadIdx.x] = (double)redq[threadIdx.x] * d.inv_scale;
   } else {
-    double acc = 0.0;
-    for (int i = warp; i < n; i += 8) {
-      const double* row = P.J64 + d.off_mat + (long long)i * d.n_pad;
-      double rr = (lane == 0) ? P.h64[d.off_vec + i] : 0.0;
-#pragma unroll 4
-      for (int j = i + 1 + lane; j < n; j += 32) rr += sigma_of(sb, j) ? -row[j] : row[j];
-      acc += sigma_of(sb, i) ? -rr : rr;
-    }
-    const double Ev = block_sum256(acc, redd);
-    if (threadIdx.x == 0) E[(long long)inst * k + r] = Ev;
+    rescore_group<double>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, mask, redd);
+    if (threadIdx.x < cnt) E[(long long)inst * k + g0 + threadIdx.x] = redd[threadIdx.x];
   }
 }
 
 cudaError_t launch_topk_all(const DevPtrs& P, int k, uint64_t* out, double* E, cudaStream_t s) {
   if (k <= 0 || P.n_inst <= 0) return cudaSuccess;
-  k_topk_all<<<P.n_inst * k, 256, 0, s>>>(P, k, out, E);
+  const size_t sm = rescore_smem(P.NP, 8);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_topk_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_topk_all<<<P.n_inst * ((k + kRG - 1) / kRG), 256, sm, s>>>(P, k, out, E);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,60 @@ def test_batch_equals_one_by_one(prec, ens):
         assert np.array_equal(got["bits"], ref["bits"][: ref["count"]])
 
 
+def _pinned(a):
+    """A page-locked host copy of a (numpy view of a pinned torch tensor)."""
+    import torch
+    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+    out = t.numpy()
+    out[...] = a
+    return out, t
+
+
+@pytest.mark.parametrize("prec,ens", [("split_bf16", "gaussian"), ("pm1_fp8", "pm1")])
+def test_page_locked_inputs_equal_pageable(prec, ens):
+    """A page-locked J is read by the layout kernel directly (no staging copy): a batch mixing
+    page-locked and pageable couplings gives the same instances and searches as pageable ones;
+    an invalid page-locked J is rejected the same way."""
+    ns, K, R, iters = [90, 150, 64], 16, 4, 12
+    data = [I.instance(ens, n, seed=405, inst=k) for k, n in enumerate(ns)]
+    phis = [I.random_states(n, R, seed=406, inst=k) for k, n in enumerate(ns)]
+    keep = []
+    mixed = []
+    for k, (J, h) in enumerate(data):
+        if k != 1:
+            Jp, t = _pinned(J)
+            keep.append(t)
+            mixed.append((Jp, h))
+        else:
+            mixed.append((J, h))
+    out = []
+    for batch in (data, mixed):
+        ctx = qis.Context(K=K, R=R, precision=prec, max_n=max(ns), max_instances=len(ns))
+        ids = ctx.create_instances(batch)
+        infos = [ctx.instance_info(k) for k in ids]
+        for k in ids:
+            ctx.init_states(k, phis[k])
+        ctx.iterate(iters)
+        lists = [[ctx.search_list(k, r) for r in range(R)] for k in ids]
+        out.append((infos, lists, ctx.topk_states_all(K + 1)))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    for k in range(len(ns)):
+        for r in range(R):
+            for key in ("count", "bits", "E", "stamp"):
+                assert np.array_equal(out[0][1][k][r][key], out[1][1][k][r][key]), (k, r, key)
+        for key in ("count", "bits", "E", "src"):
+            assert np.array_equal(out[0][2][k][key], out[1][2][k][key]), (k, key)
+    J, h = data[0]
+    Jbad, t = _pinned(J)
+    Jbad[2, 7] += 1.0   # no longer symmetric
+    ctx = qis.Context(K=K, R=R, precision=prec, max_n=max(ns), max_instances=2)
+    with pytest.raises(qis.QISError) as e:
+        ctx.create_instances([(Jbad, h)])
+    assert e.value.name == "INVALID_ARG"
+    ctx.close()
+
+
 def test_invalid_member_adds_nothing():
     ctx = qis.Context(K=8, R=2, precision="split_bf16", max_n=40, max_instances=4)
     good = I.instance("gaussian", 30, seed=410)
