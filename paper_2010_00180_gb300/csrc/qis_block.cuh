@@ -73,33 +73,25 @@ static __device__ float value_select_upper(const float* v, int cnt, int rank, in
 }
 
 // Candidate index of the kept state x if it is one or two flips from the parent p (the single
-// flip of its differing site, or the pair of its two), else -1. One pass over the W words: the
-// parent's from shared memory, the state's loaded in batches of ten (one round trip for
-// n <= 640).
+// flip of its differing site, or the pair of its two), else -1. The words are compared in
+// order and the test stops at the third differing bit: most kept states differ in more sites,
+// so most tests read only their first words (a rolled loop: a small body fetches better than
+// all the words' loads in flight).
 static __device__ __forceinline__ long long near_code_sp(const uint64_t* x, const uint64_t* p, int W, int n) {
-  int dist = 0, p0 = 0, p1 = 0;
-  for (int w0 = 0; w0 < W; w0 += 10) {
-    uint64_t xw[10];
-#pragma unroll
-    for (int u = 0; u < 10; ++u) xw[u] = (w0 + u < W) ? x[w0 + u] : 0ull;
-#pragma unroll
-    for (int u = 0; u < 10; ++u) {
-      uint64_t v = (w0 + u < W) ? (xw[u] ^ p[w0 + u]) : 0ull;
-      if (v && dist < 2) {
-        const int lo = (w0 + u) * 64 + __ffsll((long long)v) - 1;
-        if (dist == 0) {
-          p0 = lo;
-          const uint64_t r = v & (v - 1);
-          if (r) p1 = (w0 + u) * 64 + __ffsll((long long)r) - 1;
-        } else {
-          p1 = lo;
-        }
-      }
-      dist += __popcll(v);
+  int dist = 0, q0 = 0, q1 = 0;
+#pragma unroll 1
+  for (int w = 0; w < W; ++w) {
+    uint64_t v = x[w] ^ p[w];
+    while (v) {
+      const int pos = w * 64 + __ffsll((long long)v) - 1;
+      if (dist == 0) q0 = pos; else q1 = pos;
+      ++dist;
+      v &= v - 1;
+      if (dist > 2) return -1;
     }
   }
-  if (dist == 1) return p0;
-  if (dist == 2) return pair_index(n, p0, p1);
+  if (dist == 1) return q0;
+  if (dist == 2) return pair_index(n, q0, q1);
   return -1;
 }
 

@@ -12,8 +12,9 @@
 //   bound   filter threshold (the last kept energy and an order-statistic bound), the kept
 //           states one or two flips from the parent (the only possible duplicates), singles
 //   scan    pair flips dE_ij = a_i + a_j + 4 s_i s_j J_ij decided by the output-sensitive scan
-//   merge   exact integer keys of the survivors, duplicates dropped, first K+1 of the old
-//           list and the new states by (E, stamp)
+//   merge   exact integer keys of the survivors, duplicates dropped, the new states ranked by
+//           a counting sort over buckets of their keys (no sort), first K+1 of the old list and
+//           the new states by (E, stamp)
 // The kept list's order, keys, stamps and used flags, the parent's spins and {a_i, s_i} stay in
 // shared memory across the iterations; the kept states' bits, the aq ring and the survivor
 // buffer are in global memory (written and read by this block only, within the L2 cache).
@@ -40,6 +41,7 @@ struct SearchLayout {
 };
 
 constexpr int kSSV = 512;   // survivors held in shared memory (more go to the global buffer)
+constexpr int kMBits = 7, kMB = 1 << kMBits;   // buckets of the merge's new keys
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
 
@@ -65,49 +67,12 @@ __host__ __device__ inline SearchLayout search_layout(int NP, int Wmax, int K1, 
   // scratch: the phases' working arrays, one phase at a time
   const int bound = 4 * 256 * 4 + kSubSites * 4;
   const int scan = 3 * NP * 4 + (2 * kSparseNB + 1) * 4;
-  const int merge = search_pcs(cap, merge_cand) * 16 + 2 * 256 * 8 + 256 * 4;
+  const int merge = search_pcs(cap, merge_cand) * 16 + (512 + kMB + kSW * (kMB + 4)) * 4;
   int sc = bound > scan ? bound : scan;
   sc = sc > merge ? sc : merge;
   L.scratch = take(sc);
   L.total = align_up(o, 16);
   return L;
-}
-
-// Packed keys (key - kmin) << cb | c of nv <= 2 * blockDim.x candidates in ascending order:
-// runs of 32 sorted by warps (warp w takes runs w, w + warps, ...), then each key's place = its
-// index in its run + the count of smaller keys in every other run. tmp holds the runs
-// (ceil(nv / 32) * 32 entries), out receives the nv sorted keys.
-static __device__ void sort_packed_runs(const unsigned long long* key, const unsigned long long* ent, int nv,
-                                        unsigned long long kmin, int cb, unsigned long long* tmp,
-                                        unsigned long long* out) {
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nr = (nv + 31) >> 5;
-  for (int run = threadIdx.x >> 5; run < nr; run += nw) {
-    const int e = run * 32 + lane;
-    unsigned long long k = ~0ull;
-    if (e < nv) k = ((key[e] - kmin) << cb) | (uint32_t)ent[e];
-    warp_sort32_key(k);
-    tmp[e] = k;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nr * 32; e += blockDim.x) {
-    const unsigned long long k = tmp[e];
-    if (k == ~0ull) continue;   // padding (a packed key is never all ones)
-    const int run = e >> 5;
-    int pos = e & 31;
-    for (int v = 0; v < nr; ++v) {
-      if (v == run) continue;
-      const unsigned long long* rk = tmp + 32 * v;
-      int lo = 0, hi = 32;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (rk[mid] < k) lo = mid + 1; else hi = mid;
-      }
-      pos += lo;
-    }
-    out[pos] = k;
-  }
-  __syncthreads();
 }
 
 // Orderable unsigned key of a float (ascending floats -> ascending keys) and its inverse.
@@ -141,7 +106,7 @@ static __device__ __noinline__ void fields_full(const DevPtrs& P, const InstDesc
   }
 }
 
-// More kept candidates than the packed sort takes at once (rare): keep the K+1 lowest keys
+// More kept candidates than the bucket ranking takes at once (rare): keep the K+1 lowest keys
 // (ties included), compacted in place; returns their number. Out of line.
 static __device__ __noinline__ int keep_lowest(unsigned long long* sk, unsigned long long* se, int nv, int K1,
                                                int* rhist, int* wsum) {
@@ -168,8 +133,8 @@ static __device__ __noinline__ int keep_lowest(unsigned long long* sk, unsigned 
   return kept;
 }
 
-// (key, entry) sort of nv candidates in place, any size (rare: keys spanning more than the
-// packed form holds). Out of line.
+// (key, entry) sort of nv candidates in place, any size (rare: more than the bucket ranking
+// takes after keep_lowest, i.e. many equal keys). Out of line.
 static __device__ __noinline__ void sort_pairs_any(unsigned long long* sk, unsigned long long* se, int nv) {
   const int m2 = next_pow2(nv);
   for (int x = nv + threadIdx.x; x < m2; x += blockDim.x) {
@@ -300,7 +265,8 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
         const long long* __restrict__ ag = aq_of(P, b, tg);
         const long long* __restrict__ Ji = Jq + (long long)i * d.n_pad;   // row i = column i
         const long long* __restrict__ Jj = Jq + (long long)max(j, 0) * d.n_pad;
-        constexpr int U = 4;   // sites per thread and pass, their loads issued together
+        constexpr int U = 2;   // sites per thread and pass, their loads issued together (more
+                               // unrolling costs more in instruction fetch than it saves)
         for (int k0 = 0; k0 < n; k0 += U * kSNT) {
           long long vg[U], vi[U], vj[U];
 #pragma unroll
@@ -671,50 +637,38 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
         int tot = 0;
 #pragma unroll
         for (int w = 0; w < kSW; ++w) tot += s_w[w];
-        constexpr int PB = 4;
-        for (int u0 = 0; u0 < tot; u0 += PB * kSNT) {
-          float cv[PB], av[PB], pv[PB], jv[PB];
-          int ij[PB];
-          bool ok[PB];
-#pragma unroll
-          for (int u = 0; u < PB; ++u) {
-            const int e = u0 + u * kSNT + tid;
-            ok[u] = false;
-            if (e < tot) {
-              int lo = 0, hi = nl;
-              while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pc[mid] <= e) lo = mid; else hi = mid;
-              }
-              const int i = li[lo];
-              const float2 vi = as[i];
-              const int ci = __float_as_int(vi.y);
-              const int j = cj[(ci >> 1) + 1 + e - pc[lo]];
-              const float2 vj = as[j];
-              ij[u] = min(i, j) | (max(i, j) << 16);
-              cv[u] = __fsub_rn(thr, vi.x);
-              av[u] = vj.x;
-              pv[u] = ((ci ^ __float_as_int(vj.y)) & 1) ? -1.f : 1.f;
-              ok[u] = !EX || pv[u] < 0.f;
-              if (ok[u]) jv[u] = J4[(long long)i * d.n_pad + j];
+        // one pair per thread and pass (no batching: the kernel is bound by instruction issue
+        // and fetch, and a smaller loop body fetches better than more loads in flight)
+        for (int u0 = 0; u0 < tot; u0 += kSNT) {
+          const int e = u0 + tid;
+          bool hit = false;
+          int ij = 0;
+          if (e < tot) {
+            int lo = 0, hi = nl;
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (pc[mid] <= e) lo = mid; else hi = mid;
+            }
+            const int i = li[lo];
+            const float2 vi = as[i];
+            const int ci = __float_as_int(vi.y);
+            const int j = cj[(ci >> 1) + 1 + e - pc[lo]];
+            const float2 vj = as[j];
+            ij = min(i, j) | (max(i, j) << 16);
+            const float pv = ((ci ^ __float_as_int(vj.y)) & 1) ? -1.f : 1.f;
+            if (!EX || pv < 0.f) {
+              ++nev;
+              hit = fmaf(pv, J4[(long long)i * d.n_pad + j], vj.x) <= __fsub_rn(thr, vi.x);
             }
           }
-#pragma unroll
-          for (int u = 0; u < PB; ++u) {
-            bool hit = false;
-            if (ok[u]) {
-              ++nev;
-              hit = fmaf(pv[u], jv[u], av[u]) <= cv[u];
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-              const int leader = __ffs(m) - 1;
-              int sb = 0;
-              if (lane == leader) sb = atomicAdd(&s_ns, __popc(m));
-              sb = __shfl_sync(0xffffffffu, sb, leader);
-              const int slot = sb + __popc(m & ((1u << lane) - 1u));
-              if (hit) put_surv(slot, surv_entry(ij[u] & 0xffff, ij[u] >> 16));
-            }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (m) {
+            const int leader = __ffs(m) - 1;
+            int sb = 0;
+            if (lane == leader) sb = atomicAdd(&s_ns, __popc(m));
+            sb = __shfl_sync(0xffffffffu, sb, leader);
+            const int slot = sb + __popc(m & ((1u << lane) - 1u));
+            if (hit) put_surv(slot, surv_entry(ij & 0xffff, ij >> 16));
           }
         }
       }
@@ -723,10 +677,13 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
     unsigned long long* sk = reinterpret_cast<unsigned long long*>(scr);
     const int PCs = search_pcs(cap, P.merge_cand);
     unsigned long long* se = sk + PCs;
-    unsigned long long* so = se + PCs;              // [256] sorted packed keys
-    unsigned long long* st = so + 256;              // [256] sorted runs
-    int* rhist = reinterpret_cast<int*>(st + 256);            // [256]
+    // after the keys: mem [256] candidates by bucket, rank [256], bucket sizes [kMB], every
+    // warp's bucket starts [kSW][kMB + 4]; keep_lowest's histogram overlaps the starts only
+    int* mem = reinterpret_cast<int*>(se + PCs);
+    int* bcnt = mem + 512;
+    int* rhist = bcnt + 2 * kMB;                     // [256] (keep_lowest, before the buckets)
     __syncthreads();   // every survivor written; the scan's scratch is free
+    for (int x = tid; x < kMB; x += kSNT) bcnt[x] = 0;
     const int S = s_ns;
     if (S > cap) {   // block-uniform: the buffer held only the first cap survivors
       if (tid == 0) atomicOr(P.status, kStatCapacity);
@@ -794,28 +751,78 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
     }
     __syncthreads();
     int nv = s_nv;
-    // more kept candidates than the sort takes at once: only the K+1 lowest can enter the list
+    // more kept candidates than the buckets take at once: only the K+1 lowest can enter the list
     if (nv > 256 && nv > K1) nv = keep_lowest(sk, se, nv, K1, rhist, s_w);
-    const unsigned long long kmin = s_kmin;
-    const uint32_t n_cand = (uint32_t)n + (uint32_t)((long long)n * (n - 1) / 2);
-    const int cb = 32 - __clz((int)n_cand);
-    const bool packed = nv > 1 && nv <= 256 && ((s_kmax - kmin) >> (64 - cb)) == 0;
-    const unsigned long long* nk = sk;   // new keys in ascending (E, c) order
-    if (packed) {
-      sort_packed_runs(sk, se, nv, kmin, cb, st, so);
-      nk = so;
-    } else if (nv > 1) {
-      sort_pairs_any(sk, se, nv);
+    const unsigned long long kmin = s_kmin, kmax = s_kmax;
+    const bool bucketed = nv <= 256;   // block-uniform
+    int* rnk = mem + 256;              // [256] place of each new candidate among the new ones
+    int* bst = bcnt + kMB + warp * (kMB + 4);   // this warp's bucket starts [kMB + 1]
+    const int sh = max(0, 64 - __clzll((long long)(kmax - kmin)) - kMBits);
+    if (bucketed) {
+      // the new candidates' order (E, c) without sorting them: a counting sort by the top bits
+      // of E - Emin into kMB buckets (monotone in E), then a count within the bucket
+      int wb0 = 0, wb1 = 0;
+      if (tid < nv) wb0 = atomicAdd(&bcnt[(int)((sk[tid] - kmin) >> sh)], 1);
+      if (tid + kSNT < nv) wb1 = atomicAdd(&bcnt[(int)((sk[tid + kSNT] - kmin) >> sh)], 1);
+      __syncthreads();
+      {   // every warp forms the bucket starts itself (no barrier)
+        int x[kMB / 32], sum = 0;
+#pragma unroll
+        for (int q = 0; q < kMB / 32; ++q) {
+          x[q] = bcnt[lane * (kMB / 32) + q];
+          sum += x[q];
+        }
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        int acc = inc - sum;
+#pragma unroll
+        for (int q = 0; q < kMB / 32; ++q) {
+          bst[lane * (kMB / 32) + q] = acc;
+          acc += x[q];
+        }
+        if (lane == 31) bst[kMB] = acc;
+        __syncwarp();
+      }
+      if (tid < nv) mem[bst[(int)((sk[tid] - kmin) >> sh)] + wb0] = tid;
+      if (tid + kSNT < nv) mem[bst[(int)((sk[tid + kSNT] - kmin) >> sh)] + wb1] = tid + kSNT;
+      __syncthreads();
+      for (int p = tid; p < nv; p += kSNT) {
+        const unsigned long long kp = sk[p], ep = se[p];
+        const int bk = (int)((kp - kmin) >> sh);
+        int r = bst[bk];
+        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) {
+          const int m = mem[q];
+          r += kc_less(sk[m], se[m], kp, ep) ? 1 : 0;
+        }
+        rnk[p] = r;
+      }
+    } else {
+      sort_pairs_any(sk, se, nv);   // rare: sorted in place, the place of p is p
+      for (int p = tid; p < nv; p += kSNT) rnk[p] = p;
     }
-    __syncthreads();
-    const unsigned long long cmask = (1ull << cb) - 1;
-    auto new_key = [&](int p) { return packed ? (nk[p] >> cb) + kmin : nk[p]; };
+    // old entries: their place plus the new candidates strictly below their key
     for (int o = tid; o < cnt; o += kSNT) {
       const unsigned long long ko = okey[o];
-      int lo = 0, hi = nv;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (new_key(mid) < ko) lo = mid + 1; else hi = mid;
+      int lo;
+      if (nv == 0 || ko <= kmin) {
+        lo = 0;
+      } else if (ko > kmax) {
+        lo = nv;
+      } else if (bucketed) {
+        const int bk = (int)((ko - kmin) >> sh);
+        lo = bst[bk];
+        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) lo += (sk[mem[q]] < ko) ? 1 : 0;
+      } else {
+        lo = 0;
+        int hi = nv;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sk[mid] < ko) lo = mid + 1; else hi = mid;
+        }
       }
       const int rank = o + lo;
       if (rank < K1) {
@@ -828,23 +835,18 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
     __syncthreads();
     const int ocut = s_ocut, n_ev = cnt - ocut;
     for (int p = tid; p < nv; p += kSNT) {
-      const unsigned long long kp = new_key(p);
+      const unsigned long long kp = sk[p];
       int lo = 0, hi = cnt;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (okey[mid] <= kp) lo = mid + 1; else hi = mid;
       }
-      const int rank = p + lo;
+      const int rn = rnk[p], rank = rn + lo;
       if (rank >= K1) continue;
-      const int slot = (p < n_ev) ? oslot[ocut + p] : cnt + (p - n_ev);
+      const int slot = (rn < n_ev) ? oslot[ocut + rn] : cnt + (rn - n_ev);
       uint32_t c;
       int i, j;
-      if (packed) {
-        c = (uint32_t)(nk[p] & cmask);
-        decode_candidate(n, c, i, j);
-      } else {
-        surv_decode(se[p], c, i, j);
-      }
+      surv_decode(se[p], c, i, j);
       uint64_t* dst = P.lst_bits + (base + slot) * Wm;
       for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
       const uint64_t stamp = ((uint64_t)t << 32) | c;
