@@ -38,6 +38,7 @@ __host__ __device__ inline int search_pcs(int cap, int merge_cand) {
 // Byte offsets of the dynamic shared memory of a search block.
 struct SearchLayout {
   int as, pb, okey0, okey1, ostamp, oslot0, oslot1, htab, ssv, oused, scratch, total;
+  int sc;   // bytes of the scratch region
 };
 
 constexpr int kSSV = 512;   // survivors held in shared memory (more go to the global buffer)
@@ -71,6 +72,7 @@ __host__ __device__ inline SearchLayout search_layout(int NP, int Wmax, int K1, 
   int sc = bound > scan ? bound : scan;
   sc = sc > merge ? sc : merge;
   L.scratch = take(sc);
+  L.sc = sc;
   L.total = align_up(o, 16);
   return L;
 }
@@ -429,56 +431,42 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       __syncthreads();
       const int mm = min(s_nsites, lim0), m2 = min(s_n2, t1);
       const int M = FL == QIS_FLIPS_SINGLE ? min(s_nsites, kSubMax) : EX ? mm * m2 : mm + mm * (mm - 1) / 2;
-      auto member = [&](int q, int& i, int& j) {
-        j = -1;
-        if (EX) {
-          i = sites[q / m2];
-          j = sites[lim0 + q % m2];
-        } else if (q < mm) {
-          i = sites[q];
-        } else {
-          const int r = q - mm;
-          const float qq = 2.f * mm - 1.f;
-          int x = (int)((qq - sqrtf(fmaxf(qq * qq - 8.f * (float)r, 0.f))) * 0.5f);
-          x = max(0, min(x, mm - 2));
-          while (x > 0 && x * mm - x * (x + 1) / 2 > r) --x;
-          while (x < mm - 2 && (x + 1) * mm - (x + 1) * (x + 2) / 2 <= r) ++x;
-          const int y = x + 1 + (r - (x * mm - x * (x + 1) / 2));
-          i = sites[x];
-          j = sites[y];
-        }
-        if (j >= 0 && i > j) {
+      auto member = [&](int q, int& i, int& j) {   // exchanges: (class 0 site, class 1 site)
+        i = sites[q / m2];
+        j = sites[lim0 + q % m2];
+        if (i > j) {
           const int tmp = i;
           i = j;
           j = tmp;
         }
       };
       if (M >= k && FL != QIS_FLIPS_SINGLE) {
-        for (int q0 = 0; q0 < M; q0 += 4 * kSNT) {
-          int mi[4], mj[4];
-          float j4v[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * kSNT + tid;
-            mi[u] = 0;
-            mj[u] = -1;
-            j4v[u] = 0.f;
-            if (q < M) {
-              member(q, mi[u], mj[u]);
-              if (mj[u] >= 0) j4v[u] = J4[(long long)mi[u] * d.n_pad + mj[u]];
+        if (!EX) {
+          // the subset's singles, then its pairs row by row: warp w takes the rows x = w, w + 4,
+          // ..., its lanes the partners y > x (no index decoding; a warp reads one row of 4J~)
+          for (int q = tid; q < mm; q += kSNT) put_value(as[sites[q]].x);
+          for (int x = warp; x < mm; x += kSW) {
+            const int sx = sites[x];
+            for (int y = x + 1 + lane; y < mm; y += 32) {
+              const int sy = sites[y];
+              const int i = min(sx, sy), j = max(sx, sy);
+              const float j4 = J4[(long long)i * d.n_pad + j];
+              const float2 vj = as[j];
+              put_value(as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x));
             }
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int q = q0 + u * kSNT + tid;
-            if (q >= M) break;
-            const int i = mi[u], j = mj[u];
-            float de = as[i].x;
-            if (j >= 0) {
-              const float2 vj = as[j];
-              de = as[i].x + fmaf((sigma_of(pb, i) ? -j4v[u] : j4v[u]), vj.y, vj.x);
+        } else {
+          for (int q0 = 0; q0 < M; q0 += kSNT) {   // exchanges: pair q of the cross product
+            const int q = q0 + tid;
+            int i = 0, j = -1;
+            float j4 = 0.f;
+            if (q < M) {
+              member(q, i, j);
+              j4 = J4[(long long)i * d.n_pad + j];
             }
-            put_value(de);
+            if (q >= M) continue;
+            const float2 vj = as[j];
+            put_value(as[i].x + fmaf((sigma_of(pb, i) ? -j4 : j4), vj.y, vj.x));
           }
         }
       }
@@ -510,8 +498,9 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       const float delta = __fmul_ru(big, 0x1p-21f);
       thr = fminf(__fadd_ru(tE, delta), __fadd_ru(Uf, 2.f * delta));
     }
-    // single flips: dE_i = a_i (not candidates under exchanges)
-    if (!EX) {
+    // single flips: dE_i = a_i (not candidates under exchanges; with pairs, tested in the
+    // live-row pass below)
+    if (FL == QIS_FLIPS_SINGLE) {
       for (int i = tid; i < n; i += kSNT) {
         if (as[i].x <= thr) {
           const int slot = atomicAdd(&s_ns, 1);
@@ -526,6 +515,9 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       int* cj = pc + NP;                       // [NP] columns in bucket order
       int* bs = cj + NP;                       // [kSparseNB + 1]
       int* bcur = bs + kSparseNB + 1;          // [kSparseNB]
+      // the row of each pair, while the pairs fit the rest of the scratch
+      unsigned short* rowof = reinterpret_cast<unsigned short*>(bcur + kSparseNB);
+      const int rcap = (L.sc - (3 * NP + 2 * kSparseNB + 1) * 4) / 2;
       const float* rm = P.rm4 + d.off_vec;
       __syncthreads();   // the bound's scratch is free
       for (int x = tid; x < kSparseNB; x += kSNT) bcur[x] = 0;
@@ -542,7 +534,9 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
         for (int u = 0; u < SB; ++u) {
           const int i = i0 + tid + u * kSNT;
           if (i < n) {
-            const float c = __fsub_rn(thr, as[i].x);
+            const float ai = as[i].x;
+            if (!EX && ai <= thr) put_surv(atomicAdd(&s_ns, 1), surv_entry(i, -1));
+            const float c = __fsub_rn(thr, ai);
             if (c >= __fsub_rd(amin, r[u])) {
               const int q = atomicAdd(&s_nl, 1);
               li[q] = i;
@@ -630,6 +624,7 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
           for (int q = q0; q < q1; ++q) {
             const int x = pc[q];
             pc[q] = acc;
+            for (int e = acc, e1 = min(acc + x, rcap); e < e1; ++e) rowof[e] = (unsigned short)q;
             acc += x;
           }
         }
@@ -637,6 +632,7 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
         int tot = 0;
 #pragma unroll
         for (int w = 0; w < kSW; ++w) tot += s_w[w];
+        const bool direct = tot <= rcap;   // every pair's row in rowof (block-uniform)
         // one pair per thread and pass (no batching: the kernel is bound by instruction issue
         // and fetch, and a smaller loop body fetches better than more loads in flight)
         for (int u0 = 0; u0 < tot; u0 += kSNT) {
@@ -644,10 +640,15 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
           bool hit = false;
           int ij = 0;
           if (e < tot) {
-            int lo = 0, hi = nl;
-            while (hi - lo > 1) {
-              const int mid = (lo + hi) >> 1;
-              if (pc[mid] <= e) lo = mid; else hi = mid;
+            int lo = 0;
+            if (direct) {
+              lo = rowof[e];
+            } else {
+              int hi = nl;
+              while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pc[mid] <= e) lo = mid; else hi = mid;
+              }
             }
             const int i = li[lo];
             const float2 vi = as[i];
