@@ -723,7 +723,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cores = os.cpu_count() or 1
     ens, n, n_inst, K, R, I_, prec, flips = workload_spec(args.workload)
-    metric = METRIC if args.workload == DEFAULT else f"{unit_of(flips)[:-2]} decided/s ({args.workload})"
+    metric = METRIC if args.workload == DEFAULT else f"{unit_of(flips)} ({args.workload})"
     unit = unit_of(flips)
     config = {"workload": args.workload, "ensemble": ens, "n": n, "instances_per_gpu": n_inst, "K": K,
               "kept": K + 1, "R": R, "iterations": I_, "precision": prec, "flips": flips,

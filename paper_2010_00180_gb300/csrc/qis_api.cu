@@ -46,10 +46,10 @@ struct qis_ctx {
   long long* hq = nullptr;
   uint64_t* zob = nullptr;
   double* stats = nullptr;
-  double* jstage = nullptr;
+  double* jstage = nullptr;   // [max_n * max_n] one instance's J as copied from the host (FP64 mode)
   LayoutItem* items_d = nullptr;   // [max_inst] staging places of a creation batch
   uint64_t* all_bits = nullptr;   // [max_inst][K1][Wmax] every instance's merged states
-  double* all_E = nullptr;        // [max_inst][K1]   // [max_n * max_n] one instance's J as copied from the host
+  double* all_E = nullptr;        // [max_inst][K1]
   int4* work = nullptr;    // FP64 scan: 64 x 64 tiles x groups of searches
   int n_work = 0;
   int4* tasks = nullptr;   // FP32 scan: warp tasks (instance, strip, first column, chunk width)
@@ -64,10 +64,10 @@ struct qis_ctx {
   double* scratch_E = nullptr;
   int scratch_states = 0;
   uint64_t launches = 0;
-  uint64_t cand_acc[2] = {0, 0};
+  uint64_t cand_acc[2] = {0, 0};  // candidates of instances removed by qis_clear_instances
   // tunables (results never depend on them): scan chunk width 32 * tune_nc columns, searches
   // per scan task (0 = all R of the instance), searches per GEMM tile (0 = automatic)
-  qis_tuning tune{8, 0, 0, 0};  // candidates of instances removed by qis_clear_instances
+  qis_tuning tune{8, 0, 0, 0};
   // kernel timing (qis_profile_*): per class, event pairs recorded since the last query
   bool profiling = false;
   bool use_graph = true;                    // QIS_NO_GRAPH=1 launches the kernels one by one
@@ -477,6 +477,14 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ctx->scratch_states = 4096;
     ALLOC(ctx->scratch_bits, (size_t)ctx->scratch_states * W);
     ALLOC(ctx->scratch_E, ctx->scratch_states);
+    {   // partial energy sums of the rescoring when a state group's rows are split over blocks
+      size_t m = std::max<size_t>((size_t)ctx->max_inst * K1, (size_t)B);
+      m = std::max<size_t>(m, (size_t)ctx->scratch_states);
+      ALLOC(P.rs_acc, 2 * m * 32);   // [state][row part][2], at most 32 parts
+      int sms = 0;
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->cfg.device));
+      P.sms = sms;
+    }
     // Zobrist keys of the sites (SplitMix64 stream with a fixed key)
     std::vector<uint64_t> z(kMaxN);
     for (int i = 0; i < kMaxN; ++i) z[i] = splitmix64(0x2F0A7B6C5D4E3F21ull, (uint64_t)i);
@@ -663,7 +671,11 @@ int flush_init(qis_ctx* ctx) {
     while (e < ni && ctx->init_pending[e]) ctx->init_pending[e++] = 0;
     // split modes: the initial energies of the range in groups of states per block first
     const bool grouped = ctx->mode != QIS_FP64;
-    if (grouped) LAUNCH(launch_init_energy(ctx->P, a, e - a, ctx->stream));
+    if (grouped) {
+      int max_n = 0;
+      for (int x = a; x < e; ++x) max_n = std::max(max_n, ctx->inst[x].n);
+      LAUNCH(launch_init_energy(ctx->P, a, e - a, max_n, ctx->stream));
+    }
     LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream, grouped));
     a = e;
   }
@@ -1385,7 +1397,15 @@ int qis_topk_states_all(qis_ctx* ctx, int k, uint64_t* bits_out, double* E_out, 
     ctx->counts_valid = false;
   }
   const int ni = (int)ctx->inst.size(), Wm = ctx->Wmax;
-  if (k > 0) LAUNCH(launch_topk_all(ctx->P, k, ctx->all_bits, ctx->all_E, s));
+  if (k > 0) {
+    bool exact = ctx->mode != QIS_FP64;
+    int max_n = 0;
+    for (const InstDesc& d : ctx->inst) {
+      exact = exact && !d.rounded;
+      max_n = std::max(max_n, d.n);
+    }
+    LAUNCH(launch_topk_all(ctx->P, k, exact, max_n, ctx->all_bits, ctx->all_E, s));
+  }
   int rc = sync_and_check(ctx);
   if (rc) return rc;
   ctx->mrg_counts.assign(ni, 0);

@@ -95,6 +95,37 @@ static __device__ __forceinline__ long long near_code_sp(const uint64_t* x, cons
   return -1;
 }
 
+// The same test for wide states (the per-kernel form, n above 1024): the words are loaded ten at
+// a time (one round trip per ten words) and the test stops after the batch that holds the third
+// differing bit.
+static __device__ __forceinline__ long long near_code_batched(const uint64_t* x, const uint64_t* p, int W, int n) {
+  int dist = 0, p0 = 0, p1 = 0;
+  for (int w0 = 0; w0 < W; w0 += 10) {
+    uint64_t xw[10];
+#pragma unroll
+    for (int u = 0; u < 10; ++u) xw[u] = (w0 + u < W) ? x[w0 + u] : 0ull;
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      uint64_t v = (w0 + u < W) ? (xw[u] ^ p[w0 + u]) : 0ull;
+      if (v && dist < 2) {
+        const int lo = (w0 + u) * 64 + __ffsll((long long)v) - 1;
+        if (dist == 0) {
+          p0 = lo;
+          const uint64_t r = v & (v - 1);
+          if (r) p1 = (w0 + u) * 64 + __ffsll((long long)r) - 1;
+        } else {
+          p1 = lo;
+        }
+      }
+      dist += __popcll(v);
+    }
+    if (dist > 2) return -1;
+  }
+  if (dist == 1) return p0;
+  if (dist == 2) return pair_index(n, p0, p1);
+  return -1;
+}
+
 constexpr uint32_t kNoCand = 0xffffffffu;   // empty slot of the duplicate table
 static __device__ inline uint32_t chash(uint32_t c) { return (c * 2654435761u) >> 7; }
 

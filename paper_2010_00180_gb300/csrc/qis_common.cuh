@@ -111,6 +111,10 @@ struct DevPtrs {
   int* mrg_ref;           // [inst][K1] search*K1 + slot
   uint64_t* mrg_src;      // [inst][K1]
   int* mrg_count;         // [inst]
+  // rescoring from scratch: partial sums (sum of J over differing spins, sum of all J; int64 or
+  // FP64) per output state and row part when the rows of a group of states are split over blocks
+  unsigned long long* rs_acc;   // [states][32][2]
+  int sms;                      // streaming multiprocessors of the device
 };
 
 __host__ __device__ inline int words_of(int n) { return (n + 63) >> 6; }
@@ -337,8 +341,9 @@ size_t merge_smem(int K1, int cap, int merge_cand);
 size_t final_merge_smem(int K1);
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s);
-cudaError_t launch_topk_all(const DevPtrs& P, int k, uint64_t* out, double* E, cudaStream_t s);
-cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, cudaStream_t s);
+cudaError_t launch_topk_all(const DevPtrs& P, int k, bool all_exact, int max_n, uint64_t* out, double* E,
+                            cudaStream_t s);
+cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, int max_n, cudaStream_t s);
 cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, int k, uint64_t* bits_out,
                                  cudaStream_t s);
 

@@ -314,23 +314,27 @@ cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s,
 // E = sum_{i<j} J_ij s_i s_j + sum_i h_i s_i (Eq. 1) of up to kRG states of one instance per
 // block of 256 threads. With x_ij = 1 where s_i != s_j (s = -1 where the bit is set),
 // s_i s_j = 1 - 2 x_ij and s_i = 1 - 2 sigma_i, so
-//   E = (sum_{i<j} J_ij + sum_i h_i) - 2 (sum_{i<j, x_ij = 1} J_ij + sum_{sigma_i = 1} h_i):
+//   E = Q - 2 P,  Q = sum_{i<j} J_ij + sum_i h_i,  P = sum_{i<j, x_ij = 1} J_ij + sum_{sigma_i = 1} h_i:
 // one pass over the upper triangle serves every state of the block. mask[j] holds the block's
 // spins of site j as bits; a coupling loaded once is added to the accumulator of every state
-// whose two spins differ. Warp w takes rows w, w + 8, ..., its lanes the columns j > i
-// (coalesced). T = long long: the exact fixed-point couplings Jq, hq of an instance on its grid
-// 2^-q (every summation order gives the same integer); T = double: the FP64 couplings, summed in
-// an order fixed by the block shape and not by the state's place in the group.
+// whose two spins differ. Warp w takes rows w, w + 8, ... of the block's row range, its lanes the
+// columns j > i (coalesced). T = long long: the exact fixed-point couplings Jq, hq of an instance
+// on its grid 2^-q (every summation order gives the same integer); T = double: the FP64
+// couplings, summed in an order fixed by the block shape and not by the state's place in the
+// group. When there are few groups (large n, few states), the rows are split over `parts`
+// blocks per group, whose partial sums a second kernel adds in part order (the FP64 form takes a
+// number of parts fixed by n alone, so every call forms a state's energy the same way).
 constexpr int kRG = 16;
 
+// Rows [i0, i1) of the upper triangle (and the h terms if with_h): red[g] = P_g, red[kRG] = Q.
 template <typename T>
-__device__ void rescore_group(const T* __restrict__ Jm, const T* __restrict__ hv, int n, int n_pad,
-                              const uint16_t* __restrict__ mask, T* red /* [9][kRG + 1] */) {
+__device__ void rescore_part(const T* __restrict__ Jm, const T* __restrict__ hv, int n, int n_pad, int i0, int i1,
+                             bool with_h, const uint16_t* __restrict__ mask, T* red /* [9][kRG + 1] */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T q = 0, p[kRG];
 #pragma unroll
   for (int g = 0; g < kRG; ++g) p[g] = 0;
-  for (int i = warp; i < n; i += 8) {
+  for (int i = i0 + warp; i < i1; i += 8) {
     const T* __restrict__ row = Jm + (long long)i * n_pad;
     const unsigned mi = mask[i];
 #pragma unroll 2
@@ -343,14 +347,15 @@ __device__ void rescore_group(const T* __restrict__ Jm, const T* __restrict__ hv
         if ((x >> g) & 1u) p[g] += v;
     }
   }
-  for (int i = threadIdx.x; i < n; i += 256) {
-    const T v = hv[i];
-    const unsigned m = mask[i];
-    q += v;
+  if (with_h)
+    for (int i = threadIdx.x; i < n; i += 256) {
+      const T v = hv[i];
+      const unsigned m = mask[i];
+      q += v;
 #pragma unroll
-    for (int g = 0; g < kRG; ++g)
-      if ((m >> g) & 1u) p[g] += v;
-  }
+      for (int g = 0; g < kRG; ++g)
+        if ((m >> g) & 1u) p[g] += v;
+    }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -369,8 +374,50 @@ __device__ void rescore_group(const T* __restrict__ Jm, const T* __restrict__ hv
     red[8 * (kRG + 1) + threadIdx.x] = t;
   }
   __syncthreads();
-  if (threadIdx.x < kRG) red[threadIdx.x] = red[8 * (kRG + 1) + kRG] - 2 * red[8 * (kRG + 1) + threadIdx.x];
-  __syncthreads();   // red[g] = the energy of state g (times 2^q for the exact form)
+  if (threadIdx.x <= kRG) red[threadIdx.x] = red[8 * (kRG + 1) + threadIdx.x];
+  __syncthreads();
+}
+
+// First row of part b of `parts` row ranges with about equal shares of the triangle (rows i..n-1
+// hold (n - i)^2 / 2 of its pairs): n - round(n sqrt(1 - b / parts)); part 0 starts at row 0.
+__device__ inline int part_row(int n, int b, int parts) {
+  if (b <= 0) return 0;
+  if (b >= parts) return n;
+  const int r = n - (int)lrintf((float)n * sqrtf(1.f - (float)b / (float)parts));
+  return min(max(r, 0), n);
+}
+
+constexpr int kRPmax = 32;   // row parts per group at most
+
+// Rows of part blockIdx.y of `parts`, then E of the group's states (one part), or their partial
+// sums (P, Q) into part[(g * PS + blockIdx.y) * 2 ...] for the states g = 0 .. cnt - 1 of the
+// group (several parts; PS >= parts, the stride of one state). Calls out(g, E) for g < cnt in the
+// first case.
+template <typename T, typename Out>
+__device__ void rescore_group(const T* Jm, const T* hv, int n, int n_pad, const uint16_t* mask, T* red, int cnt,
+                              int parts, T* part, int PS, Out out) {
+  const int b = blockIdx.y;
+  rescore_part<T>(Jm, hv, n, n_pad, part_row(n, b, parts), part_row(n, b + 1, parts), b == 0, mask, red);
+  if (threadIdx.x < cnt) {
+    if (parts == 1) {
+      out((int)threadIdx.x, red[kRG] - 2 * red[threadIdx.x]);
+    } else {
+      T* x = part + ((long long)threadIdx.x * PS + b) * 2;
+      x[0] = red[threadIdx.x];
+      x[1] = red[kRG];
+    }
+  }
+}
+
+// E = Q - 2 P of a state from its `parts` partial sums (stride 2 between parts), added in order.
+template <typename T>
+__device__ inline T rs_energy(const T* part, int parts) {
+  T p = 0, q = 0;
+  for (int b = 0; b < parts; ++b) {
+    p += part[2 * b];
+    q += part[2 * b + 1];
+  }
+  return q - 2 * p;
 }
 
 // The spin masks of cnt <= kRG states (their words at src[g], Wn words each) into mask[0..n).
@@ -382,11 +429,27 @@ __device__ void group_masks(const uint64_t* const* src, int cnt, int n, uint16_t
   }
 }
 
-// Energies of `count` states (Wn words each, consecutive) of one instance: block g0 / kRG takes
-// states g0 .. g0 + kRG - 1.
+// Row parts of the FP64 form: a number fixed by n alone, so that a state's energy is summed the
+// same way whichever call and group rescore it.
+__host__ __device__ inline int fp64_parts(int n) { return n / 512 < 1 ? 1 : (n / 512 > kRPmax ? kRPmax : n / 512); }
+
+// Row parts per group. Exact form: one unless the groups alone leave the SMs idle (any split
+// gives the same integers). FP64 form: fp64_parts(n).
+int rescore_parts(const DevPtrs& P, int groups, int n, bool exact) {
+  if (!exact) return fp64_parts(n);
+  if (groups <= 0) return 1;
+  const int target = 4 * (P.sms > 0 ? P.sms : 148);
+  int parts = (target + groups - 1) / groups;
+  parts = std::min(std::min(parts, kRPmax), std::max(1, n / 256));
+  return std::max(parts, 1);
+}
+
+// Energies of `count` states (Wn words each, consecutive) of one instance: block x takes
+// states kRG x ... kRG x + kRG - 1, block y its part of the rows.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rescore(const T* Jm, const T* hv, int n, int n_pad, double scale,
-                                                 const uint64_t* states, int Wn, int count, double* E_out) {
+                                                 const uint64_t* states, int Wn, int count, double* E_out,
+                                                 unsigned long long* acc) {
   extern __shared__ __align__(16) unsigned char rsm[];
   T* red = reinterpret_cast<T*>(rsm);
   uint16_t* mask = reinterpret_cast<uint16_t*>(red + 9 * (kRG + 1));
@@ -396,8 +459,14 @@ __global__ void __launch_bounds__(256) k_rescore(const T* Jm, const T* hv, int n
   __syncthreads();
   group_masks(src, cnt, n, mask);
   __syncthreads();
-  rescore_group<T>(Jm, hv, n, n_pad, mask, red);
-  if (threadIdx.x < cnt) E_out[g0 + threadIdx.x] = (double)red[threadIdx.x] * scale;
+  rescore_group<T>(Jm, hv, n, n_pad, mask, red, cnt, gridDim.y, reinterpret_cast<T*>(acc) + 2ll * g0 * gridDim.y,
+                   gridDim.y, [&](int g, T E) { E_out[g0 + g] = (double)E * scale; });
+}
+
+template <typename T>
+__global__ void k_rescore_finish(const unsigned long long* acc, int count, int parts, double scale, double* E_out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < count) E_out[s] = (double)rs_energy(reinterpret_cast<const T*>(acc) + 2ll * s * parts, parts) * scale;
 }
 
 size_t rescore_smem(int n, int bytes_T) { return (size_t)9 * (kRG + 1) * bytes_T + (size_t)n * 2; }
@@ -405,16 +474,21 @@ size_t rescore_smem(int n, int bytes_T) { return (size_t)9 * (kRG + 1) * bytes_T
 cudaError_t launch_rescore(const DevPtrs& P, const InstDesc& d, const uint64_t* bits, int count, int Wn,
                            double* E_out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const int grid = (count + kRG - 1) / kRG;
+  const int groups = (count + kRG - 1) / kRG;
   const size_t sm = rescore_smem(d.n, 8);
-  if (P.mode != QIS_FP64 && !d.rounded) {
+  const bool exact = P.mode != QIS_FP64 && !d.rounded;
+  const int parts = rescore_parts(P, groups, d.n, exact);
+  if (exact) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_rescore<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_rescore<long long><<<grid, 256, sm, s>>>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, d.inv_scale, bits, Wn,
-                                               count, E_out);
+    k_rescore<long long><<<dim3(groups, parts), 256, sm, s>>>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad,
+                                                              d.inv_scale, bits, Wn, count, E_out, P.rs_acc);
+    if (parts > 1)
+      k_rescore_finish<long long><<<(count + 255) / 256, 256, 0, s>>>(P.rs_acc, count, parts, d.inv_scale, E_out);
   } else {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_rescore<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_rescore<double><<<grid, 256, sm, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, 1.0, bits, Wn, count,
-                                            E_out);
+    k_rescore<double><<<dim3(groups, parts), 256, sm, s>>>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, 1.0,
+                                                           bits, Wn, count, E_out, P.rs_acc);
+    if (parts > 1) k_rescore_finish<double><<<(count + 255) / 256, 256, 0, s>>>(P.rs_acc, count, parts, 1.0, E_out);
   }
   return cudaGetLastError();
 }
@@ -438,8 +512,13 @@ cudaError_t launch_gather_merged(const DevPtrs& P, int inst, const InstDesc& d, 
 
 // ---------------------------------------------------------------- initial energies
 // E(psi0) 2^q of the initial states of instances inst0, inst0 + 1, ... in the split modes
-// (exact int64, Eq. 1), kRG states of one instance per block, into init_q / init_E; the search
-// initialisation then takes them as cached values.
+// (exact int64, Eq. 1), kRG states of one instance per block (row parts as above), into
+// init_q / init_E; the search initialisation then takes them as cached values.
+__device__ inline void init_energy_out(const DevPtrs& P, const InstDesc& d, long long b, long long Eq) {
+  P.init_q[b] = Eq;
+  P.init_E[b] = ldexp((double)Eq, -d.q);
+}
+
 __global__ void __launch_bounds__(256) k_init_energy(DevPtrs P, int inst0, int ng) {
   const int inst = inst0 + blockIdx.x / ng, g0 = (blockIdx.x % ng) * kRG;
   const int cnt = min(kRG, P.R - g0);
@@ -453,32 +532,45 @@ __global__ void __launch_bounds__(256) k_init_energy(DevPtrs P, int inst0, int n
   __syncthreads();
   group_masks(src, cnt, d.n, mask);
   __syncthreads();
-  rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, red);
-  if (threadIdx.x < cnt) {
-    P.init_q[b0 + threadIdx.x] = red[threadIdx.x];
-    P.init_E[b0 + threadIdx.x] = ldexp((double)red[threadIdx.x], -d.q);
-  }
+  rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, red, cnt, gridDim.y,
+                           reinterpret_cast<long long*>(P.rs_acc) + 2 * b0 * gridDim.y, gridDim.y,
+                           [&](int g, long long Eq) { init_energy_out(P, d, b0 + g, Eq); });
 }
 
-cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, cudaStream_t s) {
+__global__ void k_init_energy_finish(DevPtrs P, int b0, int nb, int parts) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nb) return;
+  const long long b = (long long)b0 + x;
+  init_energy_out(P, P.inst[b / P.R], b, rs_energy(reinterpret_cast<const long long*>(P.rs_acc) + 2 * b * parts, parts));
+}
+
+cudaError_t launch_init_energy(const DevPtrs& P, int inst0, int n_inst, int max_n, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
   const int ng = (P.R + kRG - 1) / kRG;
+  const int parts = rescore_parts(P, n_inst * ng, max_n, true);
+  const long long b0 = (long long)inst0 * P.R, nb = (long long)n_inst * P.R;
   const size_t sm = rescore_smem(P.NP, 8);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_init_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_init_energy<<<n_inst * ng, 256, sm, s>>>(P, inst0, ng);
+  k_init_energy<<<dim3(n_inst * ng, parts), 256, sm, s>>>(P, inst0, ng);
+  if (parts > 1) k_init_energy_finish<<<(int)((nb + 255) / 256), 256, 0, s>>>(P, (int)b0, (int)nb, parts);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- every instance's merged list
 // Block (inst, group) for the states group * kRG ... of the first min(k, count of inst) of the
 // merged list: their bits into out[inst][r][Wmax] and their energies, rescored as above, into
-// E[inst][r].
-__global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, uint64_t* out, double* E) {
+// E[inst][r]. The row parts: the exact form's when every instance is rescored exactly (split
+// modes, on the grid), else the FP64 form's.
+__global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, int all_exact, uint64_t* out, double* E) {
   const int ng = (k + kRG - 1) / kRG;
   const int inst = blockIdx.x / ng, g0 = (blockIdx.x % ng) * kRG;
   const int cnt = min(kRG, min(k, P.mrg_count[inst]) - g0);
   if (cnt <= 0) return;
   const InstDesc d = P.inst[inst];
+  const bool exact = P.mode != QIS_FP64 && !d.rounded;
+  // this instance's parts: the grid's when every instance is exact, else its FP64 number
+  const int parts = all_exact ? (int)gridDim.y : fp64_parts(d.n);
+  if ((int)blockIdx.y >= parts) return;
   extern __shared__ __align__(16) unsigned char rsm[];
   long long* redq = reinterpret_cast<long long*>(rsm);
   double* redd = reinterpret_cast<double*>(rsm);
@@ -489,26 +581,48 @@ __global__ void __launch_bounds__(256) k_topk_all(DevPtrs P, int k, uint64_t* ou
     src[threadIdx.x] = P.lst_bits + (long long)ref * P.Wmax;
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < cnt * P.Wmax; x += blockDim.x) {
-    const int g = x / P.Wmax, w = x - g * P.Wmax;
-    out[((long long)inst * k + g0 + g) * P.Wmax + w] = (w < d.W) ? src[g][w] : 0ull;
-  }
+  if (blockIdx.y == 0)
+    for (int x = threadIdx.x; x < cnt * P.Wmax; x += blockDim.x) {
+      const int g = x / P.Wmax, w = x - g * P.Wmax;
+      out[((long long)inst * k + g0 + g) * P.Wmax + w] = (w < d.W) ? src[g][w] : 0ull;
+    }
   group_masks(src, cnt, d.n, mask);
   __syncthreads();
-  if (P.mode != QIS_FP64 && !d.rounded) {
-    rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, redq);
-    if (threadIdx.x < cnt) E[(long long)inst * k + g0 + threadIdx.x] = (double)redq[threadIdx.x] * d.inv_scale;
-  } else {
-    rescore_group<double>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, mask, redd);
-    if (threadIdx.x < cnt) E[(long long)inst * k + g0 + threadIdx.x] = redd[threadIdx.x];
-  }
+  const long long o = (long long)inst * k + g0;
+  const int PS = gridDim.y;
+  if (exact)
+    rescore_group<long long>(P.Jq + d.off_mat, P.hq + d.off_vec, d.n, d.n_pad, mask, redq, cnt, parts,
+                             reinterpret_cast<long long*>(P.rs_acc) + 2 * o * PS, PS,
+                             [&](int g, long long Eq) { E[o + g] = (double)Eq * d.inv_scale; });
+  else
+    rescore_group<double>(P.J64 + d.off_mat, P.h64 + d.off_vec, d.n, d.n_pad, mask, redd, cnt, parts,
+                          reinterpret_cast<double*>(P.rs_acc) + 2 * o * PS, PS,
+                          [&](int g, double Ev) { E[o + g] = Ev; });
 }
 
-cudaError_t launch_topk_all(const DevPtrs& P, int k, uint64_t* out, double* E, cudaStream_t s) {
+__global__ void k_topk_all_finish(DevPtrs P, int k, int all_exact, int PS, double* E) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int inst = x / k, r = x - inst * k;
+  if (inst >= P.n_inst || r >= min(k, P.mrg_count[inst])) return;
+  const InstDesc d = P.inst[inst];
+  const int parts = all_exact ? PS : fp64_parts(d.n);
+  if (parts == 1) return;   // written by the rescoring block itself
+  if (P.mode != QIS_FP64 && !d.rounded)
+    E[x] = (double)rs_energy(reinterpret_cast<const long long*>(P.rs_acc) + 2ll * x * PS, parts) * d.inv_scale;
+  else
+    E[x] = rs_energy(reinterpret_cast<const double*>(P.rs_acc) + 2ll * x * PS, parts);
+}
+
+cudaError_t launch_topk_all(const DevPtrs& P, int k, bool all_exact, int max_n, uint64_t* out, double* E,
+                            cudaStream_t s) {
   if (k <= 0 || P.n_inst <= 0) return cudaSuccess;
+  const int groups = P.n_inst * ((k + kRG - 1) / kRG);
+  const int parts = rescore_parts(P, groups, max_n, all_exact);
+  const long long nstates = (long long)P.n_inst * k;
   const size_t sm = rescore_smem(P.NP, 8);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_topk_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_topk_all<<<P.n_inst * ((k + kRG - 1) / kRG), 256, sm, s>>>(P, k, out, E);
+  k_topk_all<<<dim3(groups, parts), 256, sm, s>>>(P, k, all_exact ? 1 : 0, out, E);
+  if (parts > 1) k_topk_all_finish<<<(int)((nstates + 255) / 256), 256, 0, s>>>(P, k, all_exact ? 1 : 0, parts, E);
   return cudaGetLastError();
 }
 

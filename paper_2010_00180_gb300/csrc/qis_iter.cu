@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(128, 10) k_bound(DevPtrs P) {
   // to dup_c for the merge's duplicate test; among the K+1+near lowest candidates at least
   // K+1 are new states.
   for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
-    const long long c = near_code_sp(P.lst_bits + (base + r) * P.Wmax, pb, d.W, n);
+    const long long c = near_code_batched(P.lst_bits + (base + r) * P.Wmax, pb, d.W, n);
     if (c >= 0) P.dup_c[base + atomicAdd(&s_near, 1)] = (uint32_t)c;
   }
   __syncthreads();
