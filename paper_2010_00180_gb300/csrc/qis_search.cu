@@ -262,40 +262,36 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       if (tg >= 1 && tg > ring_t0 && tg < t && t - tg < P.ring_n) {
         int i, j;
         decode_candidate(n, (uint32_t)pst, i, j);
-        const long long gi = sigma_of(pb, i) ? 2 : -2;   // 2 s_g at the flipped sites (s_g = -s_x)
-        const long long gj = (j >= 0) ? (sigma_of(pb, j) ? 2 : -2) : 0;
         const long long* __restrict__ ag = aq_of(P, b, tg);
         const long long* __restrict__ Ji = Jq + (long long)i * d.n_pad;   // row i = column i
         const long long* __restrict__ Jj = Jq + (long long)max(j, 0) * d.n_pad;
-        constexpr int U = 2;   // sites per thread and pass, their loads issued together (more
-                               // unrolling costs more in instruction fetch than it saves)
-        for (int k0 = 0; k0 < n; k0 += U * kSNT) {
-          long long vg[U], vi[U], vj[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * kSNT + tid;
-            vg[u] = vi[u] = vj[u] = 0;
-            if (k < n) {
-              vg[u] = ag[k];
-              vi[u] = Ji[k];
-              if (j >= 0) vj[u] = Jj[k];
-            }
+        // one site per thread and pass, pipelined: the next site's three loads are issued before
+        // the current site's fields are formed. With s_g = -s_x at the flipped sites i, j,
+        //   aq_x,k = s_x,k s_g,k aq_g,k + 4 s_x,k (s_g,i Jq_ik + s_g,j Jq_jk),
+        // s_g,i = +1 where the parent's bit i is set (exact int64)
+        const bool pi = sigma_of(pb, i) != 0;
+        const bool pj = j >= 0 && sigma_of(pb, j) != 0;
+        long long g_n = 0, i_n = 0, j_n = 0;
+        auto load = [&](int k) {
+          if (k < n) {
+            g_n = ag[k];
+            i_n = Ji[k];
+            if (j >= 0) j_n = Jj[k];
           }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int k = k0 + u * kSNT + tid;
-            if (k >= n) break;
-            const int sx = sigma_of(pb, k);
-            const int sg = sx ^ (k == i || k == j);
-            const long long fg = sg ? vg[u] / 2 : -(vg[u] / 2);   // aq = -2 s f, s = -1 where sigma = 1
-            const long long fx = fg - gi * vi[u] - gj * vj[u];
-            const long long aq = sx ? 2 * fx : -2 * fx;
-            const float a = __ll2float_rn(aq) * scale_q;
-            ax[k] = aq;
-            as[k] = make_float2(a, sx ? -1.f : 1.f);
-            mn = fminf(mn, a);
-            mx = fmaxf(mx, a);
-          }
+        };
+        load(tid);
+#pragma unroll 1
+        for (int k = tid; k < n; k += kSNT) {
+          const long long vg = g_n, vi = i_n, vj = j_n;
+          load(k + kSNT);
+          const int sx = sigma_of(pb, k);
+          const long long tt = (pi ? vi : -vi) + (j >= 0 ? (pj ? vj : -vj) : 0);
+          const long long aq = ((k == i || k == j) ? -vg : vg) + (sx ? -4 * tt : 4 * tt);
+          const float a = __ll2float_rn(aq) * scale_q;
+          ax[k] = aq;
+          as[k] = make_float2(a, sx ? -1.f : 1.f);
+          mn = fminf(mn, a);
+          mx = fmaxf(mx, a);
         }
       } else {
         fields_full(P, d, pb, ax, as, mn, mx);   // no stored generator
@@ -633,12 +629,13 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
 #pragma unroll
         for (int w = 0; w < kSW; ++w) tot += s_w[w];
         const bool direct = tot <= rcap;   // every pair's row in rowof (block-uniform)
-        // one pair per thread and pass (no batching: the kernel is bound by instruction issue
-        // and fetch, and a smaller loop body fetches better than more loads in flight)
-        for (int u0 = 0; u0 < tot; u0 += kSNT) {
-          const int e = u0 + tid;
-          bool hit = false;
-          int ij = 0;
+        // one pair per thread and pass, pipelined: the coupling load of the next pass's pair is
+        // issued before the current pair is tested
+        int ij_n = 0;
+        float cv_n = 0.f, av_n = 0.f, jv_n = 0.f;
+        bool ok_n = false, neg_n = false;
+        auto stage = [&](int e) {
+          ok_n = false;
           if (e < tot) {
             int lo = 0;
             if (direct) {
@@ -655,12 +652,24 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
             const int ci = __float_as_int(vi.y);
             const int j = cj[(ci >> 1) + 1 + e - pc[lo]];
             const float2 vj = as[j];
-            ij = min(i, j) | (max(i, j) << 16);
-            const float pv = ((ci ^ __float_as_int(vj.y)) & 1) ? -1.f : 1.f;
-            if (!EX || pv < 0.f) {
-              ++nev;
-              hit = fmaf(pv, J4[(long long)i * d.n_pad + j], vj.x) <= __fsub_rn(thr, vi.x);
-            }
+            ij_n = min(i, j) | (max(i, j) << 16);
+            neg_n = ((ci ^ __float_as_int(vj.y)) & 1) != 0;
+            cv_n = __fsub_rn(thr, vi.x);
+            av_n = vj.x;
+            ok_n = !EX || neg_n;
+            if (ok_n) jv_n = J4[(long long)i * d.n_pad + j];
+          }
+        };
+        stage(tid);
+        for (int u0 = 0; u0 < tot; u0 += kSNT) {
+          const int ij = ij_n;
+          const float cv = cv_n, av = av_n, jv = jv_n;
+          const bool ok = ok_n, neg = neg_n;
+          stage(u0 + kSNT + tid);
+          bool hit = false;
+          if (ok) {
+            ++nev;
+            hit = fmaf(neg ? -1.f : 1.f, jv, av) <= cv;
           }
           const unsigned m = __ballot_sync(0xffffffffu, hit);
           if (m) {
