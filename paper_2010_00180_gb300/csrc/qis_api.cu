@@ -58,6 +58,10 @@ struct qis_ctx {
   bool work_dirty = true;
   bool merged_fresh = false;
   std::vector<char> init_pending;  // instance whose searches wait for their start (one launch for all)
+  // initial states given by the host: held here until the searches start, then uploaded in one
+  // copy per run of consecutive instances (instead of one small copy per call)
+  std::vector<uint64_t> init_host;   // [max_inst * R][Wmax]
+  std::vector<char> init_from_host;  // instance whose initial states wait in init_host
   bool counts_valid = false;      // mrg_counts holds the counts of the current merge (status checked)
   std::vector<int> mrg_counts;
   uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
@@ -644,6 +648,7 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
     if (d.digits > ctx->digits_used) ctx->digits_used = d.digits;
     ctx->inst_ready.push_back(0);
     ctx->init_pending.push_back(0);
+    ctx->init_from_host.push_back(0);
   }
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
@@ -669,6 +674,20 @@ int flush_init(qis_ctx* ctx) {
     }
     int e = a;
     while (e < ni && ctx->init_pending[e]) ctx->init_pending[e++] = 0;
+    // the host-given initial states of the range: one copy per run of such instances
+    for (int x = a; x < e;) {
+      if (!ctx->init_from_host[x]) {
+        ++x;
+        continue;
+      }
+      int y = x;
+      while (y < e && ctx->init_from_host[y]) ctx->init_from_host[y++] = 0;
+      const size_t off = (size_t)ctx->inst[x].first_search * ctx->Wmax;
+      const size_t len = (size_t)(y - x) * ctx->R * ctx->Wmax;
+      CK(cudaMemcpyAsync(ctx->P.init_bits + off, ctx->init_host.data() + off, len * sizeof(uint64_t),
+                         cudaMemcpyHostToDevice, ctx->stream));
+      x = y;
+    }
     // split modes: the initial energies of the range in groups of states per block first
     const bool grouped = ctx->mode != QIS_FP64;
     if (grouped) {
@@ -785,6 +804,7 @@ int qis_clear_instances(qis_ctx* ctx) {
   ctx->inst.clear();
   ctx->inst_ready.clear();
   ctx->init_pending.clear();
+  ctx->init_from_host.clear();
   ctx->P.n_inst = 0;
   ctx->P.B = 0;
   ctx->work_dirty = true;
@@ -816,25 +836,25 @@ int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
   CK(cudaSetDevice(ctx->cfg.device));
   const InstDesc& d = ctx->inst[instance_id];
   const int R = ctx->R, W = d.W, Wm = ctx->Wmax;
-  std::vector<uint64_t> h((size_t)R * Wm, 0ull);
   const uint64_t top = (d.n % 64) ? ((1ull << (d.n % 64)) - 1) : ~0ull;
+  if (bits)   // checked before anything is written
+    for (int r = 0; r < R; ++r)
+      if (bits[(size_t)r * W + W - 1] & ~top) return fail(ctx, QIS_ERR_INVALID_ARG, "state bits above n must be zero");
+  if (ctx->init_host.size() < (size_t)ctx->max_inst * R * Wm) ctx->init_host.assign((size_t)ctx->max_inst * R * Wm, 0ull);
+  uint64_t* h = ctx->init_host.data() + (size_t)d.first_search * Wm;
+  std::fill(h, h + (size_t)R * Wm, 0ull);
   if (bits) {
     for (int r = 0; r < R; ++r)
-      for (int w = 0; w < W; ++w) {
-        const uint64_t v = bits[(size_t)r * W + w];
-        if (w == W - 1 && (v & ~top)) return fail(ctx, QIS_ERR_INVALID_ARG, "state bits above n must be zero");
-        h[(size_t)r * Wm + w] = v;
-      }
+      for (int w = 0; w < W; ++w) h[(size_t)r * Wm + w] = bits[(size_t)r * W + w];
   } else {
     const uint64_t key = state_key(ctx->cfg.seed, instance_id);
     for (int r = 0; r < R; ++r)
       for (int i = 0; i < d.n; ++i)
         if (splitmix64(key, (uint64_t)r * d.n + i) >> 63) h[(size_t)r * Wm + (i >> 6)] |= 1ull << (i & 63);
   }
-  CK(cudaMemcpyAsync(ctx->P.init_bits + (size_t)d.first_search * Wm, h.data(), h.size() * sizeof(uint64_t),
-                     cudaMemcpyHostToDevice, ctx->stream));
-  // the searches start at the next entry point that needs them (one launch for every instance
-  // set since); no synchronisation: a copy from pageable host memory has left `h` once it returns
+  // uploaded with the searches' start at the next entry point that needs them (one copy and one
+  // launch for every instance set since)
+  ctx->init_from_host[instance_id] = 1;
   ctx->init_pending[instance_id] = 1;
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
@@ -849,6 +869,7 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
   if (d.n > mlp_max_n(m)) return fail(ctx, QIS_ERR_INVALID_ARG, "instance larger than the network's max_n");
   CK(cudaSetDevice(ctx->cfg.device));
   const uint64_t key = splitmix64(state_key(ctx->cfg.seed, instance_id) ^ 5ull, 0);
+  ctx->init_from_host[instance_id] = 0;   // states written on the device replace any pending host ones
   CK(cudaMemsetAsync(ctx->P.init_bits + (size_t)d.first_search * ctx->Wmax, 0,
                      sizeof(uint64_t) * (size_t)ctx->R * ctx->Wmax, ctx->stream));
   CK(mlp_propose_states(m, ctx->J64 + d.off_mat, d.n_pad, ctx->h64 + d.off_vec, d.n, ctx->R, key,
