@@ -764,16 +764,26 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
     // more kept candidates than the buckets take at once: only the K+1 lowest can enter the list
     if (nv > 256 && nv > K1) nv = keep_lowest(sk, se, nv, K1, rhist, s_w);
     const unsigned long long kmin = s_kmin, kmax = s_kmax;
-    const bool bucketed = nv <= 256;   // block-uniform
+    // the new candidates' order (E, c) as one 64-bit value, (E - Emin) << cb | c, where the keys'
+    // span leaves room for c (always but for extreme ranges); equal energies are ordered by c
+    const uint32_t n_cand = (uint32_t)n + (uint32_t)((long long)n * (n - 1) / 2);
+    const int cb = 32 - __clz((int)n_cand);
+    const bool bucketed = nv <= 256 && ((kmax - kmin) >> (64 - cb)) == 0;   // block-uniform
     int* rnk = mem + 256;              // [256] place of each new candidate among the new ones
     int* bst = bcnt + kMB + warp * (kMB + 4);   // this warp's bucket starts [kMB + 1]
-    const int sh = max(0, 64 - __clzll((long long)(kmax - kmin)) - kMBits);
+    const int sh = max(0, 64 - __clzll((long long)(((kmax - kmin) << cb) | ((1ull << cb) - 1))) - kMBits);
     if (bucketed) {
-      // the new candidates' order (E, c) without sorting them: a counting sort by the top bits
-      // of E - Emin into kMB buckets (monotone in E), then a count within the bucket
+      // without sorting them: the order values packed in place, a counting sort by their top
+      // bits into kMB buckets, then a count within the bucket (the values are distinct)
       int wb0 = 0, wb1 = 0;
-      if (tid < nv) wb0 = atomicAdd(&bcnt[(int)((sk[tid] - kmin) >> sh)], 1);
-      if (tid + kSNT < nv) wb1 = atomicAdd(&bcnt[(int)((sk[tid + kSNT] - kmin) >> sh)], 1);
+      if (tid < nv) {
+        sk[tid] = ((sk[tid] - kmin) << cb) | (uint32_t)se[tid];
+        wb0 = atomicAdd(&bcnt[(int)(sk[tid] >> sh)], 1);
+      }
+      if (tid + kSNT < nv) {
+        sk[tid + kSNT] = ((sk[tid + kSNT] - kmin) << cb) | (uint32_t)se[tid + kSNT];
+        wb1 = atomicAdd(&bcnt[(int)(sk[tid + kSNT] >> sh)], 1);
+      }
       __syncthreads();
       {   // every warp forms the bucket starts itself (no barrier)
         int x[kMB / 32], sum = 0;
@@ -797,17 +807,14 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
         if (lane == 31) bst[kMB] = acc;
         __syncwarp();
       }
-      if (tid < nv) mem[bst[(int)((sk[tid] - kmin) >> sh)] + wb0] = tid;
-      if (tid + kSNT < nv) mem[bst[(int)((sk[tid + kSNT] - kmin) >> sh)] + wb1] = tid + kSNT;
+      if (tid < nv) mem[bst[(int)(sk[tid] >> sh)] + wb0] = tid;
+      if (tid + kSNT < nv) mem[bst[(int)(sk[tid + kSNT] >> sh)] + wb1] = tid + kSNT;
       __syncthreads();
       for (int p = tid; p < nv; p += kSNT) {
-        const unsigned long long kp = sk[p], ep = se[p];
-        const int bk = (int)((kp - kmin) >> sh);
+        const unsigned long long vp = sk[p];
+        const int bk = (int)(vp >> sh);
         int r = bst[bk];
-        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) {
-          const int m = mem[q];
-          r += kc_less(sk[m], se[m], kp, ep) ? 1 : 0;
-        }
+        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) r += (sk[mem[q]] < vp) ? 1 : 0;
         rnk[p] = r;
       }
     } else {
@@ -823,9 +830,10 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       } else if (ko > kmax) {
         lo = nv;
       } else if (bucketed) {
-        const int bk = (int)((ko - kmin) >> sh);
+        const unsigned long long vo = (ko - kmin) << cb;   // below every new value of energy ko
+        const int bk = (int)(vo >> sh);
         lo = bst[bk];
-        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) lo += (sk[mem[q]] < ko) ? 1 : 0;
+        for (int q = bst[bk], q1 = bst[bk + 1]; q < q1; ++q) lo += (sk[mem[q]] < vo) ? 1 : 0;
       } else {
         lo = 0;
         int hi = nv;
@@ -845,7 +853,7 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
     __syncthreads();
     const int ocut = s_ocut, n_ev = cnt - ocut;
     for (int p = tid; p < nv; p += kSNT) {
-      const unsigned long long kp = sk[p];
+      const unsigned long long kp = bucketed ? (sk[p] >> cb) + kmin : sk[p];
       int lo = 0, hi = cnt;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
