@@ -656,7 +656,7 @@ def roofline_search(res, pk, src):
     dur = ms / nl / 1e3
     achieved = bytes_per_launch / dur / 1e9
     peak = float(pk.get("hbm_gbs", 6800.0))
-    # SURVEY 8(d)'s ALU speed of light of the candidate decision: 3 instructions per candidate
+    # the ALU speed of light of the candidate decision: 3 instructions per candidate
     # on the FP32 lanes of every SM at the maximum clock; the output-sensitive scan decides the
     # logical pairs without evaluating each one
     clk = pk.get("sm_max_mhz", 2070.0)
