@@ -62,6 +62,15 @@ struct qis_ctx {
   // copy per run of consecutive instances (instead of one small copy per call)
   std::vector<uint64_t> init_host;   // [max_inst * R][Wmax]
   std::vector<char> init_from_host;  // instance whose initial states wait in init_host
+  // init_E / init_q hold the energies of the instance's current initial states (formed by
+  // k_init_energy or k_init_search; the fused search kernel's deferred values do not count here:
+  // a run that failed may have formed them from bad fields)
+  std::vector<char> e0_valid;
+  // instances whose searches were started with their initial energies left to the fused search
+  // kernel, and whether that kernel has not been enqueued yet (the call failed before it): such
+  // instances are started again, energies included, by the next entry point
+  std::vector<char> e0_deferred;
+  bool e0_unresolved = false;
   bool counts_valid = false;      // mrg_counts holds the counts of the current merge (status checked)
   std::vector<int> mrg_counts;
   uint64_t* scratch_bits = nullptr;  // [kScratch][Wmax]
@@ -470,6 +479,8 @@ int qis_create(const qis_config* cfg, qis_ctx** out) {
     ALLOC(P.init_bits, B * W);
     ALLOC(P.init_E, B);
     ALLOC(P.init_q, B);
+    ALLOC(P.e0_pend, B);
+    CK(cudaMemset(P.e0_pend, 0, sizeof(int) * B));
     ALLOC(P.status, 4);
     ALLOC(P.nprod, B);
     ALLOC(P.npair, B);
@@ -649,6 +660,8 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
     ctx->inst_ready.push_back(0);
     ctx->init_pending.push_back(0);
     ctx->init_from_host.push_back(0);
+    ctx->e0_valid.push_back(0);
+    ctx->e0_deferred.push_back(0);
   }
   ctx->P.n_inst = (int)ctx->inst.size();
   ctx->P.B = ctx->P.n_inst * ctx->R;
@@ -663,10 +676,21 @@ int register_instances(qis_ctx* ctx, int first, const std::vector<InstDesc>& ds)
 namespace {
 
 // Start (Alg. 3: the initial state as the only list entry) every search whose instance got new
-// initial states since the last flush: one launch per run of consecutive such instances.
-// Called first by every entry point that reads or changes the searches.
-int flush_init(qis_ctx* ctx) {
+// initial states, or was reset, since the last flush: one launch per run of consecutive such
+// instances. Called first by every entry point that reads or changes the searches.
+// defer (qis_iterate, when the fused search kernel runs at least one iteration): the initial
+// energies of the split modes are not computed here; the kernel forms them from the exact fields
+// of the first iteration (E = (sum_i s_i f_i + sum_i s_i h_i) / 2), which the tensor-core GEMM
+// computes for every initial state anyway. Otherwise they come from k_init_energy, or from
+// init_E / init_q when those still hold them.
+int flush_init(qis_ctx* ctx, bool defer) {
   const int ni = (int)ctx->init_pending.size();
+  if (ctx->e0_unresolved) {   // a deferred start whose kernel never ran: start those again
+    for (int x = 0; x < ni; ++x)
+      if (ctx->e0_deferred[x]) ctx->init_pending[x] = 1;
+    ctx->e0_unresolved = false;
+  }
+  std::fill(ctx->e0_deferred.begin(), ctx->e0_deferred.end(), 0);
   for (int a = 0; a < ni;) {
     if (!ctx->init_pending[a]) {
       ++a;
@@ -689,13 +713,23 @@ int flush_init(qis_ctx* ctx) {
       x = y;
     }
     // split modes: the initial energies of the range in groups of states per block first
+    // (unless they are known or deferred); FP64 mode: formed by k_init_search itself
     const bool grouped = ctx->mode != QIS_FP64;
-    if (grouped) {
+    bool known = true;
+    for (int x = a; x < e; ++x) known = known && ctx->e0_valid[x];
+    const bool deferred = grouped && defer && !known;
+    if (deferred) {
+      for (int x = a; x < e; ++x) ctx->e0_deferred[x] = 1;
+      ctx->e0_unresolved = true;
+    } else if (grouped && !known) {
       int max_n = 0;
       for (int x = a; x < e; ++x) max_n = std::max(max_n, ctx->inst[x].n);
       LAUNCH(launch_init_energy(ctx->P, a, e - a, max_n, ctx->stream));
     }
-    LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream, grouped));
+    LAUNCH(launch_init_search(ctx->P, ctx->inst[a].first_search, (e - a) * ctx->R, ctx->stream,
+                              known || (grouped && !deferred), deferred));
+    if (!deferred)
+      for (int x = a; x < e; ++x) ctx->e0_valid[x] = 1;
     a = e;
   }
   return 0;
@@ -703,10 +737,10 @@ int flush_init(qis_ctx* ctx) {
 
 }  // namespace
 
-#define FLUSH_INIT(ctx)              \
-  do {                               \
-    const int rc_ = flush_init(ctx); \
-    if (rc_) return rc_;             \
+#define FLUSH_INIT(ctx)                     \
+  do {                                      \
+    const int rc_ = flush_init(ctx, false); \
+    if (rc_) return rc_;                    \
   } while (0)
 
 int qis_create_instance(qis_ctx* ctx, int n, const double* J, const double* h, int* instance_id) {
@@ -805,6 +839,9 @@ int qis_clear_instances(qis_ctx* ctx) {
   ctx->inst_ready.clear();
   ctx->init_pending.clear();
   ctx->init_from_host.clear();
+  ctx->e0_valid.clear();
+  ctx->e0_deferred.clear();
+  ctx->e0_unresolved = false;
   ctx->P.n_inst = 0;
   ctx->P.B = 0;
   ctx->work_dirty = true;
@@ -856,6 +893,7 @@ int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits) {
   // launch for every instance set since)
   ctx->init_from_host[instance_id] = 1;
   ctx->init_pending[instance_id] = 1;
+  ctx->e0_valid[instance_id] = 0;
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   return 0;
@@ -876,6 +914,7 @@ int qis_init_states_learned(qis_ctx* ctx, int instance_id, qis_mlp* m) {
                         ctx->P.init_bits + (size_t)d.first_search * ctx->Wmax, ctx->Wmax, ctx->stream));
   ctx->launches += 5;
   ctx->init_pending[instance_id] = 1;
+  ctx->e0_valid[instance_id] = 0;
   ctx->inst_ready[instance_id] = 1;
   ctx->merged_fresh = false;
   CK(cudaStreamSynchronize(ctx->stream));
@@ -896,19 +935,24 @@ int qis_set_wait_limit(qis_ctx* ctx, uint64_t limit_ns, int probe) {
 
 int qis_reset(qis_ctx* ctx) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
-  FLUSH_INIT(ctx);
   for (size_t i = 0; i < ctx->inst.size(); ++i)
     if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
+  CK(cudaSetDevice(ctx->cfg.device));
   CK(cudaMemsetAsync(ctx->P.status, 0, sizeof(int), ctx->stream));
-  LAUNCH(launch_init_search(ctx->P, 0, ctx->P.B, ctx->stream, true));   // energies of the stored states
+  // every search starts again from its stored initial state at the next entry point (one
+  // launch; the initial energies as known, or formed by the first iteration of a fused call)
+  std::fill(ctx->init_pending.begin(), ctx->init_pending.end(), 1);
   ctx->merged_fresh = false;
   return 0;
 }
 
 int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
   if (!ctx) return fail(nullptr, QIS_ERR_INVALID_ARG, "ctx is NULL");
-  FLUSH_INIT(ctx);
   if (n_iters < 0) return fail(ctx, QIS_ERR_INVALID_ARG, "n_iters must be >= 0");
+  {   // searches that start here leave their initial energies to the fused kernel
+    const int rc = flush_init(ctx, n_iters > 0 && fused_search(ctx));
+    if (rc) return rc;
+  }
   if (ctx->inst.empty()) return fail(ctx, QIS_ERR_STATE, "no instance");
   for (size_t i = 0; i < ctx->inst.size(); ++i)
     if (!ctx->inst_ready[i]) return fail(ctx, QIS_ERR_STATE, "qis_init_states was not called for every instance");
@@ -949,6 +993,7 @@ int qis_iterate(qis_ctx* ctx, int n_iters, int* n_active) {
       const int rc = launch_iterations_fused(ctx, n_iters, s);
       if (rc) return rc;
     }
+    ctx->e0_unresolved = false;   // the search kernel that forms the deferred energies is enqueued
   } else if (!ctx->profiling && ctx->use_graph) {
     // one iteration = five kernels, captured once into a CUDA graph and replayed
     if (ctx->graph_exec && ctx->graph_n != 0) drop_graph(ctx);   // a graph of the fused form
@@ -1044,12 +1089,12 @@ namespace {
 
 // Write one search's kept list (entries in key order) into the device list of search b. The
 // caller has validated the arguments; hashes are computed on the device from the bits.
-int flush_init(qis_ctx* ctx);
+int flush_init(qis_ctx* ctx, bool defer);
 
 int import_search(qis_ctx* ctx, int b, int W, int q, int count, const uint64_t* bits, const double* E,
                   const uint8_t* used, const uint64_t* stamp, int t) {
   {   // a pending start of the instance's searches comes first (its initial energies stay)
-    const int rc = flush_init(ctx);
+    const int rc = flush_init(ctx, false);
     if (rc) return rc;
   }
   const int K1 = ctx->K1, Wm = ctx->Wmax;

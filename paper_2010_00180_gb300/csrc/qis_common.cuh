@@ -99,6 +99,8 @@ struct DevPtrs {
   uint64_t* init_bits;    // [b][Wmax]
   double* init_E;         // [b] energy of the initial state (set with it)
   long long* init_q;      // [b] the same, exact E 2^q (split modes)
+  int* e0_pend;           // [b] 1: E(psi0) not formed yet; the fused search kernel's first
+                          // iteration forms it from psi0's exact fields (split modes)
   int* status;            // [0] error bits
   unsigned long long wait_ns;  // bound of every device-side wait (%globaltimer ns; 2 s by default)
   int wait_probe;         // 1: the field GEMM's MMA thread first waits on a barrier that nothing
@@ -325,7 +327,8 @@ cudaError_t launch_fields_tc(const DevPtrs& P, const void* D16, const void* S16,
 int gemm_tile_n(int R, int digits);
 cudaError_t launch_quantize(const DevPtrs& P, const InstDesc& d, int inst, __half* D16, long long* Jq,
                             float* J4, long long* hq, cudaStream_t s);
-cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached = false);
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached = false,
+                               bool deferred = false);
 cudaError_t launch_hash_list(const DevPtrs& P, int b, int count, cudaStream_t s);
 cudaError_t launch_pick(const DevPtrs& P, cudaStream_t s);
 cudaError_t launch_fields_exact(const DevPtrs& P, cudaStream_t s);

@@ -242,11 +242,14 @@ cudaError_t launch_rowmax4(const DevPtrs& P, const InstDesc& d, cudaStream_t s) 
 
 // ---------------------------------------------------------------- search initialisation
 // Alg. 3 initial list: [psi0, K placeholders], E(psi0) from Eq. (1), nothing used.
-// cached: E(psi0) is taken from init_E / init_q, written by k_init_energy (split modes: exact
-// int64 E 2^q, several states per block) or by an earlier launch for the same initial states
-// (qis_reset). Otherwise (FP64 mode) one thread adds the pair terms i-major, j ascending, then
-// the field terms.
-__global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cached) {
+// mode 1 (cached): E(psi0) is taken from init_E / init_q, written by k_init_energy (split modes:
+// exact int64 E 2^q, several states per block) or by an earlier launch for the same initial
+// states. Mode 2 (deferred, split modes): E(psi0) is left to the first iteration of the fused
+// search kernel, which forms it from the exact fields of psi0 that the iteration computes anyway;
+// the entry holds 0 until then and e0_pend marks the search. Mode 0 (FP64 mode): one thread adds
+// the pair terms i-major, j ascending, then the field terms.
+__global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int mode) {
+  const bool cached = mode == 1;
   const int b = b0 + blockIdx.x;
   const InstDesc d = P.inst[b / P.R];
   const int n = d.n, np = d.n_pad, W = d.W;
@@ -258,6 +261,8 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
   if (cached) {
     E0 = P.init_E[b];
     if (threadIdx.x == 0) red[0] = P.init_q[b];
+  } else if (mode == 2) {
+    if (threadIdx.x == 0) red[0] = 0;
   } else if (threadIdx.x == 0) {
     double Pp = 0.0, F = 0.0;
     const double* J = P.J64 + d.off_mat;
@@ -301,12 +306,13 @@ __global__ void __launch_bounds__(256) k_init_search(DevPtrs P, int b0, int cach
     P.iter_t[b] = 0;
     if (P.ring_t0) P.ring_t0[b] = 0;
     P.surv_cnt[b] = 0;
+    P.e0_pend[b] = mode == 2;
   }
 }
 
-cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached) {
+cudaError_t launch_init_search(const DevPtrs& P, int b0, int nb, cudaStream_t s, bool cached, bool deferred) {
   if (nb <= 0) return cudaSuccess;
-  k_init_search<<<nb, 256, 0, s>>>(P, b0, cached ? 1 : 0);
+  k_init_search<<<nb, 256, 0, s>>>(P, b0, deferred ? 2 : cached ? 1 : 0);
   return cudaGetLastError();
 }
 

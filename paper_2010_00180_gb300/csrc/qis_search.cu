@@ -147,6 +147,27 @@ static __device__ __noinline__ void sort_pairs_any(unsigned long long* sk, unsig
   bitonic_sort_smem(sk, se, m2);
 }
 
+// Exact energy E 2^q of an initial state whose energy the search initialisation left to this
+// kernel, from the exact fields of its first iteration (Eq. 1): with f = J s + h,
+// sum_i s_i f_i = 2 sum_{i<j} J_ij s_i s_j + sum_i h_i s_i, so E = (sum_i s_i f_i + sum_i s_i h_i) / 2,
+// and s_i f_i = -aq_i / 2. Both halvings are exact (aq_i is even; the sum is twice an integer).
+// red: kSNT / 32 free words of shared memory. Out of line (once per search and run).
+static __device__ __noinline__ long long initial_energy(const DevPtrs& P, const InstDesc& d, const uint64_t* pb,
+                                                        const long long* aq, long long* red) {
+  long long acc = 0;
+  for (int i = threadIdx.x; i < d.n; i += blockDim.x) {
+    const long long hq = P.hq[d.off_vec + i];
+    acc += (sigma_of(pb, i) ? -hq : hq) - aq[i] / 2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  long long tot = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  return tot / 2;
+}
+
 // FL: flip set (QIS_FLIPS_*). One block of kSNT threads per search; n_iters >= 1.
 template <int FL>
 __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_iters) {
@@ -199,6 +220,20 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       mx = fmaxf(mx, v.x);
     }
   __syncthreads();
+  if (act0 && P.e0_pend[b]) {   // block-uniform: the list is [psi0] and psi0 is the parent
+    Epq = initial_energy(P, d, pb, aq_of(P, b, t_first), reinterpret_cast<long long*>(scr));
+    if (tid == 0) {
+      const int s0 = oslotA[0];
+      const double E0 = ldexp((double)Epq, -d.q);
+      okeyA[0] = qkey(Epq);
+      P.lst_q[base + s0] = Epq;
+      P.lst_E[base + s0] = E0;
+      P.init_q[b] = Epq;
+      P.init_E[b] = E0;
+      P.e0_pend[b] = 0;
+    }
+    __syncthreads();
+  }
 
   int act = act0, t = t_first, cur = 0;
   int nprod = 0;

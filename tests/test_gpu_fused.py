@@ -120,3 +120,58 @@ def test_fused_runs_every_iteration_in_one_launch():
     ctx.iterate(40)
     assert ctx.kernel_launches() - l0 == 4
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,ens", [("split_bf16", "gaussian"), ("pm1_fp8", "pm1")])
+def test_initial_energies_formed_by_the_first_iteration(prec, ens):
+    """When qis_iterate starts the searches, E(psi0) is formed by the fused kernel from the exact
+    fields of the first iteration ((sum_i s_i f_i + sum_i s_i h_i) / 2, Eq. 1); any other entry
+    point, or a start whose energies are already known, takes them from the rescoring kernel.
+    Every path must give E(psi0) of the oracle exactly (grid inputs: FP64 energies are exact),
+    and the searches must equal the oracle's, across resets, new initial states and queries
+    made before any iteration. (After one iteration psi0 has usually left the list: every
+    kept energy is then E(psi0) + dE, so the list equality checks E(psi0).)"""
+    n, K, R = 300, 30, 8
+    J, h = I.instance(ens, n, seed=21)
+    phi = I.random_states(n, R, seed=22)
+    E0 = O.energies(J, h, phi)
+    ctx = qis.Context(K=K, R=R, precision=prec, max_n=n, max_instances=1)
+    ctx.create_instance(J, h)
+
+    def psi0_energies():
+        out = []
+        for r in range(R):
+            lst = ctx.search_list(0, r)
+            k = np.flatnonzero(lst["stamp"] == 0)
+            assert len(k) == 1
+            assert np.array_equal(lst["bits"][k[0]], phi[r])
+            out.append(lst["E"][k[0]])
+        return np.array(out)
+
+    def equals_oracle(iters):
+        for r in range(R):
+            got = ctx.search_list(0, r)
+            ref = O.qi_search(J, h, K, iters, phi[r])
+            c = ref["count"]
+            assert got["count"] == c
+            for key in ("bits", "E", "stamp", "used"):
+                assert np.array_equal(got[key], ref[key][:c]), key
+
+    ctx.init_states(0, phi)
+    ctx.iterate(1)                      # started by qis_iterate: energies from the first iteration
+    equals_oracle(1)                    # every new state's energy is E(psi0) + dE
+    ctx.reset()
+    assert np.array_equal(psi0_energies(), E0)   # started by a query: the rescoring kernel
+    ctx.iterate(4)                      # the same searches continue (energies known)
+    equals_oracle(4)
+    ctx.reset()
+    ctx.iterate(0)                      # no iteration: started without deferring
+    assert np.array_equal(psi0_energies(), E0)
+    ctx.init_states(0, phi)             # new initial states, then several calls
+    ctx.iterate(2)
+    ctx.iterate(3)
+    equals_oracle(5)
+    ctx.reset()
+    ctx.iterate(5)
+    equals_oracle(5)
+    ctx.close()
