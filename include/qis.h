@@ -137,11 +137,18 @@ int qis_instance_n(qis_ctx* ctx, int instance_id, int* n);
  *         value (r*n + i) of the stream keyed by key(seed, id), i.e. rand_between(0, 2^n-1)
  *         of Alg. 4.
  * The searches start (initial energies, lists) with one launch for every instance set since,
- * at the next call that reads or advances them; the caller's buffer is free on return. */
+ * at the next call that reads or advances them; the caller's buffer is free on return. When
+ * that call is qis_iterate with at least one iteration of the fused search kernel (the exact
+ * modes with a padded n up to 1024), the initial energies are formed in the first iteration
+ * from the initial states' exact local fields, E = (sum_i s_i f_i + sum_i s_i h_i) / 2 (Eq. 1
+ * with f = J s + h), which that iteration computes anyway; every other call forms them by a
+ * separate rescoring launch. Both give the same exact value. */
 int qis_init_states(qis_ctx* ctx, int instance_id, const uint64_t* bits);
 
 /* Reset every search of every instance to its stored initial state (device-side, no host
- * copy). Also clears the device error flags (timeout, survivor overflow) of earlier iterations. */
+ * copy): the searches restart, as after qis_init_states, at the next call that reads or
+ * advances them. Also clears the device error flags (timeout, survivor overflow) of earlier
+ * iterations. */
 int qis_reset(qis_ctx* ctx);
 
 /* Run n_iters iterations of Alg. 3 on every search of every instance (lockstep).

@@ -901,7 +901,20 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) k_search(DevPtrs P, int n_i
       int i, j;
       surv_decode(se[p], c, i, j);
       uint64_t* dst = P.lst_bits + (base + slot) * Wm;
-      for (int x = 0; x < W; ++x) dst[x] = pb[x] ^ flip_mask(x, i, j);
+      {   // the parent's words, two per store when the rows are 16-byte aligned (fewer store
+          // instructions of scattered rows than one word each), then the words of the flipped
+          // sites stored again with their bits flipped (same thread and address: the later wins)
+        int x = 0;
+        if ((Wm & 1) == 0)
+          for (; x + 1 < W; x += 2)
+            *reinterpret_cast<ulonglong2*>(dst + x) = *reinterpret_cast<const ulonglong2*>(pb + x);
+        for (; x < W; ++x) dst[x] = pb[x];
+        const int wi = i >> 6;
+        uint64_t vi = pb[wi] ^ (1ull << (i & 63));
+        if (j >= 0 && (j >> 6) == wi) vi ^= 1ull << (j & 63);
+        dst[wi] = vi;
+        if (j >= 0 && (j >> 6) != wi) dst[j >> 6] = pb[j >> 6] ^ (1ull << (j & 63));
+      }
       const uint64_t stamp = ((uint64_t)t << 32) | c;
       P.lst_q[base + slot] = (long long)(kp ^ (1ull << 63));
       P.lst_stamp[base + slot] = stamp;
