@@ -109,13 +109,16 @@ __global__ void k_restride(const double* src, int n, int n_pad, double* dst) {
   }
 }
 
+// Rows i = blockIdx.x, blockIdx.x + gridDim.x, ... of every instance (blockIdx.y), the threads
+// over the columns: coalesced reads of the caller's rows (page-locked host memory read in place
+// where it is), no index division.
 __global__ void k_restride_batch(const LayoutItem* items, double* J64) {
   const LayoutItem L = items[blockIdx.y];
-  const long long total = (long long)L.n_pad * L.n_pad;
   double* dst = J64 + L.off_mat;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / L.n_pad), j = (int)(e % L.n_pad);
-    dst[e] = (i < L.n && j < L.n) ? L.src[(long long)i * L.n + j] : 0.0;
+  for (int i = blockIdx.x; i < L.n_pad; i += gridDim.x) {
+    const double* src = L.src + (long long)i * L.n;
+    double* row = dst + (long long)i * L.n_pad;
+    for (int j = threadIdx.x; j < L.n_pad; j += blockDim.x) row[j] = (i < L.n && j < L.n) ? src[j] : 0.0;
   }
 }
 
@@ -123,9 +126,7 @@ __global__ void k_restride_batch(const LayoutItem* items, double* J64) {
 cudaError_t launch_layout_batch(const DevPtrs& P, const LayoutItem* items, int count, int max_n_pad, double* J64,
                                 cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const long long total = (long long)max_n_pad * max_n_pad;
-  const int bx = (int)std::min<long long>((total + 255) / 256, 2048);
-  k_restride_batch<<<dim3(bx, count), 256, 0, s>>>(items, J64);
+  k_restride_batch<<<dim3(max_n_pad, count), 256, 0, s>>>(items, J64);
   k_validate_batch<<<dim3((max_n_pad + 7) / 8, count), 256, 0, s>>>(items, P.J64, P.h64);
   return cudaGetLastError();
 }
@@ -161,26 +162,55 @@ __global__ void k_quantize(const double* J64, const double* h64, int n, int n_pa
   if (e < n_pad) hq[e] = (e < n) ? __double2ll_rn(ldexp(h64[e], q)) : 0;
 }
 
-// Instances first .. first+count-1 at once (blockIdx.y), descriptors read on the device.
+// x 2^q rounded to the nearest integer, ties to even (what __double2ll_rn(ldexp(x, q)) gives),
+// from the bit pattern of x with integer operations only (GB300's FP64 pipe is narrow). x is
+// finite (validated) and |x 2^q| < 2^62 (the grid is chosen so).
+__device__ __forceinline__ long long fixed_point_rn(double x, int q) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  unsigned long long m = u & 0xfffffffffffffull;
+  if (e == 0 && m == 0) return 0;
+  if (e != 0) m |= 1ull << 52;                    // normal: the implicit bit
+  const int sh = (e == 0 ? 1 : e) - 1075 + q;     // |x| 2^q = m 2^sh
+  long long v;
+  if (sh >= 0) {
+    v = (long long)(m << sh);
+  } else if (sh <= -54) {
+    v = 0;   // below 1/2
+  } else {
+    const int r = -sh;
+    const unsigned long long t = m >> r, rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+    v = (long long)(t + ((rem > half || (rem == half && (t & 1ull))) ? 1ull : 0ull));
+  }
+  return (u >> 63) ? -v : v;
+}
+
+// Instances first .. first+count-1 at once (blockIdx.y), descriptors read on the device; rows
+// i = blockIdx.x, blockIdx.x + gridDim.x, ..., the threads over the columns (no index division).
+// Jq = rn(J 2^q), J4 = fl32(4 Jq 2^-q) (= fl32(Jq) 2^(2-q): scaling by a power of two commutes
+// with rounding), the balanced base-2^dbits digits of Jq.
 __global__ void k_quantize_batch(DevPtrs P, int first, __half* D16, long long* Jq, float* J4, long long* hq) {
   const int inst = first + blockIdx.y;
   const InstDesc d = P.inst[inst];
-  const long long tot = (long long)d.n_pad * d.n_pad;
   const double* J64 = P.J64 + d.off_mat;
   __half* D = D16 + (long long)inst * P.NP * P.NP;
   const long long base = 1ll << d.dbits;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / d.n_pad), j = (int)(e % d.n_pad);
-    long long v = 0;
-    if (i < d.n && j < d.n) v = __double2ll_rn(ldexp(J64[e], d.q));
-    Jq[d.off_mat + e] = v;
-    J4[d.off_mat + e] = (float)(4.0 * ldexp((double)v, -d.q));
-    long long x = v;
-    for (int dg = 0; dg < d.digits; ++dg) {
-      long long r = x & (base - 1);           // x mod base
-      if (r >= base / 2) r -= base;           // balanced digit in [-base/2, base/2)
-      D[dg * P.pool_mat + d16_offset(i, j, P.NP)] = __float2half_rn((float)r);
-      x = (x - r) >> d.dbits;                 // exact
+  const bool wide_q = d.q > 120;   // 2^(2-q) below the normal floats (tiny couplings): FP64 path
+  const float s4 = wide_q ? 0.f : __int_as_float((127 + 2 - d.q) << 23);   // 2^(2-q)
+  for (int i = blockIdx.x; i < d.n_pad; i += gridDim.x) {
+    for (int j = threadIdx.x; j < d.n_pad; j += blockDim.x) {
+      const long long e = (long long)i * d.n_pad + j;
+      long long v = 0;
+      if (i < d.n && j < d.n) v = fixed_point_rn(J64[e], d.q);
+      Jq[d.off_mat + e] = v;
+      J4[d.off_mat + e] = wide_q ? (float)(4.0 * ldexp((double)v, -d.q)) : __ll2float_rn(v) * s4;
+      long long x = v;
+      for (int dg = 0; dg < d.digits; ++dg) {
+        long long r = x & (base - 1);           // x mod base
+        if (r >= base / 2) r -= base;           // balanced digit in [-base/2, base/2)
+        D[dg * P.pool_mat + d16_offset(i, j, P.NP)] = __float2half_rn((float)(int)r);
+        x = (x - r) >> d.dbits;                 // exact
+      }
     }
   }
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d.n_pad; e += gridDim.x * blockDim.x)
@@ -205,9 +235,7 @@ __global__ void __launch_bounds__(256) k_rowmax4_batch(DevPtrs P, int first) {
 cudaError_t launch_prepare_batch(const DevPtrs& P, int first, int count, int max_n_pad, __half* D16, long long* Jq,
                                  float* J4, long long* hq, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const long long tot = (long long)max_n_pad * max_n_pad;
-  const int bx = (int)std::min<long long>((tot + 255) / 256, 2048);
-  k_quantize_batch<<<dim3(bx, count), 256, 0, s>>>(P, first, D16, Jq, J4, hq);
+  k_quantize_batch<<<dim3(max_n_pad, count), 256, 0, s>>>(P, first, D16, Jq, J4, hq);
   k_rowmax4_batch<<<dim3((max_n_pad + 7) / 8, count), 256, 0, s>>>(P, first);
   return cudaGetLastError();
 }
